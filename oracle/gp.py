@@ -1,0 +1,377 @@
+"""Plain recursive FP64 evaluator, scaled MSE and gradients (the oracle).
+
+Test infrastructure only (see the package docstring).  Every function cites
+the passage of the paper it follows; readings of points the paper leaves
+open are marked READING and listed in the design doc.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "ADD", "SUB", "MUL", "AQ", "SIN", "COS", "EXP", "LOG_ABS", "SQRT_ABS", "DIV",
+    "SQUARE", "LOG", "SQRT", "ERC", "FEAT0", "PAD", "BINARY", "UNARY", "BIG",
+    "VAR_TOL", "InvalidTemplate", "Template", "active_mask", "rpn", "paper_encoding",
+    "eval_tree", "eval_tree_f32", "fitness", "grad", "fd_grad", "eval_batch",
+]
+
+# Template opcodes: the library's documented interface values.
+ADD, SUB, MUL, AQ = 0, 1, 2, 3
+SIN, COS, EXP, LOG_ABS, SQRT_ABS = 4, 5, 6, 7, 8
+DIV, SQUARE, LOG, SQRT = 9, 10, 11, 12
+ERC = 31
+FEAT0 = 32
+PAD = 255
+BINARY = (ADD, SUB, MUL, AQ, DIV)
+UNARY = (SIN, COS, EXP, LOG_ABS, SQRT_ABS, SQUARE, LOG, SQRT)
+
+#: READING: a trial whose output exceeds this magnitude at any row (or is
+#: non-finite there) has fitness +inf.  2**50 keeps every FP32 square and
+#: product of the fitness sums finite.
+BIG = 2.0 ** 50
+#: READING: a population variance of f at or below VAR_TOL * mean(f)^2 is
+#: treated as zero (a constant tree): b* = 0, a* = mean(y).
+VAR_TOL = 1e-12
+
+
+class InvalidTemplate(ValueError):
+    pass
+
+
+class Template:
+    """One trial: a fixed-shape arity-2 template of height ``h``.
+
+    Section 3.1: an individual is a fixed-length string mapped onto a tree
+    template; nodes not reached from the root are introns.  ``layout`` is
+    "heap" (children 2i+1, 2i+2) or "prefix" (pre-order of the full
+    template; children p+1 and p+2**s for a node whose subtree has height s).
+    """
+
+    def __init__(self, op, cval, h: int, layout: str = "heap", n_features: int | None = None):
+        self.op = np.asarray(op).astype(np.int64)
+        self.cval = np.asarray(cval, dtype=np.float32)
+        self.h = int(h)
+        self.layout = layout
+        self.n_features = n_features
+        if layout not in ("heap", "prefix"):
+            raise ValueError(layout)
+        if self.op.size < (1 << (self.h + 1)) - 1:
+            raise InvalidTemplate("template row shorter than 2**(h+1)-1")
+
+    def children(self, pos: int, depth: int):
+        if self.layout == "heap":
+            return 2 * pos + 1, 2 * pos + 2
+        return pos + 1, pos + (1 << (self.h - depth))
+
+    def check(self, pos: int, depth: int) -> int:
+        """Validate one ACTIVE node and return its opcode.  READING: an intron
+        may hold anything; an active node must be a known opcode, a function
+        must not sit at a leaf position, a feature index must be < F."""
+        o = int(self.op[pos])
+        if o in BINARY or o in UNARY:
+            if depth >= self.h:
+                raise InvalidTemplate(f"function {o} at leaf position {pos}")
+            return o
+        if o == ERC:
+            return o
+        if FEAT0 <= o < PAD:
+            if self.n_features is not None and o - FEAT0 >= self.n_features:
+                raise InvalidTemplate(f"feature {o - FEAT0} >= {self.n_features}")
+            return o
+        raise InvalidTemplate(f"opcode {o} active at position {pos}")
+
+
+def active_mask(t: Template) -> np.ndarray:
+    """Active nodes (Section 3.1, Fig. 1): the root is active; both children
+    of an active binary function are active; only child 0 (the left child)
+    of an active unary function is active (READING: Fig. 1 draws sin with
+    two children and fixes no operand); a terminal has no active children
+    (Fig. 1: the subtrees under the terminals -2 and x1 are introns)."""
+    mask = np.zeros(t.op.size, dtype=bool)
+
+    def visit(pos, depth):
+        o = t.check(pos, depth)
+        mask[pos] = True
+        if o in BINARY:
+            l, r = t.children(pos, depth)
+            visit(l, depth + 1)
+            visit(r, depth + 1)
+        elif o in UNARY:
+            l, _ = t.children(pos, depth)
+            visit(l, depth + 1)
+
+    visit(0, 0)
+    return mask
+
+
+def rpn(t: Template) -> list:
+    """Post-order traversal of the active nodes, left operand first
+    (Section 3.2: RPN, operators after their operands, introns ignored).
+    Returns a list of (position, opcode, constant)."""
+    out = []
+
+    def visit(pos, depth):
+        o = t.check(pos, depth)
+        if o in BINARY:
+            l, r = t.children(pos, depth)
+            visit(l, depth + 1)
+            visit(r, depth + 1)
+        elif o in UNARY:
+            l, _ = t.children(pos, depth)
+            visit(l, depth + 1)
+        out.append((pos, o, float(t.cval[pos])))
+
+    visit(0, 0)
+    return out
+
+
+#: the paper's operator indices in Fig. 1 (+ = 0, - = 1, x = 2, / = 3, sin = 4)
+PAPER_OP_INDEX = {ADD: 0, SUB: 1, MUL: 2, DIV: 3, SIN: 4}
+
+
+def paper_encoding(t: Template):
+    """(T, V) rows of Fig. 1: type 0 = variable, 1 = constant, 2 = operator;
+    value = variable index, constant value or operator index."""
+    T, V = [], []
+    for _, o, c in rpn(t):
+        if o >= FEAT0:
+            T.append(0)
+            V.append(float(o - FEAT0))
+        elif o == ERC:
+            T.append(1)
+            V.append(c)
+        else:
+            T.append(2)
+            V.append(float(PAPER_OP_INDEX[o]))
+    return T, V
+
+
+def _apply(o, a, b=None, xp=np):
+    """One function node.  AQ(a, b) = a / sqrt(1 + b^2) (analytic quotient,
+    Ni, Drieberg and Rockett 2013); log|x| and sqrt|x| are the protected
+    forms of the function set; DIV, SQUARE, LOG and SQRT are the paper's
+    Table 2 operators (plain division, square, unprotected log and sqrt).
+    Binary operands in template order: op(left, right)."""
+    if o == ADD:
+        return a + b
+    if o == SUB:
+        return a - b
+    if o == MUL:
+        return a * b
+    if o == AQ:
+        one = a.dtype.type(1)
+        return a / np.sqrt(one + b * b)
+    if o == DIV:
+        return a / b
+    if o == SIN:
+        return np.sin(a)
+    if o == COS:
+        return np.cos(a)
+    if o == EXP:
+        return np.exp(a)
+    if o == LOG_ABS:
+        return np.log(np.abs(a))
+    if o == SQRT_ABS:
+        return np.sqrt(np.abs(a))
+    if o == SQUARE:
+        return a * a
+    if o == LOG:
+        return np.log(a)
+    if o == SQRT:
+        return np.sqrt(a)
+    raise InvalidTemplate(o)
+
+
+def _eval(t: Template, X: np.ndarray, dtype, store=None) -> np.ndarray:
+    n = X.shape[0]
+
+    def visit(pos, depth):
+        o = t.check(pos, depth)
+        if o >= FEAT0:
+            v = X[:, o - FEAT0].astype(dtype)
+        elif o == ERC:
+            v = np.full(n, dtype(t.cval[pos]), dtype=dtype)
+        elif o in BINARY:
+            l, r = t.children(pos, depth)
+            v = _apply(o, visit(l, depth + 1), visit(r, depth + 1))
+        else:
+            l, _ = t.children(pos, depth)
+            v = _apply(o, visit(l, depth + 1))
+        if store is not None:
+            store[pos] = v
+        return v
+
+    with np.errstate(all="ignore"):
+        return visit(0, 0)
+
+
+def eval_tree(t: Template, X: np.ndarray) -> np.ndarray:
+    """f(x_i) for every row i, recursively from the root in FP64
+    (Section 3.2: each subexpression is evaluated before its parent)."""
+    return _eval(t, np.asarray(X), np.float64)
+
+
+def eval_tree_f32(t: Template, X: np.ndarray) -> np.ndarray:
+    """The same recursion with every node value rounded to float32 and
+    float32 library functions.  Used only to flag ill-conditioned rows."""
+    return _eval(t, np.asarray(X, dtype=np.float32), np.float32)
+
+
+def _overflowed(f: np.ndarray) -> bool:
+    with np.errstate(all="ignore"):
+        return (not np.all(np.isfinite(f))) or bool(np.any(np.abs(f) > BIG))
+
+
+def fitness(f: np.ndarray, y: np.ndarray) -> dict:
+    """MSE (Eq. 1), NMSE (Eq. 2) and linearly scaled MSE of one trial.
+
+    smse = min_{a,b} (1/N) sum_i (y_i - a - b f_i)^2, reached at
+    b* = cov(f, y) / var(f), a* = mean(y) - b* mean(f) (ordinary least
+    squares of y on f).  Two centred FP64 passes give the means and the
+    centred sums; smse is then a third, direct pass over the residuals.
+    Variances use 1/N (READING: Eq. 2 does not say; 1/N matches Eq. 1)."""
+    f = np.asarray(f, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = f.size
+    if n == 0 or _overflowed(f):
+        return dict(smse=math.inf, mse=math.inf, a=0.0, b=0.0, nmse=math.inf,
+                    var_f=math.nan, finite=False)
+    fbar = float(np.sum(f) / n)
+    ybar = float(np.sum(y) / n)
+    fc = f - fbar
+    yc = y - ybar
+    var_f = float(np.sum(fc * fc) / n)
+    cov = float(np.sum(fc * yc) / n)
+    var_y = float(np.sum(yc * yc) / n)
+    if var_f <= VAR_TOL * fbar * fbar:
+        b = 0.0
+    else:
+        b = cov / var_f
+    a = ybar - b * fbar
+    smse = float(np.sum((y - a - b * f) ** 2) / n)
+    mse = float(np.sum((f - y) ** 2) / n)
+    return dict(smse=smse, mse=mse, a=a, b=b, nmse=mse / var_y if var_y > 0 else math.inf,
+                var_f=var_f, finite=True)
+
+
+def _dapply(o, a, b, out):
+    """Local partial derivatives of one function node at its inputs (a, b)
+    and its output ``out``.  READING at kinks: d sqrt|x| / dx = 0 at x = 0."""
+    one = 1.0
+    if o == ADD:
+        return np.ones_like(a), np.ones_like(b)
+    if o == SUB:
+        return np.ones_like(a), -np.ones_like(b)
+    if o == MUL:
+        return b, a
+    if o == AQ:
+        q = one / np.sqrt(one + b * b)
+        return q, -a * b * q * q * q
+    if o == DIV:
+        return one / b, -a / (b * b)
+    if o == SIN:
+        return np.cos(a), None
+    if o == COS:
+        return -np.sin(a), None
+    if o == EXP:
+        return out, None
+    if o == LOG_ABS or o == LOG:
+        return one / a, None
+    if o == SQRT_ABS:
+        s = np.sqrt(np.abs(a))
+        return np.where(a == 0, 0.0, np.sign(a) / (2.0 * np.where(s == 0, 1.0, s))), None
+    if o == SQRT:
+        return 0.5 / out, None
+    if o == SQUARE:
+        return 2.0 * a, None
+    raise InvalidTemplate(o)
+
+
+def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse"):
+    """Reverse-mode FP64 gradient of smse (or mse) with respect to the
+    constant of every active ERC node; 0 at every other template position.
+
+    For smse, a* and b* are the least-squares optimum, so their own
+    partials vanish (envelope theorem) and
+        d smse / d c_k = (2 b*/N) sum_i (a* + b* f_i - y_i) d f_i / d c_k.
+    For mse: (2/N) sum_i (f_i - y_i) d f_i / d c_k.  READING: the gradient
+    is 0 for trials with infinite fitness and (smse) for b* = 0.
+    Returns (gradient float64 [stride], fitness dict)."""
+    X = np.asarray(X)
+    y = np.asarray(y, dtype=np.float64)
+    vals = {}
+    f = _eval(t, X, np.float64, store=vals)
+    fit = fitness(f, y)
+    g = np.zeros(t.op.size, dtype=np.float64)
+    n = f.size
+    if not fit["finite"]:
+        return g, fit
+    if mode == "smse":
+        if fit["b"] == 0.0:
+            return g, fit
+        seed = (2.0 / n) * fit["b"] * (fit["a"] + fit["b"] * f - y)
+    elif mode == "mse":
+        seed = (2.0 / n) * (f - y)
+    else:
+        raise ValueError(mode)
+
+    def back(pos, depth, adj):
+        o = int(t.op[pos])
+        if o == ERC:
+            g[pos] += float(np.sum(adj))
+            return
+        if o >= FEAT0:
+            return
+        l, r = t.children(pos, depth)
+        if o in BINARY:
+            da, db = _dapply(o, vals[l], vals[r], vals[pos])
+            back(l, depth + 1, adj * da)
+            back(r, depth + 1, adj * db)
+        else:
+            da, _ = _dapply(o, vals[l], None, vals[pos])
+            back(l, depth + 1, adj * da)
+
+    with np.errstate(all="ignore"):
+        back(0, 0, seed)
+    return g, fit
+
+
+def fd_grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse",
+            rel_step: float = 1e-6) -> np.ndarray:
+    """Central finite differences of smse (or mse) in every active ERC
+    constant, step h = rel_step * max(1, |c|), constants held in FP64."""
+    mask = active_mask(t)
+    g = np.zeros(t.op.size, dtype=np.float64)
+    X = np.asarray(X)
+
+    def value(pos, c):
+        tt = Template(t.op, t.cval, t.h, t.layout, t.n_features)
+        # evaluate with an FP64 constant at ``pos`` (not rounded to float32)
+        vals = {}
+        saved = tt.cval
+        tt.cval = saved.astype(np.float64)
+        tt.cval[pos] = c
+        f = _eval(tt, X, np.float64, store=vals)
+        return fitness(f, y)[mode]
+
+    for pos in np.nonzero(mask & (t.op == ERC))[0]:
+        c = float(t.cval[pos])
+        h = rel_step * max(1.0, abs(c))
+        g[pos] = (value(pos, c + h) - value(pos, c - h)) / (2.0 * h)
+    return g
+
+
+def eval_batch(op, cval, heights, h_max, X, y, layout="heap", n_features=None):
+    """Fitness of every trial of a batch: arrays smse, a, b, mse (float64)."""
+    op = np.asarray(op)
+    P = op.shape[0]
+    out = {k: np.zeros(P) for k in ("smse", "a", "b", "mse")}
+    for p in range(P):
+        h = int(heights[p]) if heights is not None else int(h_max)
+        t = Template(op[p], cval[p], h, layout, n_features)
+        fit = fitness(eval_tree(t, X), y)
+        for k in out:
+            out[k][p] = fit[k]
+    return out
