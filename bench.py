@@ -1,0 +1,399 @@
+"""Benchmark: batched fitness evaluation of one GOM/FOS step on GB300.
+
+One step = one batched evaluation of every trial of one FOS step (pack,
+batched forward, finalise), replayed as a CUDA graph, on the workload
+"fos-step-4096xh4-100000x8": 4,096 trials of height 4 (31 nodes, full
+function set), X 100,000 x 8 ~ U[-3, 3], y from a seeded height-4 tree plus
+1 % noise.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (a 512 MB write) between timed steps.  Reported:
+
+  value      node-row evals/s (active nodes x rows x trials / s), graph form
+  e2e        the same through the C ABI with pinned HOST buffers: the H2D
+             copy of the trial arrays and the D2H copy of the fitness inside
+             every step
+  plain      the one-launch-per-trial form (multi-block per trial + a
+             second-stage reduction launch per trial)
+  roofline   the batched forward kernel against the FP32 issue peak
+             (152 SMs x 128 lanes x the SM clock sampled during the run)
+  cpu_baseline  the FP64 oracle on the host cores, on a sample of trials
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = ("node-row evals/sec and trial fitness evals/sec at scaled-MSE rel err ≤1e-4, "
+          "batched vs plain")
+UNIT = "node-row evals/s"
+CFG = "c2"
+SMS, FP32_LANES, SFU_LANES = 152, 128, 16
+# algorithmic FP32 / SFU operations per evaluated node (by class) and per
+# row-trial for the fitness sums (shift, sum d, sum d^2, sum d*y)
+OPS_FP32 = {"term": 0, "addsubmul": 1, "aq": 2, "div": 1, "sincos": 2, "exp": 1, "log": 1,
+            "sqrt": 0, "square": 1}
+OPS_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, "log": 1,
+           "sqrt": 1, "square": 0}
+ACC_FP32 = 4
+STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
+             "sqrt": 8, "square": 9}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=CFG, choices=sorted(synth.CONFIGS))
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(cfg, rep, gg, torch, device):
+    """Seeded workload; the target comes from the library's own per-row
+    evaluation of the first usable generator tree."""
+    w = synth.workload(cfg, rep)
+    X = torch.from_numpy(w["X"])
+    dummy = torch.zeros(w["N"], dtype=torch.float32)
+    probe = gg.Dataset(X, dummy, device=device)
+    for gop, gcv, gh in w["y_cands"]():
+        f = probe.eval_rows(torch.from_numpy(gop[None]).cuda(device),
+                            torch.from_numpy(gcv[None]).cuda(device))[0].double().cpu().numpy()
+        if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
+            break
+    probe.sync()
+    probe.close()
+    w["y"] = synth.make_target(f, w["z"], w["noise"])
+    return w
+
+
+def node_counts(gg, torch, w):
+    st = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
+                        torch.from_numpy(w["heights"]) if "h_min" in synth.CONFIGS[w["cfg"]] else None,
+                        n_features=w["F"]).numpy()
+    ok = st[:, 0] >= 0
+    nodes = int(st[ok, 0].sum())
+    fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in STAT_COLS.items())
+    sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in STAT_COLS.items())
+    return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 10].sum())
+
+
+def cpu_baseline(w, seconds, torch):
+    """Time the FP64 oracle (as it stands) on a sample of the workload's
+    trials at the full row count, on one host core."""
+    import oracle as O
+    torch.set_num_threads(1)
+    P, N = w["P"], w["N"]
+    y = w["y"]
+    t0 = time.perf_counter()
+    done = nodes = 0
+    while done < P and time.perf_counter() - t0 < seconds:
+        t = O.Template(w["op"][done], w["cval"][done], int(w["heights"][done]), w["layout"], w["F"])
+        try:
+            O.fitness(O.eval_tree(t, w["X"]), y)
+            nodes += int(O.active_mask(t).sum())
+        except O.InvalidTemplate:
+            pass
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": nodes * N / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "trial_evals_per_s": done / el,
+            "sample": f"first {done} of {P} trials at all {N} rows ({el:.1f} s, FP64 numpy)"}
+
+
+def run_reference(a):
+    """The reference arm: the FP64 oracle on the host cores, each step a
+    bounded sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    import torch
+    torch.set_num_threads(1)
+    w = synth.workload(a.config, 0)
+    for gop, gcv, gh in w["y_cands"]():
+        f = O.eval_tree(O.Template(gop, gcv, gh, "heap", w["F"]), w["X"])
+        if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
+            break
+    y = synth.make_target(f, w["z"], w["noise"])
+    per_step = 1
+    idx = 0
+
+    def step():
+        nonlocal idx
+        nodes = 0
+        for _ in range(per_step):
+            p = idx % w["P"]
+            idx += 1
+            t = O.Template(w["op"][p], w["cval"][p], int(w["heights"][p]), w["layout"], w["F"])
+            O.fitness(O.eval_tree(t, w["X"]), y)
+            nodes += int(O.active_mask(t).sum())
+        return nodes
+
+    t0 = time.perf_counter()
+    step()
+    per_trial = time.perf_counter() - t0
+    # size each step so the whole run takes about cpu_seconds of host time
+    per_step = max(1, int(a.cpu_seconds / max(a.steps + a.warmup, 1) / per_trial))
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    nodes = sum(step() for _ in range(a.steps))
+    el = time.perf_counter() - t0
+    v = nodes * w["N"] / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "trials_per_step": per_step,
+                                        "rows": w["N"], "flush_l2": False},
+        "trial_evals_per_s": per_step * a.steps / el,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} trials per step at all {w['N']} rows"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import paper_2605_30954_gb300 as gg
+
+    rank, world, local = dist_env()
+    dev = local
+    torch.cuda.set_device(dev)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def allreduce(x, op):
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=op)
+        return t.item()
+
+    w = make_workload(a.config, rank, gg, torch, dev)
+    nodes, fp32_ops, sfu_ops, valid, instrs = node_counts(gg, torch, w)
+    N, P = w["N"], w["P"]
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
+    op = torch.from_numpy(w["op"]).cuda(dev)
+    cv = torch.from_numpy(w["cval"]).cuda(dev)
+    hs = torch.from_numpy(w["heights"]).cuda(dev) if "h_min" in synth.CONFIGS[a.config] else None
+    ds.autotune(op, cv, hs)
+    st = torch.cuda.Stream(dev)
+    outs = [torch.empty(P, device=f"cuda:{dev}") for _ in range(4)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+
+    def graph_step():
+        ds.eval_batch(op, cv, hs, flags=gg.F_GRAPH, stream=st, out=outs)
+
+    def timed(fn, steps, clocks=None, name="timed"):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        torch.cuda.nvtx.range_push(name)
+        for i in range(steps):
+            with torch.cuda.stream(st):
+                flush.fill_(float(i))
+                ev[i][0].record(st)
+                fn()
+                ev[i][1].record(st)
+        st.synchronize()
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        ck = clocks.stop() if clocks else None
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        return float(np.sum(ms)), ck
+
+    # ---- batched form, graph replay (the headline) ----
+    for _ in range(a.warmup):
+        with torch.cuda.stream(st):
+            graph_step()
+    st.synchronize()
+    clocks = Clocks(dev)
+    tot_ms, ck = timed(graph_step, a.steps, clocks, "timed_graph")
+    tot_ms = allreduce(tot_ms, pg.ReduceOp.MAX if pg else None)
+    ms_step = tot_ms / a.steps
+    all_nodes = allreduce(float(nodes), pg.ReduceOp.SUM if pg else None)
+    all_trials = allreduce(float(P), pg.ReduceOp.SUM if pg else None)
+    value = all_nodes * N / (ms_step * 1e-3)
+    trial_rate = all_trials / (ms_step * 1e-3)
+    ds.sync(st)
+
+    # ---- forward kernel alone: live CUDA events around it (roofline) ----
+    def prof_step():
+        ds.eval_batch(op, cv, hs, flags=gg.F_PROFILE, stream=st, out=outs)
+    for _ in range(2):
+        with torch.cuda.stream(st):
+            prof_step()
+    st.synchronize()
+    ds.profile_read()
+    clocks2 = Clocks(dev)
+    eager_ms, ck2 = timed(prof_step, a.steps, clocks2, "timed_eager")
+    fwd_ms, launches = ds.profile_read()
+    fwd_avg = fwd_ms / max(launches, 1)
+    sm_mhz = (ck2 or ck or {}).get("sm_mhz") or 1477.0
+    peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9  # Gop/s
+    peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
+    alg_fp32 = (fp32_ops + ACC_FP32 * valid) * N  # per launch
+    alg_sfu = sfu_ops * N
+    ach_fp32 = alg_fp32 / (fwd_avg * 1e-3) / 1e9
+    ach_sfu = alg_sfu / (fwd_avg * 1e-3) / 1e9
+    x_bytes = (w["F"] + 1) * N * 4
+
+    # ---- plain form: one launch per trial ----
+    def plain_step():
+        ds.eval_plain(op, cv, hs, stream=st, out=outs)
+    with torch.cuda.stream(st):
+        plain_step()
+    st.synchronize()
+    plain_ms, _ = timed(plain_step, a.plain_steps, name="timed_plain")
+    plain_step_ms = allreduce(plain_ms, pg.ReduceOp.MAX if pg else None) / a.plain_steps
+    plain_trials = all_trials / (plain_step_ms * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    hop = torch.from_numpy(w["op"]).pin_memory()
+    hcv = torch.from_numpy(w["cval"]).pin_memory()
+    hhs = torch.from_numpy(w["heights"]).pin_memory() if hs is not None else None
+    hout = [torch.empty(P, dtype=torch.float32).pin_memory(), None, None, None]
+
+    def e2e_step():
+        ds.eval_batch(hop, hcv, hhs, stream=st, out=hout)
+    for _ in range(a.warmup):
+        with torch.cuda.stream(st):
+            e2e_step()
+    st.synchronize()
+    e2e_ms, _ = timed(e2e_step, a.steps, name="timed_e2e")
+    e2e_ms = allreduce(e2e_ms, pg.ReduceOp.MAX if pg else None) / a.steps
+    h2d = w["op"].nbytes + w["cval"].nbytes + (w["heights"].nbytes if hs is not None else 0)
+    ds.sync(st)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "trials_per_step": P, "rows": N,
+                   "features": w["F"], "template_height": w["h_max"],
+                   "active_nodes_per_step": nodes, "flush_l2": "512 MB write between steps",
+                   "form": "persistent batched kernel, CUDA graph replay, autotuned tiles",
+                   "parallelism": f"replicas x{world} (independent FOS steps)"},
+        "trial_evals_per_s": trial_rate,
+        "plain": {"trial_evals_per_s": plain_trials, "ms_per_step": plain_step_ms,
+                  "node_row_evals_per_s": all_nodes * N / (plain_step_ms * 1e-3),
+                  "launches_per_step": 2 * P + 2},
+        "batched_over_plain": trial_rate / plain_trials,
+        "e2e": {"value": all_nodes * N / (e2e_ms * 1e-3), "unit": UNIT,
+                "trial_evals_per_s": all_trials / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(4 * P)},
+        "roofline": {"bound": "alu", "achieved": ach_fp32, "peak": peak_fp32, "unit": "Gop/s",
+                     "frac": ach_fp32 / peak_fp32, "traffic": None,
+                     "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
+                     "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
+                                   "(sampled SM clock)",
+                     "sfu": {"achieved": ach_sfu, "peak": peak_sfu, "frac": ach_sfu / peak_sfu},
+                     "hbm_gbs": x_bytes / (fwd_avg * 1e-3) / 1e9,
+                     "eager_ms_per_step": eager_ms / a.steps},
+        "gpu_launches": 3 * a.steps,
+        "clocks": ck,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, a.cpu_seconds, torch)
+    ds.close()
+    if pg:
+        pg.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

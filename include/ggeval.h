@@ -1,0 +1,241 @@
+/*
+ * ggeval: batched fitness evaluation of GP-GOMEA trial solutions on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The paper ("GP-GOMEA with GPU-Based Fitness Evaluations") restructures
+ * gene-pool optimal mixing so that every offspring changed in one FOS step
+ * is evaluated together (Algorithm 1, the GPU-side Evaluate(O[changed])
+ * call); it linearises each template tree to RPN with introns dropped
+ * (Section 3.2, Fig. 1) and evaluates the batch on the GPU, returning one
+ * fitness per trial to the host (Section 3.2, "Evaluation on the GPU").
+ * This C ABI is that Evaluate call.  Fitness is linearly scaled MSE
+ * (least-squares a, b), with the paper's plain MSE (Eq. 1) returned beside
+ * it; a reverse-mode adjoint gives the gradient of either in every ERC.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a ggeval_status; on failure ggeval_last_error()
+ *    returns a thread-local message.  Argument errors are reported
+ *    synchronously and leave every output untouched.
+ *  - GPU work is enqueued on the caller's CUDA stream (cudaStream_t passed
+ *    as void*; NULL = legacy default stream) and is asynchronous: outputs
+ *    are valid once that stream has reached the call's end.  Call
+ *    ggeval_sync() to wait and to collect device-side errors.
+ *  - Device-side errors (an invalid template in a device-memory batch, a
+ *    bounded wait that gave up) are recorded in a per-dataset status word,
+ *    reported and cleared by ggeval_sync().  An invalid trial gets NaN in
+ *    every output; the other trials are unaffected.
+ *  - A non-finite fitness is a value, not an error: a trial whose output
+ *    is non-finite, or exceeds 2^50 in magnitude, at any row gets +inf
+ *    smse and mse, a = b = 0 and a zero gradient.
+ *  - Buffers passed in are borrowed: the caller owns them and keeps them
+ *    alive until the stream work completes.  The dataset owns its copies
+ *    of X and y and a workspace that grows on demand (the growing call
+ *    allocates with cudaMalloc, so call once with the largest batch before
+ *    capturing the stream in a CUDA graph).
+ *  - A dataset is used from one host thread at a time.
+ */
+#ifndef GGEVAL_H
+#define GGEVAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ggeval_dataset ggeval_dataset;
+
+typedef enum {
+  GGEVAL_OK = 0,
+  GGEVAL_ERR_ARG = -1,         /* bad argument (null pointer, size, range)   */
+  GGEVAL_ERR_TEMPLATE = -2,    /* a trial's template is invalid              */
+  GGEVAL_ERR_CUDA = -3,        /* a CUDA runtime call failed                 */
+  GGEVAL_ERR_OOM = -4,         /* device allocation failed                   */
+  GGEVAL_ERR_TIMEOUT = -5,     /* a bounded device wait gave up              */
+  GGEVAL_ERR_CHECKED = -6,     /* bounds check failed (checked build only)   */
+  GGEVAL_ERR_UNSUPPORTED = -7  /* size beyond what this build supports       */
+} ggeval_status;
+
+/* Template layouts.  A trial of height h has 2^(h+1)-1 nodes of arity 2.
+ * HEAP: node i has children 2i+1 and 2i+2.  PREFIX: pre-order of the full
+ * template, so a node at position p whose subtree has height s has children
+ * p+1 and p+2^s.  (Section 3.1: an individual is a fixed-length string of
+ * variables mapped onto a fixed tree template.) */
+enum { GGEVAL_LAYOUT_HEAP = 0, GGEVAL_LAYOUT_PREFIX = 1 };
+
+/* Where a batch's arrays live.  HOST batches are copied to the device by
+ * the call (inside the stream work); their outputs are host memory written
+ * by a device-to-host copy on the stream.  Use pinned host memory for
+ * asynchronous copies. */
+enum { GGEVAL_MEM_DEVICE = 0, GGEVAL_MEM_HOST = 1 };
+
+/* Template node opcodes (one uint8 per node).
+ * Functions: binary operands are (left child, right child); a unary
+ * function reads its left child and its right subtree is an intron.
+ * AQ(a, b) = a / sqrt(1 + b^2) (analytic quotient).  DIV, SQUARE, LOG and
+ * SQRT are the paper's Table 2 operators (plain division, x^2, unprotected
+ * log and sqrt).  Terminals: ERC reads the node's constant from cval;
+ * FEATURE0 + k reads feature k (k < n_features).  The root is active; the
+ * children of an active function are active (only the left child of a
+ * unary one); a terminal's subtree is an intron.  Introns may hold any
+ * byte; an active node must be one of the codes below, and an active
+ * function must not sit at a leaf position (Fig. 1 shows a multiplication
+ * at a leaf as an intron). */
+enum {
+  GGEVAL_OP_ADD = 0, GGEVAL_OP_SUB = 1, GGEVAL_OP_MUL = 2, GGEVAL_OP_AQ = 3,
+  GGEVAL_OP_SIN = 4, GGEVAL_OP_COS = 5, GGEVAL_OP_EXP = 6,
+  GGEVAL_OP_LOG_ABS = 7, GGEVAL_OP_SQRT_ABS = 8,
+  GGEVAL_OP_DIV = 9, GGEVAL_OP_SQUARE = 10, GGEVAL_OP_LOG = 11, GGEVAL_OP_SQRT = 12,
+  GGEVAL_OP_ERC = 31,
+  GGEVAL_OP_FEATURE0 = 32,
+  GGEVAL_OP_PAD = 255
+};
+
+/* Largest template height this build evaluates (511 nodes, the paper's
+ * depth-8 templates of Table 2) and the largest feature count. */
+#define GGEVAL_MAX_HEIGHT 8
+#define GGEVAL_MAX_FEATURES 223
+
+/* One FOS step's trials (the batch O[changed] of Algorithm 1).
+ * op and cval are [n][stride] row-major with stride = 2^(max_height+1)-1;
+ * trial p of height h_p uses its first 2^(h_p+1)-1 entries.  height is
+ * int8 [n] (each 0..max_height) or NULL for "all max_height".  All three
+ * live in `memory`. */
+typedef struct {
+  int32_t n;           /* number of trials, >= 0                          */
+  int32_t max_height;  /* 0..GGEVAL_MAX_HEIGHT                            */
+  int32_t layout;      /* GGEVAL_LAYOUT_*                                 */
+  int32_t memory;      /* GGEVAL_MEM_*                                    */
+  const uint8_t* op;
+  const float* cval;
+  const int8_t* height;
+} ggeval_batch;
+
+/* Flags for the evaluation calls. */
+enum {
+  GGEVAL_F_GRAPH = 1u << 0,   /* replay (or capture once) the call's launch
+                                 sequence as a CUDA graph, keyed on every
+                                 argument value; needs a device batch      */
+  GGEVAL_F_EXACT = 1u << 1,   /* per-row error-free FP32 sums (slower); the
+                                 default picks them for small row counts   */
+  GGEVAL_F_GRAD_MSE = 1u << 2,/* ggeval_grad_batch: gradient of plain MSE
+                                 instead of scaled MSE                     */
+  GGEVAL_F_PROFILE = 1u << 3  /* record CUDA events around the batched
+                                 forward kernel (not with GGEVAL_F_GRAPH);
+                                 read them with ggeval_profile_read        */
+};
+
+/* Create a dataset from X (n_rows x n_features, float32, row-major when
+ * x_row_major != 0, else feature-major) and the target y (n_rows float32).
+ * X and y may be host or device pointers (unified addressing decides); they
+ * are copied, so the caller may free them when the call returns (the call
+ * synchronises `stream`).  Section 3.2 evaluates every trial over every
+ * dataset row; the dataset is stored once, feature-major, and reused by
+ * every batch.  y must be finite with |y| <= 2^50.
+ * Errors: ERR_ARG (null, n_rows < 1, n_features outside 1..223, bad y),
+ * ERR_CUDA / ERR_OOM. */
+ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_rows,
+                                    int32_t n_features, int32_t x_row_major,
+                                    int32_t device, void* stream,
+                                    ggeval_dataset** out);
+
+/* Release a dataset and its workspace (synchronises its device).  NULL is
+ * a no-op. */
+void ggeval_destroy(ggeval_dataset* ds);
+
+/* Evaluate every trial of the batch over all dataset rows: the batched
+ * Evaluate(O[changed]) of Algorithm 1.  Outputs are float [n] in the
+ * batch's memory; any of a, b, mse may be NULL.
+ *   smse = min_{a,b} (1/N) sum_i (y_i - a - b f_i)^2, a, b the minimisers
+ *   mse  = (1/N) sum_i (f_i - y_i)^2                   (Eq. 1)
+ * with f_i the trial's active expression at row i (introns are skipped).
+ * A trial whose f has population variance <= 1e-12 mean(f)^2 counts as
+ * constant: b = 0, a = mean(y), smse = Var(y).
+ * Errors: ERR_ARG, ERR_UNSUPPORTED (max_height > 8), ERR_CUDA, ERR_OOM;
+ * template errors come back through ggeval_sync(). */
+ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* batch,
+                                uint32_t flags, float* smse, float* a, float* b,
+                                float* mse, void* stream);
+
+/* Per-row values f_i of every trial (float [n][n_rows], batch memory), the
+ * quantity each "sub-evaluation" of Section 3.2 squares.  For checking and
+ * for building targets; not the fast path. */
+ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* batch,
+                               float* f, void* stream);
+
+/* The same fitness as ggeval_eval_batch computed the plain way: one launch
+ * of the row-parallel kernel per trial followed by a second-stage
+ * reduction launch (the multi-block-per-individual design of Fig. 2,
+ * right).  Device batches only.  For comparison with the batched form. */
+ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* batch,
+                                uint32_t flags, float* smse, float* a, float* b,
+                                float* mse, void* stream);
+
+/* Fitness and its gradient with respect to every ERC constant:
+ * dcval is float [n][stride] in the batch's memory, d smse / d cval (or
+ * d mse / d cval with GGEVAL_F_GRAD_MSE), 0 at every non-ERC or intron
+ * position.  Uses the envelope theorem for a, b:
+ *   d smse/d c = (2b/N) sum_i (a + b f_i - y_i) d f_i/d c.
+ * Node values are recomputed per row on chip, never stored in HBM.
+ * smse may be NULL.  Errors as ggeval_eval_batch. */
+ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* batch,
+                                uint32_t flags, float* smse, float* dcval,
+                                void* stream);
+
+/* One Adam step on the ERC constants of a device batch, in place:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * c -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps), for every
+ * position whose op is ERC.  cval, grad, m, v: float [n][stride] device;
+ * t >= 1 is the step number. */
+ggeval_status ggeval_adam_step(const ggeval_batch* batch, float* cval, const float* grad,
+                               float* m, float* v, int32_t t, float lr, float beta1,
+                               float beta2, float eps, void* stream);
+
+/* Time candidate tile shapes (rows per tile, trials per work item, rows per
+ * lane) on this batch and keep the fastest for batches of the same shape
+ * (n, max_height, layout, flags).  Synchronises the stream; runs the
+ * evaluation several times.  Device batches only. */
+ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* batch,
+                              uint32_t flags, void* stream);
+
+/* Wait for the dataset's work on `stream`, then report and clear the
+ * device-side status: GGEVAL_OK, ERR_TEMPLATE, ERR_TIMEOUT or ERR_CHECKED. */
+ggeval_status ggeval_sync(ggeval_dataset* ds, void* stream);
+
+/* Sum of the batched forward kernel's durations (ms, from CUDA events on
+ * the launching stream) and the number of launches timed since the last
+ * read, for calls made with GGEVAL_F_PROFILE; waits for those events and
+ * resets the sums.  At most 4096 launches are kept between reads. */
+ggeval_status ggeval_profile_read(ggeval_dataset* ds, double* fwd_ms, int64_t* launches);
+
+/* Thread-local message for the last non-OK status (never NULL). */
+const char* ggeval_last_error(void);
+
+/* Statistics of a batch for throughput accounting: for each trial, counts
+ * of active nodes by class.  out is int64 [n][GGEVAL_NSTAT] host memory:
+ * [0] active nodes, [1] terminals, [2] +/-/x, [3] AQ, [4] DIV,
+ * [5] sin/cos, [6] exp, [7] log, [8] sqrt, [9] square; [10] interpreter
+ * instructions after fusion; [11] stack slots used.  An invalid trial has
+ * -1 in [0].  Host batches only; runs on the CPU, no dataset needed. */
+#define GGEVAL_NSTAT 12
+ggeval_status ggeval_batch_stats(const ggeval_batch* batch, int32_t n_features,
+                                 int64_t* out);
+
+/* The packer on the CPU, for inspection and tests: linearises trial `index`
+ * of a host batch into the interpreter's instruction words (post-order of
+ * the active nodes, Section 3.2, with operands of a binary node reordered
+ * so the subtree needing more stack goes first).  words: uint32 [cap]
+ * opcode | feature << 8; consts: float [cap]; tpos: int32 [cap], template
+ * position of each instruction's main node.  Returns the instruction count
+ * in *len (ERR_TEMPLATE for an invalid trial). */
+ggeval_status ggeval_pack_host(const ggeval_batch* batch, int32_t index, int32_t n_features,
+                               uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
+                               int32_t* len);
+
+/* Library version string. */
+const char* ggeval_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GGEVAL_H */

@@ -14,7 +14,8 @@ __all__ = [
     "ADD", "SUB", "MUL", "AQ", "SIN", "COS", "EXP", "LOG_ABS", "SQRT_ABS", "DIV",
     "SQUARE", "LOG", "SQRT", "ERC", "FEAT0", "PAD", "BINARY", "UNARY", "BIG",
     "VAR_TOL", "InvalidTemplate", "Template", "active_mask", "rpn", "paper_encoding",
-    "eval_tree", "eval_tree_f32", "fitness", "grad", "fd_grad", "eval_batch",
+    "eval_tree", "eval_tree_f32", "eval_tree_perturbed", "fitness", "grad", "fd_grad",
+    "eval_batch",
 ]
 
 # Template opcodes: the library's documented interface values.
@@ -184,7 +185,7 @@ def _apply(o, a, b=None, xp=np):
     raise InvalidTemplate(o)
 
 
-def _eval(t: Template, X: np.ndarray, dtype, store=None) -> np.ndarray:
+def _eval(t: Template, X: np.ndarray, dtype, store=None, perturb=None) -> np.ndarray:
     n = X.shape[0]
 
     def visit(pos, depth):
@@ -199,6 +200,9 @@ def _eval(t: Template, X: np.ndarray, dtype, store=None) -> np.ndarray:
         else:
             l, _ = t.children(pos, depth)
             v = _apply(o, visit(l, depth + 1))
+        if perturb is not None and o < ERC:
+            rel, rng = perturb
+            v = v * (1.0 + rel * rng.choice(np.array([-1.0, 1.0]), n))
         if store is not None:
             store[pos] = v
         return v
@@ -217,6 +221,16 @@ def eval_tree_f32(t: Template, X: np.ndarray) -> np.ndarray:
     """The same recursion with every node value rounded to float32 and
     float32 library functions.  Used only to flag ill-conditioned rows."""
     return _eval(t, np.asarray(X, dtype=np.float32), np.float32)
+
+
+def eval_tree_perturbed(t: Template, X: np.ndarray, rel: float, rng) -> np.ndarray:
+    """FP64 evaluation with the value of every function node multiplied by
+    (1 + rel * s), s = +1 or -1 at random per row: a first-order probe of
+    how far rounding errors of relative size ``rel`` at each node can move
+    the result.  Tests use it (with rel a few FP32 units in the last place)
+    to tell rows and trials whose FP32 value is ill-conditioned, the effect
+    Section 5 of the paper notes for redundant subexpressions."""
+    return _eval(t, np.asarray(X), np.float64, perturb=(rel, rng))
 
 
 def _overflowed(f: np.ndarray) -> bool:

@@ -1,0 +1,9 @@
+"""ggeval: batched GP-GOMEA fitness evaluation on NVIDIA GB300 (sm_103a).
+
+The compute path is the CUDA library built from ``csrc/`` (see
+``include/ggeval.h``); :mod:`.ggeval` is its Python binding.
+"""
+from .ggeval import (  # noqa: F401
+    F_EXACT, F_GRAD_MSE, F_GRAPH, F_PROFILE, LAYOUT_HEAP, LAYOUT_PREFIX, Dataset, GGEvalError, ScaledMSE,
+    adam_step, batch_stats, lib, make_batch, pack_host)
+from .build import build  # noqa: F401

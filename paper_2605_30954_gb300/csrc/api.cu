@@ -1,0 +1,901 @@
+// Host side of the C ABI (include/ggeval.h): datasets, workspace, launch
+// planning, CUDA-graph replay, the autotuner and argument validation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ggeval.h"
+#include "misc.cuh"
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+ggeval_status fail(ggeval_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define GG_CU(call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? GGEVAL_ERR_OOM : GGEVAL_ERR_CUDA,        \
+                  "%s: %s", #call, cudaGetErrorString(e_));                                  \
+  } while (0)
+
+#define GG_TRY(expr)                  \
+  do {                                        \
+    ggeval_status s_ = (expr);                \
+    if (s_ != GGEVAL_OK) return s_;           \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline int stride_of(int h) { return (1 << (h + 1)) - 1; }
+inline int dmax_of(int h) { return h <= 4 ? 3 : (h <= 6 ? 5 : 7); }
+inline int lstride_of(int h) { return stride_of(h) + 1; }
+
+const void* fwd_ptr(int dmax, int variant) {
+  switch (dmax) {
+    case 3: return gg::fwd_ptr_d3(variant);
+    case 5: return gg::fwd_ptr_d5(variant);
+    default: return gg::fwd_ptr_d7(variant);
+  }
+}
+
+// Raise the dynamic shared-memory limit of a kernel once per device.
+ggeval_status prepare_kernel(int device, const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({device, fn})) return GGEVAL_OK;
+  int optin = 0;
+  GG_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  GG_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  done.insert({device, fn});
+  return GGEVAL_OK;
+}
+
+struct Cfg {
+  int variant = 0, tile_rows = 0, group = 0, warps = 0;
+  bool operator==(const Cfg& o) const {
+    return variant == o.variant && tile_rows == o.tile_rows && group == o.group &&
+           warps == o.warps;
+  }
+};
+
+struct Plan {
+  Cfg cfg;
+  int dmax = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
+  size_t smem = 0;
+  const void* fn = nullptr;
+};
+
+struct GraphKey {
+  ggeval_batch b;
+  uint32_t flags;
+  const void* out[4];
+  const void* ws[7];  // workspace buffers the captured launches point at
+  Cfg cfg;
+  int kind;
+};
+
+bool same_key(const GraphKey& x, const GraphKey& y) {
+  return std::memcmp(&x.b, &y.b, sizeof x.b) == 0 && x.flags == y.flags &&
+         std::memcmp(x.out, y.out, sizeof x.out) == 0 && std::memcmp(x.ws, y.ws, sizeof x.ws) == 0 &&
+         x.cfg == y.cfg && x.kind == y.kind;
+}
+
+}  // namespace
+
+struct ggeval_dataset {
+  int device = 0, sms = 0;
+  int64_t N = 0;
+  int F = 0, ldx = 0;
+  size_t smem_optin = 0;
+  float* X = nullptr;        // [F + 1][ldx], row F = y - mean(y)
+  double* pref = nullptr;    // [N + 1] prefix sums of the stored centred target
+  double ybar = 0, syc = 0, sycyc = 0;
+  cudaStream_t cap_stream = nullptr;
+  // workspace (grown on demand)
+  uint2* prog = nullptr;
+  size_t cap_prog = 0;
+  gg::Aux* aux = nullptr;
+  size_t cap_aux = 0;
+  int* len = nullptr;
+  size_t cap_len = 0;
+  double* part = nullptr;
+  size_t cap_part = 0;
+  double* ab = nullptr;
+  size_t cap_ab = 0;
+  double* gacc = nullptr;
+  size_t cap_gacc = 0;
+  int* counters = nullptr;
+  size_t cap_counters = 0;
+  unsigned* status = nullptr;
+  // device staging of host-memory batches
+  unsigned char* stage = nullptr;
+  size_t cap_stage = 0;
+  std::map<std::tuple<int, int, int, int>, Cfg> tuned;
+  GraphKey gkey{};
+  cudaGraphExec_t gexec = nullptr;
+  // GGEVAL_F_PROFILE: event pairs around the batched forward kernel
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  size_t prof_used = 0;
+};
+
+namespace {
+
+template <class T>
+ggeval_status grow(T*& p, size_t& cap, size_t need) {
+  if (need <= cap) return GGEVAL_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  size_t n = need + need / 4 + 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), n * sizeof(T));
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return fail(GGEVAL_ERR_OOM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  cap = n;
+  return GGEVAL_OK;
+}
+
+ggeval_status check_batch(const ggeval_dataset* ds, const ggeval_batch* b) {
+  if (!ds) return fail(GGEVAL_ERR_ARG, "dataset is NULL");
+  if (!b) return fail(GGEVAL_ERR_ARG, "batch is NULL");
+  if (b->n < 0) return fail(GGEVAL_ERR_ARG, "batch n = %d < 0", b->n);
+  if (b->max_height < 0) return fail(GGEVAL_ERR_ARG, "max_height %d < 0", b->max_height);
+  if (b->max_height > GGEVAL_MAX_HEIGHT)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "max_height %d > %d", b->max_height, GGEVAL_MAX_HEIGHT);
+  if (b->layout != GGEVAL_LAYOUT_HEAP && b->layout != GGEVAL_LAYOUT_PREFIX)
+    return fail(GGEVAL_ERR_ARG, "unknown layout %d", b->layout);
+  if (b->memory != GGEVAL_MEM_DEVICE && b->memory != GGEVAL_MEM_HOST)
+    return fail(GGEVAL_ERR_ARG, "unknown memory kind %d", b->memory);
+  if (b->n > 0 && (!b->op || !b->cval)) return fail(GGEVAL_ERR_ARG, "op or cval is NULL");
+  if ((int64_t)b->n * stride_of(b->max_height) > (int64_t)1 << 31)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "batch of %d trials too large", b->n);
+  return GGEVAL_OK;
+}
+
+// Default tile shape: enough work items for every SM several times over, X
+// tiles as large as the work allows (each tile is reused by `group` trials).
+Cfg default_cfg(const ggeval_dataset* ds, int n, int h_max, uint32_t flags) {
+  Cfg c;
+  const bool exact = (flags & GGEVAL_F_EXACT) || ds->N < 32768;
+  c.variant = exact ? 2 : 0;
+  c.warps = 8;
+  const int rpp = 32 * gg::variant_rows(c.variant);
+  const int lst = lstride_of(h_max);
+  int max_tile = exact ? 2048 : 2048;
+  while (max_tile > rpp &&
+         gg::fwd_smem_bytes(ds->F, max_tile, c.warps, lst) > ds->smem_optin / 2)
+    max_tile /= 2;
+  const double target = 16.0 * ds->sms * 2;
+  double want = (double)ds->N * n / ((double)c.warps * target);
+  int tile = rpp;
+  while (tile < max_tile && tile < want && tile < ds->N) tile *= 2;
+  c.tile_rows = tile;
+  const int n_tiles = (int)((ds->N + tile - 1) / tile);
+  long long n_groups = (long long)std::ceil(target / n_tiles);
+  const long long max_groups = (n + c.warps - 1) / c.warps;
+  if (n_groups > max_groups) n_groups = max_groups;
+  if (n_groups < 1) n_groups = 1;
+  c.group = (int)((n + n_groups - 1) / n_groups);
+  if (c.group < 1) c.group = 1;
+  return c;
+}
+
+ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Plan* pl) {
+  pl->cfg = cfg;
+  pl->dmax = dmax_of(h_max);
+  pl->stride = stride_of(h_max);
+  pl->lstride = lstride_of(h_max);
+  pl->fn = fwd_ptr(pl->dmax, cfg.variant);
+  if (!pl->fn) return fail(GGEVAL_ERR_ARG, "no kernel for variant %d", cfg.variant);
+  const int rpp = 32 * gg::variant_rows(cfg.variant);
+  if (cfg.tile_rows < rpp || cfg.tile_rows % rpp || cfg.group < 1 || cfg.warps < 1 ||
+      cfg.warps > 16)
+    return fail(GGEVAL_ERR_ARG, "bad tile configuration");
+  pl->smem = gg::fwd_smem_bytes(ds->F, cfg.tile_rows, cfg.warps, pl->lstride);
+  if (pl->smem > ds->smem_optin) return fail(GGEVAL_ERR_ARG, "tile needs too much shared memory");
+  pl->n_tiles = (int)((ds->N + cfg.tile_rows - 1) / cfg.tile_rows);
+  const long long n_groups = (n + cfg.group - 1) / cfg.group;
+  if ((long long)pl->n_tiles * n_groups > (1ll << 31) - 1)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "too many work items");
+  pl->n_items = (int)(pl->n_tiles * n_groups);
+  GG_TRY(prepare_kernel(ds->device, pl->fn));
+  int nb = 0;
+  GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pl->fn, cfg.warps * 32, pl->smem));
+  if (nb < 1) return fail(GGEVAL_ERR_ARG, "tile configuration does not fit on an SM");
+  long long grid = (long long)nb * ds->sms;
+  pl->grid = (int)(grid < pl->n_items ? grid : pl->n_items);
+  if (pl->grid < 1) pl->grid = 1;
+  return GGEVAL_OK;
+}
+
+Cfg pick_cfg(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags) {
+  auto it = ds->tuned.find({b->n, b->max_height, b->layout, (int)(flags & GGEVAL_F_EXACT)});
+  if (it != ds->tuned.end()) return it->second;
+  return default_cfg(ds, b->n, b->max_height, flags);
+}
+
+struct DevBatch {
+  const uint8_t* op;
+  const float* cval;
+  const int8_t* height;
+};
+
+// Copy a host batch into the staging area (on the stream) and return the
+// device pointers; `extra` bytes after it are handed back in *scratch.
+ggeval_status stage_batch(ggeval_dataset* ds, const ggeval_batch* b, size_t extra,
+                          cudaStream_t st, DevBatch* db, unsigned char** scratch) {
+  const size_t cnt = (size_t)b->n * stride_of(b->max_height);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_op = 0, o_cv = al(cnt), o_h = o_cv + al(cnt * 4), o_x = o_h + al(b->n);
+  GG_TRY(grow(ds->stage, ds->cap_stage, o_x + extra));
+  if (b->memory == GGEVAL_MEM_HOST) {
+    GG_CU(cudaMemcpyAsync(ds->stage + o_op, b->op, cnt, cudaMemcpyHostToDevice, st));
+    GG_CU(cudaMemcpyAsync(ds->stage + o_cv, b->cval, cnt * 4, cudaMemcpyHostToDevice, st));
+    if (b->height)
+      GG_CU(cudaMemcpyAsync(ds->stage + o_h, b->height, b->n, cudaMemcpyHostToDevice, st));
+    db->op = ds->stage + o_op;
+    db->cval = reinterpret_cast<const float*>(ds->stage + o_cv);
+    db->height = b->height ? reinterpret_cast<const int8_t*>(ds->stage + o_h) : nullptr;
+  } else {
+    db->op = b->op;
+    db->cval = b->cval;
+    db->height = b->height;
+  }
+  if (scratch) *scratch = ds->stage + o_x;
+  return GGEVAL_OK;
+}
+
+ggeval_status ensure_ws(ggeval_dataset* ds, int n, const Plan& pl, bool grad) {
+  GG_TRY(grow(ds->prog, ds->cap_prog, (size_t)n * pl.lstride));
+  GG_TRY(grow(ds->len, ds->cap_len, (size_t)n + 1));
+  GG_TRY(grow(ds->part, ds->cap_part, (size_t)n * pl.n_tiles * gg::NPART));
+  GG_TRY(grow(ds->ab, ds->cap_ab, (size_t)n * 4 + 4));
+  GG_TRY(grow(ds->counters, ds->cap_counters, (size_t)n + 8));
+  if (grad) {
+    GG_TRY(grow(ds->aux, ds->cap_aux, (size_t)n * pl.lstride));
+    GG_TRY(grow(ds->gacc, ds->cap_gacc, (size_t)n * pl.stride));
+  }
+  return GGEVAL_OK;
+}
+
+ggeval_status launch(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     void* params) {
+  void* args[] = {params};
+  GG_CU(cudaLaunchKernel(fn, grid, block, args, smem, st));
+  return GGEVAL_OK;
+}
+
+ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_max, int layout,
+                           const Plan& pl, bool with_aux, cudaStream_t st) {
+  gg::PackParams pp;
+  pp.op = db.op;
+  pp.cval = db.cval;
+  pp.height = db.height;
+  pp.n = n;
+  pp.h_max = h_max;
+  pp.stride = pl.stride;
+  pp.layout = layout;
+  pp.n_features = ds->F;
+  pp.max_slots = pl.dmax;
+  pp.lstride = pl.lstride;
+  pp.prog = ds->prog;
+  pp.aux = with_aux ? ds->aux : nullptr;
+  pp.len = ds->len;
+  pp.status = ds->status;
+  return launch(gg::pack_ptr(), dim3((n + 127) / 128), dim3(128), 0, st, &pp);
+}
+
+gg::FwdParams fwd_params(ggeval_dataset* ds, int n, const Plan& pl) {
+  gg::FwdParams fp;
+  fp.X = ds->X;
+  fp.N = (int)ds->N;
+  fp.F = ds->F;
+  fp.ldx = ds->ldx;
+  fp.prog = ds->prog;
+  fp.len = ds->len;
+  fp.lstride = pl.lstride;
+  fp.P = n;
+  fp.tile_rows = pl.cfg.tile_rows;
+  fp.n_tiles = pl.n_tiles;
+  fp.group = pl.cfg.group;
+  fp.n_items = pl.n_items;
+  fp.part = ds->part;
+  fp.counter = ds->counters;
+  fp.status = ds->status;
+  fp.rows_out = nullptr;
+  return fp;
+}
+
+gg::FinParams fin_params(ggeval_dataset* ds, int n, const Plan& pl, float* smse, float* a,
+                         float* b, float* mse) {
+  gg::FinParams q;
+  q.part = ds->part;
+  q.len = ds->len;
+  q.P = n;
+  q.n_tiles = pl.n_tiles;
+  q.tile_rows = pl.cfg.tile_rows;
+  q.N = ds->N;
+  q.pref = ds->pref;
+  q.ybar = ds->ybar;
+  q.syc = ds->syc;
+  q.sycyc = ds->sycyc;
+  q.smse = smse;
+  q.a = a;
+  q.b = b;
+  q.mse = mse;
+  q.ab = ds->ab;
+  return q;
+}
+
+constexpr size_t PROF_MAX = 4096;
+
+// pack -> zero counter -> batched forward -> finalise
+ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_batch* b,
+                           const Plan& pl, float* smse, float* a, float* bb, float* mse,
+                           bool with_aux, cudaStream_t st, bool profile = false) {
+  const int n = b->n;
+  GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st));
+  GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int), st));
+  gg::FwdParams fp = fwd_params(ds, n, pl);
+  std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+  if (profile && ds->prof_used < PROF_MAX) {
+    if (ds->prof_used == ds->prof_ev.size()) {
+      cudaEvent_t e0, e1;
+      GG_CU(cudaEventCreate(&e0));
+      GG_CU(cudaEventCreate(&e1));
+      ds->prof_ev.push_back({e0, e1});
+    }
+    ev = &ds->prof_ev[ds->prof_used++];
+    GG_CU(cudaEventRecord(ev->first, st));
+  }
+  GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+  if (ev) GG_CU(cudaEventRecord(ev->second, st));
+  gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
+  GG_TRY(launch(gg::fin_ptr(), dim3((n + 127) / 128), dim3(128), 0, st, &q));
+  return GGEVAL_OK;
+}
+
+void drop_graph(ggeval_dataset* ds) {
+  if (ds->gexec) cudaGraphExecDestroy(ds->gexec);
+  ds->gexec = nullptr;
+  std::memset(&ds->gkey, 0, sizeof ds->gkey);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ggeval_last_error(void) { return g_err.c_str(); }
+
+const char* ggeval_version(void) { return "ggeval 0.1 (sm_103a)"; }
+
+ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_rows,
+                                    int32_t n_features, int32_t x_row_major, int32_t device,
+                                    void* stream, ggeval_dataset** out) {
+  if (!out) return fail(GGEVAL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!X || !y) return fail(GGEVAL_ERR_ARG, "X or y is NULL");
+  if (n_rows < 1 || n_rows > (int64_t)1 << 30)
+    return fail(GGEVAL_ERR_ARG, "n_rows = %lld out of range", (long long)n_rows);
+  if (n_features < 1 || n_features > GGEVAL_MAX_FEATURES)
+    return fail(GGEVAL_ERR_ARG, "n_features = %d out of range", n_features);
+  int ndev = 0;
+  GG_CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(GGEVAL_ERR_ARG, "no device %d", device);
+  DeviceGuard guard(device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t N = n_rows;
+  const int F = n_features;
+  // target: centre in FP64, store as float
+  std::vector<float> yh((size_t)N);
+  GG_CU(cudaMemcpy(yh.data(), y, (size_t)N * 4, cudaMemcpyDefault));
+  double sum = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const double v = yh[i];
+    if (!std::isfinite(v) || std::fabs(v) > 1125899906842624.0)
+      return fail(GGEVAL_ERR_ARG, "y[%lld] = %g is not finite or exceeds 2^50", (long long)i, v);
+    sum += v;
+  }
+  auto* ds = new ggeval_dataset();
+  ds->device = device;
+  ds->N = N;
+  ds->F = F;
+  ds->ldx = (int)((N + 3) & ~(int64_t)3);
+  ds->ybar = sum / (double)N;
+  std::vector<double> pref((size_t)N + 1);
+  pref[0] = 0;
+  double s2 = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    yh[i] = (float)((double)yh[i] - ds->ybar);
+    pref[i + 1] = pref[i] + (double)yh[i];
+    s2 += (double)yh[i] * (double)yh[i];
+  }
+  ds->syc = pref[N];
+  ds->sycyc = s2;
+  auto cleanup = [&](ggeval_status s) {
+    ggeval_destroy(ds);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaDeviceGetAttribute(&ds->sms, cudaDevAttrMultiProcessorCount, device)) ||
+      (e = cudaStreamCreateWithFlags(&ds->cap_stream, cudaStreamNonBlocking))) {
+    fail(GGEVAL_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+    return cleanup(GGEVAL_ERR_CUDA);
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  ds->smem_optin = (size_t)optin;
+  const size_t xbytes = (size_t)(F + 1) * ds->ldx * 4;
+  if ((e = cudaMalloc(&ds->X, xbytes)) || (e = cudaMalloc(&ds->pref, ((size_t)N + 1) * 8)) ||
+      (e = cudaMalloc(&ds->status, sizeof(unsigned)))) {
+    fail(GGEVAL_ERR_OOM, "dataset allocation: %s", cudaGetErrorString(e));
+    return cleanup(GGEVAL_ERR_OOM);
+  }
+  float* tmp = nullptr;
+  do {
+    if ((e = cudaMemsetAsync(ds->X, 0, xbytes, st))) break;
+    if ((e = cudaMemsetAsync(ds->status, 0, sizeof(unsigned), st))) break;
+    if (x_row_major) {
+      if ((e = cudaMalloc(&tmp, (size_t)N * F * 4))) break;
+      if ((e = cudaMemcpyAsync(tmp, X, (size_t)N * F * 4, cudaMemcpyDefault, st))) break;
+      gg::TransposeParams tp{tmp, ds->X, (int)N, F, ds->ldx};
+      void* args[] = {&tp};
+      if ((e = cudaLaunchKernel(gg::transpose_ptr(), dim3((unsigned)((N + 31) / 32), (F + 31) / 32),
+                                dim3(32, 8), args, 0, st)))
+        break;
+    } else {
+      if ((e = cudaMemcpy2DAsync(ds->X, (size_t)ds->ldx * 4, X, (size_t)N * 4, (size_t)N * 4, F,
+                                 cudaMemcpyDefault, st)))
+        break;
+    }
+    if ((e = cudaMemcpyAsync(ds->X + (size_t)F * ds->ldx, yh.data(), (size_t)N * 4,
+                             cudaMemcpyHostToDevice, st)))
+      break;
+    if ((e = cudaMemcpyAsync(ds->pref, pref.data(), ((size_t)N + 1) * 8, cudaMemcpyHostToDevice,
+                             st)))
+      break;
+    e = cudaStreamSynchronize(st);
+  } while (0);
+  if (tmp) cudaFree(tmp);
+  if (e) {
+    fail(e == cudaErrorMemoryAllocation ? GGEVAL_ERR_OOM : GGEVAL_ERR_CUDA, "dataset upload: %s",
+         cudaGetErrorString(e));
+    return cleanup(e == cudaErrorMemoryAllocation ? GGEVAL_ERR_OOM : GGEVAL_ERR_CUDA);
+  }
+  *out = ds;
+  return GGEVAL_OK;
+}
+
+void ggeval_destroy(ggeval_dataset* ds) {
+  if (!ds) return;
+  DeviceGuard guard(ds->device);
+  cudaDeviceSynchronize();
+  drop_graph(ds);
+  cudaFree(ds->X);
+  cudaFree(ds->pref);
+  cudaFree(ds->status);
+  cudaFree(ds->prog);
+  cudaFree(ds->aux);
+  cudaFree(ds->len);
+  cudaFree(ds->part);
+  cudaFree(ds->ab);
+  cudaFree(ds->gacc);
+  cudaFree(ds->counters);
+  cudaFree(ds->stage);
+  for (auto& e : ds->prof_ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (ds->cap_stream) cudaStreamDestroy(ds->cap_stream);
+  delete ds;
+}
+
+ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                                float* smse, float* a, float* bb, float* mse, void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return GGEVAL_OK;
+  if (!smse) return fail(GGEVAL_ERR_ARG, "smse is NULL");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan pl;
+  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl));
+  GG_TRY(ensure_ws(ds, b->n, pl, false));
+  const bool host = b->memory == GGEVAL_MEM_HOST;
+  DevBatch db;
+  unsigned char* scratch = nullptr;
+  GG_TRY(stage_batch(ds, b, host ? (size_t)b->n * 16 : 0, st, &db, &scratch));
+  float* outs[4] = {smse, a, bb, mse};
+  float* dev[4] = {smse, a, bb, mse};
+  if (host)
+    for (int i = 0; i < 4; ++i) dev[i] = outs[i] ? reinterpret_cast<float*>(scratch) + (size_t)i * b->n : nullptr;
+
+  if ((flags & GGEVAL_F_GRAPH) && !host) {
+    GraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.b = *b;
+    key.flags = flags;
+    for (int i = 0; i < 4; ++i) key.out[i] = outs[i];
+    const void* ws[7] = {ds->prog, ds->len, ds->part, ds->ab, ds->counters, ds->stage, ds->status};
+    std::memcpy(key.ws, ws, sizeof ws);
+    key.cfg = pl.cfg;
+    key.kind = 1;
+    if (!ds->gexec || !same_key(key, ds->gkey)) {
+      drop_graph(ds);
+      cudaGraph_t g = nullptr;
+      GG_CU(cudaStreamBeginCapture(ds->cap_stream, cudaStreamCaptureModeThreadLocal));
+      ggeval_status s = enqueue_eval(ds, db, b, pl, dev[0], dev[1], dev[2], dev[3], false,
+                                     ds->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(ds->cap_stream, &g);
+      if (s != GGEVAL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return fail(GGEVAL_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ds->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        ds->gexec = nullptr;
+        return fail(GGEVAL_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      }
+      ds->gkey = key;
+    }
+    GG_CU(cudaGraphLaunch(ds->gexec, st));
+    return GGEVAL_OK;
+  }
+  GG_TRY(enqueue_eval(ds, db, b, pl, dev[0], dev[1], dev[2], dev[3], false, st,
+                      (flags & GGEVAL_F_PROFILE) != 0));
+  if (host)
+    for (int i = 0; i < 4; ++i)
+      if (outs[i])
+        GG_CU(cudaMemcpyAsync(outs[i], dev[i], (size_t)b->n * 4, cudaMemcpyDeviceToHost, st));
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* b, float* f,
+                               void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return GGEVAL_OK;
+  if (!f) return fail(GGEVAL_ERR_ARG, "f is NULL");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Cfg c = default_cfg(ds, b->n, b->max_height, GGEVAL_F_EXACT);
+  c.variant = 3;
+  Plan pl;
+  GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl));
+  GG_TRY(ensure_ws(ds, b->n, pl, false));
+  const bool host = b->memory == GGEVAL_MEM_HOST;
+  const size_t fbytes = (size_t)b->n * ds->N * 4;
+  DevBatch db;
+  unsigned char* scratch = nullptr;
+  GG_TRY(stage_batch(ds, b, host ? fbytes : 0, st, &db, &scratch));
+  float* fd = host ? reinterpret_cast<float*>(scratch) : f;
+  GG_TRY(enqueue_pack(ds, db, b->n, b->max_height, b->layout, pl, false, st));
+  GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int), st));
+  gg::FwdParams fp = fwd_params(ds, b->n, pl);
+  fp.rows_out = fd;
+  GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+  if (host) GG_CU(cudaMemcpyAsync(f, fd, fbytes, cudaMemcpyDeviceToHost, st));
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                                float* smse, float* a, float* bb, float* mse, void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return GGEVAL_OK;
+  if (!smse) return fail(GGEVAL_ERR_ARG, "smse is NULL");
+  if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "plain form needs a device batch");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // one trial per launch: tiles only over rows
+  Cfg c = default_cfg(ds, 1, b->max_height, flags);
+  c.group = 1;
+  Plan pl;
+  GG_TRY(make_plan(ds, 1, b->max_height, c, &pl));
+  GG_TRY(ensure_ws(ds, b->n, pl, false));
+  DevBatch db{b->op, b->cval, b->height};
+  GG_TRY(enqueue_pack(ds, db, b->n, b->max_height, b->layout, pl, false, st));
+  GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int) * (size_t)b->n, st));
+  for (int t = 0; t < b->n; ++t) {
+    gg::FwdParams fp = fwd_params(ds, 1, pl);
+    fp.prog = ds->prog + (size_t)t * pl.lstride;
+    fp.len = ds->len + t;
+    fp.part = ds->part + (size_t)t * pl.n_tiles * gg::NPART;
+    fp.counter = ds->counters + t;
+    GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+    gg::FinParams q = fin_params(ds, 1, pl, smse + t, a ? a + t : nullptr, bb ? bb + t : nullptr,
+                                 mse ? mse + t : nullptr);
+    q.part = fp.part;
+    q.len = fp.len;
+    q.ab = nullptr;
+    GG_TRY(launch(gg::fin_ptr(), dim3(1), dim3(32), 0, st, &q));
+  }
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                                float* smse, float* dcval, void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return GGEVAL_OK;
+  if (!dcval) return fail(GGEVAL_ERR_ARG, "dcval is NULL");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan pl;
+  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl));
+  GG_TRY(ensure_ws(ds, b->n, pl, true));
+  const bool host = b->memory == GGEVAL_MEM_HOST;
+  const size_t gcount = (size_t)b->n * pl.stride;
+  DevBatch db;
+  unsigned char* scratch = nullptr;
+  GG_TRY(stage_batch(ds, b, host ? gcount * 4 + (size_t)b->n * 4 : 0, st, &db, &scratch));
+  float* dg = host ? reinterpret_cast<float*>(scratch) : dcval;
+  float* ds_smse = smse ? (host ? dg + gcount : smse) : nullptr;
+  GG_TRY(enqueue_eval(ds, db, b, pl, ds_smse, nullptr, nullptr, nullptr, true, st));
+  // adjoint
+  const void* afn = gg::adj_ptr(pl.dmax);
+  GG_TRY(prepare_kernel(ds->device, afn));
+  int warps = (int)((ds->smem_optin - 64) / ((size_t)pl.lstride * gg::ADJ_WARP_BYTES_PER_INSTR));
+  if (warps > 8) warps = 8;
+  if (warps < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
+  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride);
+  int nb = 0;
+  GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, afn, warps * 32, asmem));
+  if (nb < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "adjoint does not fit on an SM");
+  const long long slots = (long long)nb * ds->sms * warps;
+  long long n_chunks = (8 * slots + b->n - 1) / b->n;
+  const long long max_chunks = (ds->N + 31) / 32;
+  if (n_chunks > max_chunks) n_chunks = max_chunks;
+  if (n_chunks < 1) n_chunks = 1;
+  int chunk_rows = (int)(((ds->N + n_chunks - 1) / n_chunks + 31) / 32 * 32);
+  n_chunks = (ds->N + chunk_rows - 1) / chunk_rows;
+  gg::AdjParams ap;
+  ap.X = ds->X;
+  ap.N = (int)ds->N;
+  ap.F = ds->F;
+  ap.ldx = ds->ldx;
+  ap.prog = ds->prog;
+  ap.aux = ds->aux;
+  ap.len = ds->len;
+  ap.lstride = pl.lstride;
+  ap.P = b->n;
+  ap.stride = pl.stride;
+  ap.ab = ds->ab;
+  ap.mse_mode = (flags & GGEVAL_F_GRAD_MSE) ? 1 : 0;
+  ap.ybar = ds->ybar;
+  ap.chunk_rows = chunk_rows;
+  ap.n_chunks = (int)n_chunks;
+  if ((long long)b->n * n_chunks > (1ll << 31) - 1) return fail(GGEVAL_ERR_UNSUPPORTED, "too many items");
+  ap.n_items = (int)(b->n * n_chunks);
+  ap.counter = ds->counters + 1;
+  ap.gacc = ds->gacc;
+  GG_CU(cudaMemsetAsync(ds->counters + 1, 0, sizeof(int), st));
+  GG_CU(cudaMemsetAsync(ds->gacc, 0, gcount * 8, st));
+  long long agrid = (long long)nb * ds->sms;
+  const long long need_blocks = (ap.n_items + warps - 1) / warps;
+  if (agrid > need_blocks) agrid = need_blocks;
+  GG_TRY(launch(afn, dim3((unsigned)agrid), dim3(warps * 32), asmem, st, &ap));
+  gg::GradOutParams gp{ds->gacc, ds->len, b->n, pl.stride, dg};
+  GG_TRY(launch(gg::gradout_ptr(), dim3((unsigned)((gcount + 255) / 256)), dim3(256), 0, st, &gp));
+  if (host) {
+    GG_CU(cudaMemcpyAsync(dcval, dg, gcount * 4, cudaMemcpyDeviceToHost, st));
+    if (smse) GG_CU(cudaMemcpyAsync(smse, ds_smse, (size_t)b->n * 4, cudaMemcpyDeviceToHost, st));
+  }
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_adam_step(const ggeval_batch* b, float* cval, const float* grad, float* m,
+                               float* v, int32_t t, float lr, float beta1, float beta2, float eps,
+                               void* stream) {
+  if (!b || !cval || !grad || !m || !v) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "adam needs device memory");
+  if (b->max_height < 0 || b->max_height > GGEVAL_MAX_HEIGHT || b->n < 0 || t < 1)
+    return fail(GGEVAL_ERR_ARG, "bad batch or step");
+  if (b->n == 0) return GGEVAL_OK;
+  gg::AdamParams p;
+  p.op = b->op;
+  p.cval = cval;
+  p.grad = grad;
+  p.m = m;
+  p.v = v;
+  p.count = (long long)b->n * stride_of(b->max_height);
+  p.lr = lr;
+  p.b1 = beta1;
+  p.b2 = beta2;
+  p.eps = eps;
+  p.c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)t)));
+  p.c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)t)));
+  return launch(gg::adam_ptr(), dim3((unsigned)((p.count + 255) / 256)), dim3(256), 0,
+                static_cast<cudaStream_t>(stream), &p);
+}
+
+ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                              void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return GGEVAL_OK;
+  if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "autotune needs a device batch");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Cfg base = default_cfg(ds, b->n, b->max_height, flags);
+  std::vector<int> variants;
+  if (base.variant == 2) variants = {2};
+  else variants = {0, 1};
+  std::vector<Cfg> cands;
+  for (int v : variants)
+    for (int warps : {8, 16})
+      for (int tmul : {1, 2, 4, 8, 16, 32})
+        for (int gdiv : {1, 2, 4}) {
+          Cfg c;
+          c.variant = v;
+          c.warps = warps;
+          c.tile_rows = 32 * gg::variant_rows(v) * tmul;
+          if (c.tile_rows > 2 * ds->N + 256) continue;
+          const int n_tiles = (int)((ds->N + c.tile_rows - 1) / c.tile_rows);
+          const double target = 32.0 * ds->sms;
+          long long ng = (long long)std::ceil(target * gdiv / n_tiles);
+          if (ng < 1) ng = 1;
+          if (ng > b->n) ng = b->n;
+          c.group = (int)((b->n + ng - 1) / ng);
+          cands.push_back(c);
+        }
+  cands.push_back(base);
+  float* out = nullptr;
+  GG_CU(cudaMalloc(&out, (size_t)b->n * 4));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  DevBatch db{b->op, b->cval, b->height};
+  float best_ms = 1e30f;
+  Cfg best = base;
+  ggeval_status result = GGEVAL_OK;
+  for (const Cfg& c : cands) {
+    Plan pl;
+    if (make_plan(ds, b->n, b->max_height, c, &pl) != GGEVAL_OK) continue;
+    if ((result = ensure_ws(ds, b->n, pl, false)) != GGEVAL_OK) break;
+    if ((result = enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st)) !=
+        GGEVAL_OK)
+      break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r) enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      result = fail(GGEVAL_ERR_CUDA, "autotune run failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (result != GGEVAL_OK) return result;
+  ds->tuned[{b->n, b->max_height, b->layout, (int)(flags & GGEVAL_F_EXACT)}] = best;
+  drop_graph(ds);
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_sync(ggeval_dataset* ds, void* stream) {
+  if (!ds) return fail(GGEVAL_ERR_ARG, "dataset is NULL");
+  DeviceGuard guard(ds->device);
+  GG_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  GG_CU(cudaStreamSynchronize(ds->cap_stream));
+  unsigned s = 0;
+  GG_CU(cudaMemcpy(&s, ds->status, sizeof s, cudaMemcpyDeviceToHost));
+  if (!s) return GGEVAL_OK;
+  GG_CU(cudaMemset(ds->status, 0, sizeof(unsigned)));
+  if (s & gg::ST_TIMEOUT) return fail(GGEVAL_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (s & gg::ST_CHECKED) return fail(GGEVAL_ERR_CHECKED, "a device bounds check failed");
+  return fail(GGEVAL_ERR_TEMPLATE, "a trial's template is invalid (its outputs are NaN)");
+}
+
+ggeval_status ggeval_profile_read(ggeval_dataset* ds, double* fwd_ms, int64_t* launches) {
+  if (!ds || !fwd_ms || !launches) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  DeviceGuard guard(ds->device);
+  double tot = 0;
+  for (size_t i = 0; i < ds->prof_used; ++i) {
+    GG_CU(cudaEventSynchronize(ds->prof_ev[i].second));
+    float ms = 0;
+    GG_CU(cudaEventElapsedTime(&ms, ds->prof_ev[i].first, ds->prof_ev[i].second));
+    tot += ms;
+  }
+  *fwd_ms = tot;
+  *launches = (int64_t)ds->prof_used;
+  ds->prof_used = 0;
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int64_t* out) {
+  if (!b || !out) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  if (b->memory != GGEVAL_MEM_HOST) return fail(GGEVAL_ERR_ARG, "batch_stats needs a host batch");
+  if (b->n < 0 || b->max_height < 0 || b->max_height > GGEVAL_MAX_HEIGHT)
+    return fail(GGEVAL_ERR_ARG, "bad batch");
+  if (b->n > 0 && (!b->op || !b->cval)) return fail(GGEVAL_ERR_ARG, "op or cval is NULL");
+  const int stride = stride_of(b->max_height);
+  std::vector<uint32_t> w(stride + 1);
+  std::vector<float> c(stride + 1);
+  for (int t = 0; t < b->n; ++t) {
+    const int h = b->height ? b->height[t] : b->max_height;
+    int64_t* o = out + (size_t)t * GGEVAL_NSTAT;
+    for (int i = 0; i < GGEVAL_NSTAT; ++i) o[i] = 0;
+    if (h < 0 || h > b->max_height) {
+      o[0] = -1;
+      continue;
+    }
+    const gg::PackResult r =
+        gg::pack_tree(b->op + (size_t)t * stride, b->cval + (size_t)t * stride, h, b->layout,
+                      n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, nullptr, stride);
+    if (r.status) {
+      o[0] = -1;
+      continue;
+    }
+    for (int i = 0; i < 10; ++i) o[i] = r.counts[i];
+    o[10] = r.len;
+    o[11] = r.slots;
+  }
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_pack_host(const ggeval_batch* b, int32_t index, int32_t n_features,
+                               uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
+                               int32_t* len) {
+  if (!b || !words || !consts || !len) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  if (b->memory != GGEVAL_MEM_HOST) return fail(GGEVAL_ERR_ARG, "pack_host needs a host batch");
+  if (index < 0 || index >= b->n) return fail(GGEVAL_ERR_ARG, "index out of range");
+  if (b->max_height < 0 || b->max_height > GGEVAL_MAX_HEIGHT)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "max_height out of range");
+  const int stride = stride_of(b->max_height);
+  if (cap < stride) return fail(GGEVAL_ERR_ARG, "cap %d < %d", cap, stride);
+  const int h = b->height ? b->height[index] : b->max_height;
+  if (h < 0 || h > b->max_height) return fail(GGEVAL_ERR_TEMPLATE, "height out of range");
+  std::vector<uint32_t> w(stride + 1);
+  std::vector<float> c(stride + 1);
+  std::vector<gg::Aux> ax(stride + 1);
+  const gg::PackResult r =
+      gg::pack_tree(b->op + (size_t)index * stride, b->cval + (size_t)index * stride, h, b->layout,
+                    n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, ax.data(), stride);
+  if (r.status) return fail(GGEVAL_ERR_TEMPLATE, "trial %d: invalid template", index);
+  for (int k = 0; k < r.len; ++k) {
+    words[k] = w[k];
+    consts[k] = c[k];
+    if (tpos) tpos[k] = ax[k].tpos;
+  }
+  *len = r.len;
+  return GGEVAL_OK;
+}
+
+}  // extern "C"

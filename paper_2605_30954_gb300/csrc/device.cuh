@@ -1,0 +1,290 @@
+// Device-side building blocks shared by the kernels: the register-file
+// interpreter, error-free FP32 summation, and the mbarrier / bulk-copy PTX.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "isa.h"
+
+namespace gg {
+
+// ------------------------------------------------------------- status word
+enum : unsigned { ST_TEMPLATE = 1u, ST_TIMEOUT = 2u, ST_CHECKED = 4u };
+
+// Magnitude above which a trial's output makes its fitness +inf (2^50).
+constexpr float OUT_BIG = 1125899906842624.0f;
+
+// ------------------------------------------------------------ the operators
+// AQ(a, b) = a / sqrt(1 + b^2): one FMA, one reciprocal square root (SFU),
+// one multiply.  Division is IEEE (no fast-math).
+template <int K>
+__device__ __forceinline__ float binop(float a, float b) {
+  if constexpr (K == K_ADD) return a + b;
+  if constexpr (K == K_SUB) return a - b;
+  if constexpr (K == K_MUL) return a * b;
+  if constexpr (K == K_AQ) return a * rsqrtf(fmaf(b, b, 1.0f));
+  if constexpr (K == K_DIV) return a / b;
+  return 0.f;
+}
+
+template <int U>
+__device__ __forceinline__ float unop(float a) {
+  if constexpr (U == U_SIN) return sinf(a);
+  if constexpr (U == U_COS) return cosf(a);
+  if constexpr (U == U_EXP) return expf(a);
+  if constexpr (U == U_LOG_ABS) return logf(fabsf(a));
+  if constexpr (U == U_SQRT_ABS) return sqrtf(fabsf(a));
+  if constexpr (U == U_SQUARE) return a * a;
+  if constexpr (U == U_LOG) return logf(a);
+  if constexpr (U == U_SQRT) return sqrtf(a);
+  return 0.f;
+}
+
+// ------------------------------------------------------------ interpreter
+// Load R consecutive rows of one feature row of the shared-memory tile.
+template <int R>
+__device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v)[R]) {
+  static_assert(R == 1 || R % 4 == 0, "R must be 1 or a multiple of 4");
+  if constexpr (R == 1) {
+    v[0] = *p;
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < R / 4; ++q) {
+    const float4 t = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q + 0] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
+// Run one packed program on R rows per lane.  `prog` is the warp's copy of
+// the program in shared memory (word, const bits) with a NOP at [L];
+// `xs` points at row r0 of feature 0 of the tile, features `ts` floats
+// apart.  Every lane of the warp executes the same instruction sequence, so
+// the switch below is warp-uniform (Section 3.2: all threads interpret the
+// same individual, avoiding divergence).  The slot operand of each
+// instruction is part of its opcode, so S[] is indexed with constants and
+// stays in registers.
+// S is the caller's slot file (kept in registers across calls); the first
+// instruction of every program is a push into A.
+// With TAPE (R == 1 only) the value of A after instruction k is stored at
+// tape[32 k] (the caller offsets `tape` by its lane): the forward half of
+// the adjoint.
+template <int DMAX, int R, bool TAPE = false>
+__device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
+                                            const float* __restrict__ xs, int ts,
+                                            float (&A)[R], float (&S)[DMAX][R],
+                                            float* __restrict__ tape = nullptr) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) A[r] = 0.f;
+
+  uint2 ins = prog[0];
+  for (int k = 0; k < L; ++k) {
+    const uint2 nxt = prog[k + 1];
+    const uint32_t opc = ins.x & 0xffu;
+    const float c = __uint_as_float(ins.y);
+    const float* xf = xs + (ins.x >> 8) * ts;
+    float t[R];
+
+#define GG_ROWS _Pragma("unroll") for (int r = 0; r < R; ++r)
+#define GG_UN(u)                                   \
+  case I_UN + u:                                   \
+    GG_ROWS A[r] = unop<u>(A[r]);                  \
+    break;
+#define GG_BIN(kd)                                                    \
+  case I_BF + kd:                                                     \
+    load_rows<R>(xf, t);                                              \
+    GG_ROWS A[r] = binop<kd>(A[r], t[r]);                             \
+    break;                                                            \
+  case I_BC + kd:                                                     \
+    GG_ROWS A[r] = binop<kd>(A[r], c);                                \
+    break;                                                            \
+  case I_LF + kd:                                                     \
+    load_rows<R>(xf, t);                                              \
+    GG_ROWS A[r] = binop<kd>(t[r], A[r]);                             \
+    break;                                                            \
+  case I_LC + kd:                                                     \
+    GG_ROWS A[r] = binop<kd>(c, A[r]);                                \
+    break;
+#define GG_SLOT_BIN(kd, j)                                            \
+  case I_BS + kd * 8 + j:                                             \
+    if (j < DMAX) {                                                   \
+      GG_ROWS A[r] = binop<kd>(S[j < DMAX ? j : 0][r], A[r]);         \
+    }                                                                 \
+    break;                                                            \
+  case I_RS + kd * 8 + j:                                             \
+    if (j < DMAX) {                                                   \
+      GG_ROWS A[r] = binop<kd>(A[r], S[j < DMAX ? j : 0][r]);         \
+    }                                                                 \
+    break;
+#define GG_SLOT_KINDS(j) \
+  GG_SLOT_BIN(K_ADD, j)  \
+  GG_SLOT_BIN(K_SUB, j)  \
+  GG_SLOT_BIN(K_MUL, j)  \
+  GG_SLOT_BIN(K_AQ, j)   \
+  GG_SLOT_BIN(K_DIV, j)
+#define GG_PUSH(j)                                                    \
+  case I_LDF + j:                                                     \
+    if (j < DMAX) {                                                   \
+      GG_ROWS S[j < DMAX ? j : 0][r] = A[r];                          \
+    }                                                                 \
+    load_rows<R>(xf, A);                                              \
+    break;                                                            \
+  case I_LDC + j:                                                     \
+    if (j < DMAX) {                                                   \
+      GG_ROWS S[j < DMAX ? j : 0][r] = A[r];                          \
+    }                                                                 \
+    GG_ROWS A[r] = c;                                                 \
+    break;
+
+    switch (opc) {
+      case I_LDF0:
+        load_rows<R>(xf, A);
+        break;
+      case I_LDC0:
+        GG_ROWS A[r] = c;
+        break;
+      GG_UN(U_SIN)
+      GG_UN(U_COS)
+      GG_UN(U_EXP)
+      GG_UN(U_LOG_ABS)
+      GG_UN(U_SQRT_ABS)
+      GG_UN(U_SQUARE)
+      GG_UN(U_LOG)
+      GG_UN(U_SQRT)
+      GG_BIN(K_ADD)
+      GG_BIN(K_SUB)
+      GG_BIN(K_MUL)
+      GG_BIN(K_AQ)
+      GG_BIN(K_DIV)
+      GG_SLOT_KINDS(0)
+      GG_SLOT_KINDS(1)
+      GG_SLOT_KINDS(2)
+      GG_SLOT_KINDS(3)
+      GG_SLOT_KINDS(4)
+      GG_SLOT_KINDS(5)
+      GG_SLOT_KINDS(6)
+      GG_SLOT_KINDS(7)
+      GG_PUSH(0)
+      GG_PUSH(1)
+      GG_PUSH(2)
+      GG_PUSH(3)
+      GG_PUSH(4)
+      GG_PUSH(5)
+      GG_PUSH(6)
+      GG_PUSH(7)
+      default:
+        break;
+    }
+#undef GG_ROWS
+#undef GG_UN
+#undef GG_BIN
+#undef GG_SLOT_BIN
+#undef GG_SLOT_KINDS
+#undef GG_PUSH
+    if constexpr (TAPE) tape[32 * k] = A[0];
+    ins = nxt;
+  }
+}
+
+// ------------------------------------------------- error-free FP32 sums
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// (hi, lo) += x with the rounding error of the high part kept in lo.
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo += e;
+}
+
+// (hi, lo) += a * b with the product's rounding error (via FMA) kept too.
+__device__ __forceinline__ void acc_dot(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  float s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo += e + pe;
+}
+
+// Sum of two double-float values (hi1, lo1) + (hi2, lo2), renormalised.
+__device__ __forceinline__ void dd_add(float& hi, float& lo, float h2, float l2) {
+  float s, e;
+  two_sum(hi, h2, s, e);
+  e += lo + l2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+__device__ __forceinline__ void warp_dd_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    dd_add(hi, lo, h2, l2);
+  }
+}
+
+// -------------------------------------------------- mbarrier and bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// One TMA bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0),
+// completing as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`.  Gives up after `limit` polls
+// (each poll may suspend the thread for a hardware-defined time) and
+// records ST_TIMEOUT instead of hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned* status, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+}  // namespace gg

@@ -1,0 +1,15 @@
+// Instantiations of the batched forward kernel for programs that use at
+// most 3 stack slots (template heights up to 4).
+#include "kernels.cuh"
+
+namespace gg {
+const void* fwd_ptr_d3(int variant) {
+  switch (variant) {
+    case 0: return reinterpret_cast<const void*>(&fwd_kernel<3, 8, false, false>);
+    case 1: return reinterpret_cast<const void*>(&fwd_kernel<3, 4, false, false>);
+    case 2: return reinterpret_cast<const void*>(&fwd_kernel<3, 4, true, false>);
+    case 3: return reinterpret_cast<const void*>(&fwd_kernel<3, 4, true, true>);
+    default: return nullptr;
+  }
+}
+}  // namespace gg

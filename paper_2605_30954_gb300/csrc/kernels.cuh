@@ -1,0 +1,271 @@
+// Kernel templates: packer, batched forward interpreter, fitness finaliser.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+#include "isa.h"
+
+namespace gg {
+
+// ----------------------------------------------------------------- packing
+struct PackParams {
+  const uint8_t* op;
+  const float* cval;
+  const int8_t* height;  // nullable: every trial has height h_max
+  int n, h_max, stride, layout, n_features, max_slots, lstride;
+  uint2* prog;           // [n][lstride] (word, const bits)
+  Aux* aux;              // nullable, [n][lstride]
+  int* len;              // [n] instruction count, -1 for an invalid trial
+  unsigned* status;
+};
+
+// pack_kernel (defined in misc.cu): one thread per trial.
+
+// ------------------------------------------------------- batched forward
+// Work item = (group of `group` trials, row tile of `tile_rows` rows).  A
+// persistent CTA claims items from a global counter; for each it stages the
+// tile's feature rows and centred target (feature-major, row F = y - mean y)
+// into shared memory with TMA bulk copies, then its warps claim the group's
+// trials one at a time.  A warp runs its trial over every row of the tile,
+// R rows per lane per pass, and accumulates per-lane error-free FP32 sums of
+// d = f - c, d^2 and d * yc, where c is the mean of f over the tile's first
+// pass (a shift that keeps the sums well conditioned).  The warp combines
+// its lanes' sums in double-float arithmetic and writes one partial record
+// {c, S_d, S_dd, S_dy, max|f|} per (trial, tile) in FP64; fin_kernel merges
+// them.  (Section 3.2 accumulates squared errors per thread in registers
+// and reduces them per block; here the tile of rows is shared by many
+// trials so X is read from HBM once per group instead of once per trial.)
+struct FwdParams {
+  const float* X;      // [F + 1][ldx]: features, then centred target
+  int N, F, ldx;
+  const uint2* prog;   // [P][lstride]
+  const int* len;      // [P]
+  int lstride, P;
+  int tile_rows, n_tiles, group, n_items;
+  double* part;        // [P][n_tiles][5]
+  int* counter;        // work-item counter, zero at launch
+  unsigned* status;
+  float* rows_out;     // [P][N] per-row values (ROWS variant only)
+};
+
+constexpr int NPART = 5;
+
+__host__ __device__ inline size_t fwd_smem_bytes(int F, int tile_rows, int warps, int lstride) {
+  return (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * lstride * 8 + 16;
+}
+
+template <int R, bool MASK>
+__device__ __forceinline__ void accumulate_exact(const float (&A)[R], const float (&yv)[R], float cs,
+                                                 int valid, float& s1h, float& s1l, float& s2h,
+                                                 float& s2l, float& s3h, float& s3l, float& fm) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const bool ok = !MASK || r < valid;
+    const float d = ok ? A[r] - cs : 0.f;
+    fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
+    acc_add(s1h, s1l, d);
+    acc_dot(s2h, s2l, d, d);
+    acc_dot(s3h, s3l, d, yv[r]);
+  }
+}
+
+template <int R, bool MASK>
+__device__ __forceinline__ void accumulate_pairwise(const float (&A)[R], const float (&yv)[R],
+                                                    float cs, int valid, float& s1h, float& s1l,
+                                                    float& s2h, float& s2l, float& s3h, float& s3l,
+                                                    float& fm) {
+  float d[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const bool ok = !MASK || r < valid;
+    d[r] = ok ? A[r] - cs : 0.f;
+    fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
+  }
+  float a[R / 2], b[R / 2], c[R / 2];
+#pragma unroll
+  for (int i = 0; i < R / 2; ++i) {
+    a[i] = d[2 * i] + d[2 * i + 1];
+    b[i] = fmaf(d[2 * i], d[2 * i], d[2 * i + 1] * d[2 * i + 1]);
+    c[i] = fmaf(d[2 * i], yv[2 * i], d[2 * i + 1] * yv[2 * i + 1]);
+  }
+#pragma unroll
+  for (int w = R / 4; w >= 1; w >>= 1) {
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      a[i] = a[2 * i] + a[2 * i + 1];
+      b[i] = b[2 * i] + b[2 * i + 1];
+      c[i] = c[2 * i] + c[2 * i + 1];
+    }
+  }
+  acc_add(s1h, s1l, a[0]);
+  acc_add(s2h, s2l, b[0]);
+  acc_add(s3h, s3l, c[0]);
+}
+
+template <int DMAX, int R, bool EXACT, bool ROWS>
+__global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  float* xs = reinterpret_cast<float*>(smem);
+  uint2* wprog = reinterpret_cast<uint2*>(xs + (size_t)(p.F + 1) * p.tile_rows) +
+                 (size_t)warp * p.lstride;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint2*>(
+                      xs + (size_t)(p.F + 1) * p.tile_rows) + (size_t)nw * p.lstride);
+  int* ctl = reinterpret_cast<int*>(bar + 1);
+
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+
+  float S[DMAX][R];
+#pragma unroll
+  for (int j = 0; j < DMAX; ++j)
+#pragma unroll
+    for (int r = 0; r < R; ++r) S[j][r] = 0.f;
+
+  constexpr int RPP = 32 * R;  // rows per pass of a warp
+  uint32_t parity = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      ctl[0] = atomicAdd(p.counter, 1);
+      ctl[1] = 0;
+    }
+    __syncthreads();
+    const int item = ctl[0];
+    if (item >= p.n_items) break;
+    const int g = item / p.n_tiles;
+    const int tile = item - g * p.n_tiles;
+    const int row0 = tile * p.tile_rows;
+    const int nrows = min(p.tile_rows, p.N - row0);
+    const int ncopy = (nrows + 3) & ~3;
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, (uint32_t)((p.F + 1) * ncopy * 4));
+      for (int f = 0; f <= p.F; ++f)
+        bulk_g2s(xs + (size_t)f * p.tile_rows, p.X + (size_t)f * p.ldx + row0,
+                 (uint32_t)(ncopy * 4), bar);
+    }
+    if (ncopy < p.tile_rows) {  // zero the tail of a ragged tile
+      const int tail = p.tile_rows - ncopy;
+      for (int i = threadIdx.x; i < (p.F + 1) * tail; i += blockDim.x) {
+        const int f = i / tail;
+        xs[(size_t)f * p.tile_rows + ncopy + (i - f * tail)] = 0.f;
+      }
+    }
+    const bool ok = mbar_wait_bounded(bar, parity, p.status, WAIT_LIMIT);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) return;
+
+    const int npass = (nrows + RPP - 1) / RPP;
+    for (;;) {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&ctl[1], 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      const int trial = g * p.group + t;
+      if (t >= p.group || trial >= p.P) break;
+      const int L = p.len[trial];
+      if (L <= 0) continue;
+      const uint2* src = p.prog + (size_t)trial * p.lstride;
+      for (int k = lane; k <= L; k += 32) wprog[k] = src[k];
+      __syncwarp();
+
+      float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
+      float cs = 0.f;
+      for (int ps = 0; ps < npass; ++ps) {
+        const int r0 = ps * RPP + lane * R;
+        float A[R];
+        run_program<DMAX, R>(wprog, L, xs + r0, p.tile_rows, A, S);
+        const int valid = nrows - r0;  // rows of this lane inside the tile
+        if constexpr (ROWS) {
+          float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (r < valid) out[r] = A[r];
+        }
+        if (ps == 0) {  // shift: mean of f over the first pass's rows
+          float s = 0.f;
+          int cnt = 0;
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (r < valid) {
+              s += A[r];
+              ++cnt;
+            }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+          }
+          cs = s / (float)cnt;
+        }
+        float yv[R];
+        load_rows<R>(xs + (size_t)p.F * p.tile_rows + r0, yv);
+        const bool full = (ps + 1) * RPP <= nrows;
+        if constexpr (EXACT) {
+          if (full)
+            accumulate_exact<R, false>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+          else
+            accumulate_exact<R, true>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+        } else {
+          if (full)
+            accumulate_pairwise<R, false>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+          else
+            accumulate_pairwise<R, true>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+        }
+      }
+      warp_dd_sum(s1h, s1l);
+      warp_dd_sum(s2h, s2l);
+      warp_dd_sum(s3h, s3l);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+      if (lane == 0) {
+        double* q = p.part + ((size_t)trial * p.n_tiles + tile) * NPART;
+        q[0] = (double)cs;
+        q[1] = (double)s1h + (double)s1l;
+        q[2] = (double)s2h + (double)s2l;
+        q[3] = (double)s3h + (double)s3l;
+        q[4] = (double)fm;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- finaliser
+// Merge the per-tile partial sums of every trial in FP64 (fixed order, so
+// the result is deterministic) and turn them into a*, b*, smse and mse.
+// With d = f - c* (c* the first tile's shift) and yc = y - mean(y):
+//   var_N = S_dd - S_d^2/N,  cov_N = S_dy - S_d S_yc/N,  b* = cov_N/var_N,
+//   smse  = (Syy_N - b* cov_N)/N   (the least-squares residual, Eq. 1 with
+//   the optimal affine map), mse = (1/N) sum (d - yc + c* - ybar)^2.
+struct FinParams {
+  const double* part;
+  const int* len;
+  int P, n_tiles, tile_rows;
+  long long N;
+  const double* pref;  // [N + 1] prefix sums of the stored centred target
+  double ybar, syc, sycyc;
+  float* smse;
+  float* a;
+  float* b;
+  float* mse;
+  double* ab;          // [P][4]: a* - ybar, b*, finite flag, 0 (adjoint), nullable
+};
+
+constexpr double VAR_TOL = 1e-12;
+
+// fin_kernel is defined in misc.cu.
+
+// kernel pointers, one table per translation unit (fwd_d3.cu, fwd_d5.cu,
+// fwd_d7.cu): variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
+// pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values
+constexpr int NVARIANT = 4;
+const void* fwd_ptr_d3(int variant);
+const void* fwd_ptr_d5(int variant);
+const void* fwd_ptr_d7(int variant);
+inline int variant_rows(int v) { return v == 0 ? 8 : 4; }
+inline bool variant_exact(int v) { return v >= 2; }
+
+}  // namespace gg

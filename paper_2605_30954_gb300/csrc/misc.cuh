@@ -1,0 +1,63 @@
+// Parameter blocks and entry points of the kernels defined in misc.cu and
+// adjoint.cu (the packer, the fitness finaliser, the adjoint, Adam and the
+// dataset transpose).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace gg {
+
+struct AdjParams {
+  const float* X;      // [F + 1][ldx], row F = centred target
+  int N, F, ldx;
+  const uint2* prog;   // [P][lstride]
+  const Aux* aux;      // [P][lstride]
+  const int* len;      // [P]
+  int lstride, P, stride;
+  const double* ab;    // [P][4]: a* - mean(y), b*, finite flag, unused
+  int mse_mode;        // 0: d smse / d c, 1: d mse / d c
+  double ybar;
+  int chunk_rows, n_chunks, n_items;
+  int* counter;        // zero at launch
+  double* gacc;        // [P][stride], zero at launch
+};
+
+struct GradOutParams {
+  const double* gacc;
+  const int* len;
+  int P, stride;
+  float* dcval;        // [P][stride]
+};
+
+struct AdamParams {
+  const uint8_t* op;
+  float* cval;
+  const float* grad;
+  float* m;
+  float* v;
+  long long count;     // P * stride
+  float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+};
+
+struct TransposeParams {
+  const float* src;    // [N][F] row-major
+  float* dst;          // [F][ldx]
+  int N, F, ldx;
+};
+
+constexpr int ADJ_WARP_BYTES_PER_INSTR = 8 + 8 + 2 * 32 * 4 + 8;
+
+inline size_t adj_smem_bytes(int warps, int lstride) {
+  return (size_t)warps * lstride * ADJ_WARP_BYTES_PER_INSTR + 16;
+}
+
+const void* pack_ptr();
+const void* fin_ptr();
+const void* adj_ptr(int dmax);
+const void* gradout_ptr();
+const void* adam_ptr();
+const void* transpose_ptr();
+
+}  // namespace gg

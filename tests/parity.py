@@ -1,0 +1,161 @@
+"""Parity helpers: build a seeded workload with its target from the oracle,
+and compare library outputs with the oracle under the stated tolerances.
+
+Tolerances (from the accuracy targets of this evaluator):
+  per row   |g - r| <= 1e-5 (|r| + rms(r))      rms over the trial's rows
+  smse      |g - r| <= 1e-4 r + 1e-8 Var(y)
+  mse       |g - r| <= 1e-4 r + 1e-8 (mean y^2 + mean f^2)
+  gradient  |g - r| <= 1e-3 (|r| + 1e-3 max_k |r_k|)
+A row (trial) is ill-conditioned in FP32, and excluded, when its value
+moves by more than a quarter of its tolerance either in the FP32-emulated
+oracle or under relative perturbations of 4 FP32 units in the last place at
+every function node (oracle.eval_tree_perturbed, two random draws); a trial
+whose fitness is infinite under one of these and finite under another is
+ambiguous and excluded.  Both counts are reported.
+"""
+import math
+
+import numpy as np
+
+import oracle as O
+import synth
+
+ROW_TOL = 1e-5
+SMSE_RTOL, SMSE_FLOOR = 1e-4, 1e-8
+GRAD_TOL = 1e-3
+COND_MARGIN = 0.25
+
+
+def target_from_oracle(w):
+    """First candidate generator tree with finite values, nonzero variance
+    and |f| <= 1e6 (the oracle evaluates it), plus the workload's noise."""
+    for gop, gcv, gh in w["y_cands"]():
+        f = O.eval_tree(O.Template(gop, gcv, gh, "heap", w["F"]), w["X"])
+        with np.errstate(all="ignore"):
+            if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
+                return synth.make_target(f, w["z"], w["noise"]), (gop, gcv, gh)
+    raise RuntimeError("no usable generator tree")
+
+
+def build(cfg, n_rows=None, n_trials=None, rep=0, layout="heap"):
+    w = synth.workload(cfg, rep, n_rows, n_trials, layout)
+    w["y"], w["gen"] = target_from_oracle(w)
+    return w
+
+
+def template(w, p):
+    h = int(w["heights"][p])
+    return O.Template(w["op"][p], w["cval"][p], h, w["layout"], w["F"])
+
+
+class Tally:
+    def __init__(self):
+        self.checked = self.excluded = self.failed = 0
+        self.worst = 0.0
+        self.msgs = []
+
+    def __repr__(self):
+        return (f"checked={self.checked} excluded={self.excluded} failed={self.failed} "
+                f"worst={self.worst:.3g} {self.msgs[:5]}")
+
+
+def check_rows(g, f64, f32, tally, tag="", pert=()):
+    """Per-row values of one trial.  ``pert``: perturbed FP64 evaluations
+    (oracle.eval_tree_perturbed) used with f32 to flag ill-conditioned rows."""
+    with np.errstate(all="ignore"):
+        fin = np.isfinite(f64)
+        rms = math.sqrt(np.mean(f64[fin] ** 2)) if fin.any() else 0.0
+        tol = ROW_TOL * (np.abs(f64) + rms)
+        err32 = np.abs(f32.astype(np.float64) - f64)
+        ill = ~fin | ~np.isfinite(f32) | (err32 > COND_MARGIN * tol)
+        for fp in pert:
+            ill |= ~np.isfinite(fp) | (np.abs(fp - f64) > COND_MARGIN * tol)
+        err = np.abs(g.astype(np.float64) - f64)
+        bad = ~ill & ~(err <= tol)
+    tally.checked += int((~ill).sum())
+    tally.excluded += int(ill.sum())
+    if bad.any():
+        tally.failed += int(bad.sum())
+        i = int(np.argmax(np.where(bad, err / np.maximum(tol, 1e-300), 0)))
+        tally.msgs.append(f"{tag} row {i}: gpu {g[i]!r} oracle {f64[i]!r}")
+    ok = ~ill
+    if ok.any():
+        tally.worst = max(tally.worst, float(np.max(err[ok] / np.maximum(tol[ok], 1e-300))))
+
+
+def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", fits_pert=()):
+    """smse (and mse) of one trial.  ``fits_pert``: fitness of perturbed
+    evaluations, used with fit32 to flag ill-conditioned trials."""
+    inf64 = not fit64["finite"]
+    inf32 = not fit32["finite"]
+    if inf64 != inf32 or any(fp["finite"] != fit64["finite"] for fp in fits_pert):
+        tally.excluded += 1
+        return
+    if inf64:
+        tally.checked += 1
+        if not (math.isinf(g_smse) and g_smse > 0):
+            tally.failed += 1
+            tally.msgs.append(f"{tag}: oracle +inf, gpu {g_smse}")
+        return
+    r = fit64["smse"]
+    tol = SMSE_RTOL * r + SMSE_FLOOR * var_y
+    if (abs(fit32["smse"] - r) > COND_MARGIN * tol or (fit64["b"] == 0.0) != (fit32["b"] == 0.0)
+            or any(abs(fp["smse"] - r) > COND_MARGIN * tol or (fp["b"] == 0.0) != (fit64["b"] == 0.0)
+                   for fp in fits_pert)):
+        tally.excluded += 1
+        return
+    tally.checked += 1
+    err = abs(g_smse - r)
+    tally.worst = max(tally.worst, err / tol)
+    if not err <= tol:
+        tally.failed += 1
+        tally.msgs.append(f"{tag}: smse gpu {g_smse!r} oracle {r!r} tol {tol:.3g}")
+    if g_mse is not None:
+        rm = fit64["mse"]
+        tm = SMSE_RTOL * rm + SMSE_FLOOR * mean_y2
+        if abs(fit32["mse"] - rm) <= COND_MARGIN * tm and not abs(g_mse - rm) <= tm:
+            tally.failed += 1
+            tally.msgs.append(f"{tag}: mse gpu {g_mse!r} oracle {rm!r}")
+
+
+#: relative size of the per-node perturbations: 4 FP32 units in the last place
+PERTURB_REL = 4 * 2.0 ** -24
+N_PERTURB = 2
+
+
+def oracle_trial(w, p, X=None, y=None, with_pert=True):
+    """Oracle data of trial p: template, FP64 rows, FP32-emulated rows,
+    their fitness, and N_PERTURB perturbed evaluations with their fitness."""
+    X = w["X"] if X is None else X
+    y = w["y"] if y is None else y
+    t = template(w, p)
+    f64 = O.eval_tree(t, X)
+    f32 = O.eval_tree_f32(t, X)
+    pert = []
+    if with_pert:
+        rng = np.random.default_rng(12345 + p)
+        pert = [O.eval_tree_perturbed(t, X, PERTURB_REL, rng) for _ in range(N_PERTURB)]
+    fits = [O.fitness(fp, y) for fp in pert]
+    return t, f64, f32, O.fitness(f64, y), O.fitness(f32.astype(np.float64), y), pert, fits
+
+
+def intermediates_finite_f32(t, X):
+    """True if every active node of the FP32-emulated evaluation is finite."""
+    store = {}
+    O.gp._eval(t, np.asarray(X, dtype=np.float32), np.float32, store=store)
+    with np.errstate(all="ignore"):
+        return all(np.all(np.isfinite(v)) for v in store.values())
+
+
+def check_grad(g, r, tally, tag=""):
+    scale = 1e-3 * float(np.max(np.abs(r))) if r.size else 0.0
+    tol = GRAD_TOL * (np.abs(r) + scale)
+    err = np.abs(g.astype(np.float64) - r)
+    tally.checked += 1
+    with np.errstate(all="ignore"):
+        ratio = np.where(tol > 0, err / np.maximum(tol, 1e-300), np.where(err > 0, np.inf, 0.0))
+    tally.worst = max(tally.worst, float(np.max(ratio)) if ratio.size else 0.0)
+    if not np.all(err <= tol):
+        tally.failed += 1
+        k = int(np.argmax(ratio))
+        tally.msgs.append(f"{tag} pos {k}: gpu {g[k]!r} oracle {r[k]!r}")

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Small cases span several row tiles and a ragged
+tail; the full-size cases run every configuration at its benchmark size and
+compare a sample of trials the oracle computes one by one."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from fixtures import fig1, heap_template
+import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_30954_gb300 as pkg
+    pkg.lib()  # raises ImportError if the library is not built
+    return pkg
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.cuda() if dtype is None else t.to(dtype).cuda()
+
+
+def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0):
+    X = torch.from_numpy(w["X"])
+    y = torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    op, cv = dev(w["op"]), dev(w["cval"])
+    hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
+    smse, a, b, mse = ds.eval_batch(op, cv, hs, layout=layout, flags=flags)
+    idx = range(w["P"]) if sample is None else sample
+    rows = None
+    if check_rows:
+        rows = ds.eval_rows(op, cv, hs, layout=layout).cpu().numpy()
+    ds.sync()
+    smse, a, b, mse = (t.cpu().numpy() for t in (smse, a, b, mse))
+    tr, tf = PA.Tally(), PA.Tally()
+    var_y = float(np.var(w["y"].astype(np.float64)))
+    mean_y2 = float(np.mean(w["y"].astype(np.float64) ** 2))
+    for p in idx:
+        t, f64, f32, fit64, fit32, pert, fits = PA.oracle_trial(w, p)
+        if rows is not None:
+            PA.check_rows(rows[p], f64, f32, tr, tag=f"trial {p}", pert=pert)
+        PA.check_fit(float(smse[p]), float(mse[p]), fit64, fit32, var_y, mean_y2, tf,
+                     tag=f"trial {p}", fits_pert=fits)
+    ds.close()
+    return tr, tf, (smse, a, b, mse)
+
+
+def assert_tally(t, min_checked=1, max_excl=0.08):
+    assert t.failed == 0, repr(t)
+    assert t.checked >= min_checked, repr(t)
+    assert t.excluded <= max_excl * (t.checked + t.excluded) + 2, repr(t)
+
+
+# ------------------------------------------------------------------ basics --
+def test_fig1_on_gpu(gg):
+    op, cv, _ = fig1()
+    X = np.random.default_rng(0).uniform(1, 2, (777, 6)).astype(np.float32)
+    y = (np.sin(X[:, 0]) + X[:, 1]).astype(np.float32)
+    ds = gg.Dataset(torch.from_numpy(X), torch.from_numpy(y))
+    f = ds.eval_rows(dev(op[None]), dev(cv[None])).cpu().numpy()[0]
+    want = -2.0 / (4.0 * X[:, 0].astype(np.float64) + X[:, 1])
+    np.testing.assert_allclose(f, want, rtol=2e-7)
+    smse, a, b, mse = ds.eval_batch(dev(op[None]), dev(cv[None]))
+    fit = O.fitness(want, y)
+    assert abs(smse.item() - fit["smse"]) <= 1e-4 * fit["smse"]
+    ds.sync()
+    ds.close()
+
+
+@pytest.mark.parametrize("cfg,n_rows,n_trials", [
+    ("c1", 1000, 256), ("c1", 3001, 97), ("c2", 5003, 64), ("c3", 4099, 48),
+    ("c4", 2500, 40), ("c5", 3000, 32),
+])
+def test_small_configs_rows_and_fitness(gg, cfg, n_rows, n_trials):
+    w = PA.build(cfg, n_rows, n_trials)
+    tr, tf, _ = run_case(gg, w)
+    assert_tally(tr, min_checked=n_rows * n_trials // 3)
+    assert_tally(tf, min_checked=n_trials // 3, max_excl=0.2)
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c3"])
+def test_prefix_layout_matches_heap(gg, cfg):
+    wh = PA.build(cfg, 2000, 40, layout="heap")
+    wp = PA.build(cfg, 2000, 40, layout="prefix")
+    _, tf, outs_p = run_case(gg, wp, layout=1, check_rows=False)
+    assert_tally(tf)
+    _, _, outs_h = run_case(gg, wh, layout=0, check_rows=False)
+    np.testing.assert_array_equal(outs_p[0], outs_h[0])
+
+
+def test_pairwise_sums_large_n(gg):
+    # N >= 32768 selects the 8-rows-per-lane kernel with pairwise sums
+    w = PA.build("c2", 40_000, 48)
+    tr, tf, _ = run_case(gg, w, check_rows=True)
+    assert_tally(tr, min_checked=40_000 * 10)
+    assert_tally(tf, min_checked=16)
+
+
+def test_exact_flag_and_plain_form_agree(gg):
+    w = PA.build("c2", 9000, 40)
+    X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    op, cv = dev(w["op"]), dev(w["cval"])
+    s0 = ds.eval_batch(op, cv)[0]
+    s1 = ds.eval_batch(op, cv, flags=gg.F_EXACT)[0]
+    s2 = ds.eval_plain(op, cv)[0]
+    ds.sync()
+    for s in (s1, s2):
+        a, b = s0.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+        fin = np.isfinite(a)
+        assert np.array_equal(fin, np.isfinite(b))
+        np.testing.assert_allclose(b[fin], a[fin], rtol=2e-4, atol=1e-8 * np.var(w["y"]))
+    ds.close()
+
+
+def test_graph_replay_and_host_batches(gg):
+    w = PA.build("c1", 1000, 256)
+    X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    op, cv = dev(w["op"]), dev(w["cval"])
+    ref = [t.clone() for t in ds.eval_batch(op, cv)]
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    outs = [torch.empty(256, device="cuda") for _ in range(4)]
+    for _ in range(3):
+        with torch.cuda.stream(st):
+            ds.eval_batch(op, cv, flags=gg.F_GRAPH, out=outs, stream=st)
+        st.synchronize()
+        for r, o in zip(ref, outs):
+            assert torch.equal(r, o)
+    hop = torch.from_numpy(w["op"]).pin_memory()
+    hcv = torch.from_numpy(w["cval"]).pin_memory()
+    hout = ds.eval_batch(hop, hcv)
+    torch.cuda.synchronize()
+    for r, o in zip(ref, hout):
+        assert not o.is_cuda
+        assert torch.equal(r.cpu(), o)
+    ds.sync()
+    ds.close()
+
+
+def test_autotune_keeps_results(gg):
+    w = PA.build("c2", 50_000, 300)
+    X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    op, cv = dev(w["op"]), dev(w["cval"])
+    a = ds.eval_batch(op, cv)[0].cpu().numpy()
+    ds.autotune(op, cv)
+    b = ds.eval_batch(op, cv)[0].cpu().numpy()
+    ds.sync()
+    fin = np.isfinite(a)
+    np.testing.assert_array_equal(fin, np.isfinite(b))
+    np.testing.assert_allclose(b[fin], a[fin], rtol=2e-4, atol=1e-8 * np.var(w["y"]))
+    ds.close()
+
+
+# -------------------------------------------------------------- edge cases --
+def test_empty_batch_and_single_row(gg):
+    X = torch.tensor([[0.5, -1.0]], dtype=torch.float32)
+    y = torch.tensor([2.0])
+    ds = gg.Dataset(X, y)
+    op, cv = heap_template(["+", "x0", "sin", None, None, "x1"], 2)
+    empty = torch.zeros((0, 7), dtype=torch.uint8, device="cuda")
+    assert ds.eval_batch(empty, torch.zeros((0, 7), device="cuda"))[0].numel() == 0
+    smse, a, b, mse = ds.eval_batch(dev(op[None]), dev(cv[None]))
+    ds.sync()
+    assert smse.item() == 0.0 and b.item() == 0.0
+    assert abs(a.item() - 2.0) < 1e-6
+    f = 0.5 + math.sin(-1.0)
+    assert abs(mse.item() - (f - 2.0) ** 2) < 1e-5
+    ds.close()
+
+
+def test_degenerate_trees(gg):
+    rng = np.random.default_rng(1)
+    N = 3333
+    X = rng.uniform(-1, 1, (N, 3)).astype(np.float32)
+    X[17, 0] = 0.0
+    y = (X[:, 0] * 2 + 1).astype(np.float32)
+    trees = [
+        (["2.5"], 0),                                  # constant, height 0
+        (["x1"], 0),                                   # single feature
+        (["*", "3", "-4"], 1),                         # constant tree
+        (["logabs", "x0", "x1"], 1),                   # log|0| at row 17 -> +inf
+        (["+", "x0", "1"], 1),                         # exact affine fit of y
+        (["exp", "*", None, "60", "x1"], 2),           # > 2^50 somewhere -> +inf
+        (["aq", "x0", "*", None, None, "1e10", "x1"], 2),  # huge denominator
+    ]
+    ops, cvs = [], []
+    for toks, h in trees:
+        o, c = heap_template(toks, h)
+        oo = np.full(7, 255, np.uint8)
+        cc = np.zeros(7, np.float32)
+        # re-embed a height-h template into a height-2 row with its own height
+        oo[:o.size], cc[:c.size] = o, c
+        ops.append(oo)
+        cvs.append(cc)
+    hs = np.array([h for _, h in trees], dtype=np.int8)
+    ds = gg.Dataset(torch.from_numpy(X), torch.from_numpy(y))
+    smse, a, b, mse = (t.cpu().numpy() for t in ds.eval_batch(dev(np.stack(ops)), dev(np.stack(cvs)),
+                                                               dev(hs)))
+    ds.sync()
+    vy = np.var(y.astype(np.float64))
+    np.testing.assert_allclose(smse[0], vy, rtol=1e-5)
+    assert b[0] == 0.0 and b[2] == 0.0
+    rho = np.corrcoef(X[:, 1], y)[0, 1]
+    np.testing.assert_allclose(smse[1], vy * (1 - rho ** 2), rtol=1e-4)
+    np.testing.assert_allclose(smse[2], vy, rtol=1e-5)
+    assert math.isinf(smse[3]) and math.isinf(mse[3]) and a[3] == 0 and b[3] == 0
+    assert smse[4] <= 1e-8 * vy and abs(b[4] - 2) < 1e-5 and abs(a[4] + 1) < 1e-5
+    assert math.isinf(smse[5])
+    for p in (6,):
+        t = O.Template(ops[p], cvs[p], int(hs[p]), n_features=3)
+        fit = O.fitness(O.eval_tree(t, X), y)
+        assert abs(smse[p] - fit["smse"]) <= 1e-4 * fit["smse"] + 1e-8 * vy
+    ds.close()
+
+
+def test_invalid_trial_reports_and_isolates(gg):
+    w = PA.build("c1", 1000, 8)
+    op = w["op"].copy()
+    op[3, 0] = 200  # unknown opcode at the root
+    X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    smse = ds.eval_batch(dev(op), dev(w["cval"]))[0]
+    with pytest.raises(gg.GGEvalError) as e:
+        ds.sync()
+    assert e.value.status == -2
+    s = smse.cpu().numpy()
+    assert math.isnan(s[3]) and np.isfinite(s[np.arange(8) != 3]).sum() >= 5
+    ds.sync()  # status was cleared
+    ds.close()
+
+
+def test_bad_arguments_rejected(gg):
+    X = torch.zeros((10, 2))
+    y = torch.arange(10, dtype=torch.float32)
+    with pytest.raises(gg.GGEvalError):
+        gg.Dataset(X, y * float("nan"))
+    ds = gg.Dataset(X, y)
+    op = torch.zeros((2, 1023), dtype=torch.uint8, device="cuda")  # height 9
+    with pytest.raises(gg.GGEvalError) as e:
+        ds.eval_batch(op, torch.zeros((2, 1023), device="cuda"))
+    assert e.value.status == -7
+    ds.close()
+
+
+@pytest.mark.parametrize("h,nf", [(8, 1), (8, 40), (0, 3)])
+def test_max_height_and_feature_counts(gg, h, nf):
+    rng = np.random.default_rng(h * 100 + nf)
+    N = 2100
+    X = rng.uniform(-1, 1, (N, nf)).astype(np.float32)
+    y = (np.cos(X[:, 0]) + 0.1 * rng.standard_normal(N)).astype(np.float32)
+    op, cv, hs = synth.random_templates(rng, 24, h, h, synth.BASIC_SET, nf, 0.9)
+    w = dict(X=X, y=y, op=op, cval=cv, heights=hs, layout="heap", F=nf, P=24)
+    tr, tf, _ = run_case(gg, w)
+    assert_tally(tr, min_checked=N * 8, max_excl=0.2)
+    assert_tally(tf, min_checked=8, max_excl=0.3)
+
+
+# -------------------------------------------------------- full-size configs --
+FULL = [("c1", None), ("c2", 24), ("c3", 24), ("c4", 24), ("c5", 12)]
+
+
+@pytest.mark.parametrize("cfg,n_sample", FULL)
+def test_full_size_config_sampled(gg, cfg, n_sample):
+    w = PA.build(cfg)
+    sample = None
+    if n_sample is not None:
+        sample = np.random.default_rng(7).choice(w["P"], n_sample, replace=False).tolist()
+    tr, tf, outs = run_case(gg, w, sample=sample, check_rows=False)
+    assert_tally(tf, min_checked=(n_sample or w["P"]) // 2, max_excl=0.25)
+    assert np.sum(np.isnan(outs[0])) == 0

@@ -313,6 +313,19 @@ def test_fp32_emulation_close_on_benign_tree():
     np.testing.assert_allclose(f32, f64, rtol=1e-6, atol=1e-6)
 
 
+def test_perturbed_evaluation_bounds():
+    rng, X = rand_xy(12)
+    t = T(["*", "x0", "x1"], 1)
+    f = O.eval_tree(t, X)
+    np.testing.assert_array_equal(O.eval_tree_perturbed(t, X, 0.0, rng), f)
+    fp = O.eval_tree_perturbed(t, X, 1e-3, rng)
+    np.testing.assert_allclose(np.abs(fp / f - 1.0), 1e-3, rtol=1e-9)
+    # sin of a large argument: a tiny relative change of the argument moves it a lot
+    ts = T(["sin", "*", None, "1e6", "x0"], 2)
+    spread = np.abs(O.eval_tree_perturbed(ts, X, 1e-7, rng) - O.eval_tree(ts, X))
+    assert np.median(spread) > 1e-2
+
+
 def test_eval_batch_matches_single():
     rng, X = rand_xy(11)
     y = X[:, 0] * 2
