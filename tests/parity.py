@@ -6,12 +6,13 @@ Tolerances (from the accuracy targets of this evaluator):
   smse      |g - r| <= 1e-4 r + 1e-8 Var(y)
   mse       |g - r| <= 1e-4 r + 1e-8 (mean y^2 + mean f^2)
   gradient  |g - r| <= 1e-3 (|r| + 1e-3 max_k |r_k|)
-A row (trial) is ill-conditioned in FP32, and excluded, when its value
-moves by more than a quarter of its tolerance either in the FP32-emulated
-oracle or under relative perturbations of 4 FP32 units in the last place at
-every function node (oracle.eval_tree_perturbed, two random draws); a trial
-whose fitness is infinite under one of these and finite under another is
-ambiguous and excluded.  Both counts are reported.
+A row is ill-conditioned in FP32, and excluded, when its FP32-emulated
+oracle value or the first-order bound on the effect of relative errors of
+4 FP32 units in the last place at every function node
+(oracle.condition_bound) exceeds a quarter of its tolerance.  A trial is
+excluded when the same bound, carried to its smse (or mse), exceeds a
+quarter of that tolerance, or when its FP64 and FP32-emulated fitness
+disagree on being infinite (ambiguous).  Both counts are reported.
 """
 import math
 
@@ -23,7 +24,7 @@ import synth
 ROW_TOL = 1e-5
 SMSE_RTOL, SMSE_FLOOR = 1e-4, 1e-8
 GRAD_TOL = 1e-3
-COND_MARGIN = 0.25
+COND_MARGIN = 0.5
 
 
 def target_from_oracle(w):
@@ -59,17 +60,17 @@ class Tally:
                 f"worst={self.worst:.3g} {self.msgs[:5]}")
 
 
-def check_rows(g, f64, f32, tally, tag="", pert=()):
-    """Per-row values of one trial.  ``pert``: perturbed FP64 evaluations
-    (oracle.eval_tree_perturbed) used with f32 to flag ill-conditioned rows."""
+def check_rows(g, f64, f32, tally, tag="", cond=None):
+    """Per-row values of one trial.  ``cond``: per-row error bound
+    (oracle.condition_bound) used with f32 to flag ill-conditioned rows."""
     with np.errstate(all="ignore"):
         fin = np.isfinite(f64)
         rms = math.sqrt(np.mean(f64[fin] ** 2)) if fin.any() else 0.0
         tol = ROW_TOL * (np.abs(f64) + rms)
         err32 = np.abs(f32.astype(np.float64) - f64)
         ill = ~fin | ~np.isfinite(f32) | (err32 > COND_MARGIN * tol)
-        for fp in pert:
-            ill |= ~np.isfinite(fp) | (np.abs(fp - f64) > COND_MARGIN * tol)
+        if cond is not None:
+            ill |= ~(cond <= COND_MARGIN * tol)
         err = np.abs(g.astype(np.float64) - f64)
         bad = ~ill & ~(err <= tol)
     tally.checked += int((~ill).sum())
@@ -83,12 +84,26 @@ def check_rows(g, f64, f32, tally, tag="", pert=()):
         tally.worst = max(tally.worst, float(np.max(err[ok] / np.maximum(tol[ok], 1e-300))))
 
 
-def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", fits_pert=()):
-    """smse (and mse) of one trial.  ``fits_pert``: fitness of perturbed
-    evaluations, used with fit32 to flag ill-conditioned trials."""
+def fit_bounds(f64, y, fit64, cond):
+    """Bounds on the change of smse and mse when every row value moves by at
+    most cond_i: (1/N) sum (2 |r_i| e_i + e_i^2) with r_i the residual of
+    the scaled (b e_i) or plain fit."""
+    y = np.asarray(y, dtype=np.float64)
+    with np.errstate(all="ignore"):
+        r = y - fit64["a"] - fit64["b"] * f64
+        e = np.abs(fit64["b"]) * cond
+        ds = float(np.mean(2 * np.abs(r) * e + e * e))
+        rm = f64 - y
+        dm = float(np.mean(2 * np.abs(rm) * cond + cond * cond))
+    return ds, dm
+
+
+def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", bounds=None):
+    """smse (and mse) of one trial.  ``bounds``: (smse, mse) change bounds
+    from fit_bounds, used with fit32 to flag ill-conditioned trials."""
     inf64 = not fit64["finite"]
     inf32 = not fit32["finite"]
-    if inf64 != inf32 or any(fp["finite"] != fit64["finite"] for fp in fits_pert):
+    if inf64 != inf32 or (bounds is not None and not inf64 and not np.isfinite(bounds[0])):
         tally.excluded += 1
         return
     if inf64:
@@ -100,8 +115,7 @@ def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", fits_p
     r = fit64["smse"]
     tol = SMSE_RTOL * r + SMSE_FLOOR * var_y
     if (abs(fit32["smse"] - r) > COND_MARGIN * tol or (fit64["b"] == 0.0) != (fit32["b"] == 0.0)
-            or any(abs(fp["smse"] - r) > COND_MARGIN * tol or (fp["b"] == 0.0) != (fit64["b"] == 0.0)
-                   for fp in fits_pert)):
+            or (bounds is not None and not bounds[0] <= COND_MARGIN * tol)):
         tally.excluded += 1
         return
     tally.checked += 1
@@ -113,30 +127,29 @@ def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", fits_p
     if g_mse is not None:
         rm = fit64["mse"]
         tm = SMSE_RTOL * rm + SMSE_FLOOR * mean_y2
-        if abs(fit32["mse"] - rm) <= COND_MARGIN * tm and not abs(g_mse - rm) <= tm:
+        well = abs(fit32["mse"] - rm) <= COND_MARGIN * tm and (
+            bounds is None or bounds[1] <= COND_MARGIN * tm)
+        if well and not abs(g_mse - rm) <= tm:
             tally.failed += 1
             tally.msgs.append(f"{tag}: mse gpu {g_mse!r} oracle {rm!r}")
 
 
-#: relative size of the per-node perturbations: 4 FP32 units in the last place
-PERTURB_REL = 4 * 2.0 ** -24
-N_PERTURB = 2
+#: relative error assumed at every function node: 4 FP32 units in the last place
+COND_REL = 4 * 2.0 ** -24
 
 
-def oracle_trial(w, p, X=None, y=None, with_pert=True):
+def oracle_trial(w, p, X=None, y=None):
     """Oracle data of trial p: template, FP64 rows, FP32-emulated rows,
-    their fitness, and N_PERTURB perturbed evaluations with their fitness."""
+    their fitness, the per-row condition bound and the fitness bounds."""
     X = w["X"] if X is None else X
     y = w["y"] if y is None else y
     t = template(w, p)
     f64 = O.eval_tree(t, X)
     f32 = O.eval_tree_f32(t, X)
-    pert = []
-    if with_pert:
-        rng = np.random.default_rng(12345 + p)
-        pert = [O.eval_tree_perturbed(t, X, PERTURB_REL, rng) for _ in range(N_PERTURB)]
-    fits = [O.fitness(fp, y) for fp in pert]
-    return t, f64, f32, O.fitness(f64, y), O.fitness(f32.astype(np.float64), y), pert, fits
+    fit64 = O.fitness(f64, y)
+    cond = O.condition_bound(t, X, COND_REL)
+    bounds = fit_bounds(f64, y, fit64, cond) if fit64["finite"] else None
+    return t, f64, f32, fit64, O.fitness(f32.astype(np.float64), y), cond, bounds
 
 
 def intermediates_finite_f32(t, X):

@@ -1,0 +1,133 @@
+"""GPU parity of the reverse-mode adjoint (d fitness / d ERC) against the FP64
+oracle's reverse-mode gradient, plus the autograd wrapper and the Adam
+kernel.  Trials whose fitness is excluded as ill-conditioned or ambiguous,
+or whose FP32 evaluation overflows at an intermediate node, are skipped and
+counted."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_30954_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def grad_case(gg, w, mode="smse", sample=None):
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op, cv = dev(w["op"]), dev(w["cval"])
+    hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
+    flags = gg.F_GRAD_MSE if mode == "mse" else 0
+    smse, dc = ds.grad_batch(op, cv, hs, flags=flags)
+    ds.sync()
+    smse, dc = smse.cpu().numpy(), dc.cpu().numpy()
+    ds.close()
+    tally, fit_tally = PA.Tally(), PA.Tally()
+    var_y = float(np.var(w["y"].astype(np.float64)))
+    mean_y2 = float(np.mean(w["y"].astype(np.float64) ** 2))
+    idx = range(w["P"]) if sample is None else sample
+    for p in idx:
+        t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
+        before = fit_tally.excluded
+        PA.check_fit(float(smse[p]), None, fit64, fit32, var_y, mean_y2, fit_tally,
+                     tag=f"trial {p}", bounds=bounds)
+        if fit_tally.excluded != before or not PA.intermediates_finite_f32(t, w["X"]):
+            tally.excluded += 1
+            continue
+        g64, _ = O.grad(t, w["X"], w["y"], mode)
+        if not fit64["finite"] or (mode == "smse" and fit64["b"] == 0.0):
+            assert np.all(dc[p] == 0.0), p
+            tally.checked += 1
+            continue
+        PA.check_grad(dc[p], g64, tally, tag=f"trial {p}")
+    return tally, fit_tally
+
+
+@pytest.mark.parametrize("mode", ["smse", "mse"])
+def test_adjoint_small_c4(gg, mode):
+    w = PA.build("c4", 2500, 48)
+    t, tf = grad_case(gg, w, mode)
+    assert t.failed == 0 and tf.failed == 0, (repr(t), repr(tf))
+    assert t.checked >= 24, repr(t)
+
+
+@pytest.mark.parametrize("cfg,n_rows,n_trials", [("c2", 3000, 40), ("c3", 2100, 32),
+                                                  ("c1", 1000, 64)])
+def test_adjoint_other_shapes(gg, cfg, n_rows, n_trials):
+    w = PA.build(cfg, n_rows, n_trials)
+    t, tf = grad_case(gg, w)
+    assert t.failed == 0 and tf.failed == 0, (repr(t), repr(tf))
+    assert t.checked >= n_trials // 3, repr(t)
+
+
+def test_adjoint_full_size_c4_sampled(gg):
+    w = PA.build("c4")
+    sample = np.random.default_rng(3).choice(w["P"], 16, replace=False).tolist()
+    t, tf = grad_case(gg, w, sample=sample)
+    assert t.failed == 0 and tf.failed == 0, (repr(t), repr(tf))
+    assert t.checked >= 8, repr(t)
+
+
+def test_autograd_function_and_adam(gg):
+    w = PA.build("c4", 3000, 32)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op = dev(w["op"])
+    cv = dev(w["cval"]).requires_grad_(True)
+    smse = gg.ScaledMSE.apply(cv, op, ds)
+    smse_ref, dc_ref = ds.grad_batch(op, cv.detach().clone())
+    fin = torch.isfinite(smse)
+    (smse[fin] * 2.0).sum().backward()
+    torch.cuda.synchronize()
+    assert torch.equal(smse, smse_ref)
+    g = cv.grad.clone()
+    assert torch.allclose(g[fin], 2.0 * dc_ref[fin])
+    # Adam kernel vs the textbook update on the same gradient
+    c = dev(w["cval"])
+    m = torch.zeros_like(c)
+    v = torch.zeros_like(c)
+    cn, mn, vn = (x.cpu().numpy().astype(np.float64) for x in (c, m, v))
+    gn = dc_ref.cpu().numpy().astype(np.float64)
+    erc = w["op"] == synth.ERC
+    for t in (1, 2, 3):
+        gg.adam_step(op, c, dc_ref, m, v, t, lr=0.05)
+        mn = np.where(erc, 0.9 * mn + 0.1 * gn, mn)
+        vn = np.where(erc, 0.999 * vn + 0.001 * gn * gn, vn)
+        step = 0.05 * (mn / (1 - 0.9 ** t)) / (np.sqrt(vn / (1 - 0.999 ** t)) + 1e-8)
+        cn = np.where(erc, cn - step, cn)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(c.cpu().numpy(), cn, rtol=1e-5, atol=1e-6)
+    ds.close()
+
+
+def test_constant_tuning_reduces_fitness(gg):
+    w = PA.build("c4", 5000, 64)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op = dev(w["op"])
+    c = dev(w["cval"])
+    m, v = torch.zeros_like(c), torch.zeros_like(c)
+    s0 = ds.eval_batch(op, c)[0].clone()
+    for t in range(1, 21):
+        _, g = ds.grad_batch(op, c)
+        g = torch.nan_to_num(g, nan=0.0, posinf=0.0, neginf=0.0)
+        gg.adam_step(op, c, g, m, v, t, lr=0.05)
+    s1 = ds.eval_batch(op, c)[0]
+    ds.sync()
+    fin = torch.isfinite(s0) & torch.isfinite(s1)
+    improved = (s1[fin] <= s0[fin] * (1 + 1e-6)).float().mean().item()
+    assert improved >= 0.8, improved
+    assert (s1[fin] < s0[fin] * 0.999).sum().item() >= 4
+    ds.close()

@@ -47,11 +47,11 @@ def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0):
     var_y = float(np.var(w["y"].astype(np.float64)))
     mean_y2 = float(np.mean(w["y"].astype(np.float64) ** 2))
     for p in idx:
-        t, f64, f32, fit64, fit32, pert, fits = PA.oracle_trial(w, p)
+        t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
         if rows is not None:
-            PA.check_rows(rows[p], f64, f32, tr, tag=f"trial {p}", pert=pert)
+            PA.check_rows(rows[p], f64, f32, tr, tag=f"trial {p}", cond=cond)
         PA.check_fit(float(smse[p]), float(mse[p]), fit64, fit32, var_y, mean_y2, tf,
-                     tag=f"trial {p}", fits_pert=fits)
+                     tag=f"trial {p}", bounds=bounds)
     ds.close()
     return tr, tf, (smse, a, b, mse)
 

@@ -326,6 +326,25 @@ def test_perturbed_evaluation_bounds():
     assert np.median(spread) > 1e-2
 
 
+def test_condition_bound_closed_forms():
+    rng, X = rand_xy(13)
+    rel = 1e-6
+    # one multiplication: the bound is rel * |x0 x1|
+    t = T(["*", "x0", "x1"], 1)
+    np.testing.assert_allclose(O.condition_bound(t, X, rel), rel * np.abs(X[:, 0] * X[:, 1]),
+                               rtol=1e-12)
+    # exp(x0 * x1): errors at the product are amplified by |x0 x1|
+    t = T(["exp", "*", None, "x0", "x1"], 2)
+    e = np.exp(X[:, 0] * X[:, 1])
+    np.testing.assert_allclose(O.condition_bound(t, X, rel),
+                               rel * (e + e * np.abs(X[:, 0] * X[:, 1])), rtol=1e-12)
+    # sin(c x0): slope bound 1 at the sin node, so the product's size counts fully
+    t = T(["sin", "*", None, "300", "x0"], 2)
+    np.testing.assert_allclose(O.condition_bound(t, X, rel),
+                               rel * (np.abs(np.sin(300 * X[:, 0])) + 300 * np.abs(X[:, 0])),
+                               rtol=1e-12)
+
+
 def test_eval_batch_matches_single():
     rng, X = rand_xy(11)
     y = X[:, 0] * 2
