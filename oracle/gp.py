@@ -345,7 +345,7 @@ def _dapply(o, a, b, out):
     raise InvalidTemplate(o)
 
 
-def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse"):
+def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs: bool = False):
     """Reverse-mode FP64 gradient of smse (or mse) with respect to the
     constant of every active ERC node; 0 at every other template position.
 
@@ -354,19 +354,23 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse"):
         d smse / d c_k = (2 b*/N) sum_i (a* + b* f_i - y_i) d f_i / d c_k.
     For mse: (2/N) sum_i (f_i - y_i) d f_i / d c_k.  READING: the gradient
     is 0 for trials with infinite fitness and (smse) for b* = 0.
-    Returns (gradient float64 [stride], fitness dict)."""
+    Returns (gradient float64 [stride], fitness dict); with ``with_abs``
+    also the sum over rows of the absolute row contributions to each
+    gradient entry (the scale FP32 accumulation errors are relative to)."""
     X = np.asarray(X)
     y = np.asarray(y, dtype=np.float64)
     vals = {}
     f = _eval(t, X, np.float64, store=vals)
     fit = fitness(f, y)
     g = np.zeros(t.op.size, dtype=np.float64)
+    gabs = np.zeros(t.op.size, dtype=np.float64)
     n = f.size
+    out = (lambda: (g, fit, gabs)) if with_abs else (lambda: (g, fit))
     if not fit["finite"]:
-        return g, fit
+        return out()
     if mode == "smse":
         if fit["b"] == 0.0:
-            return g, fit
+            return out()
         seed = (2.0 / n) * fit["b"] * (fit["a"] + fit["b"] * f - y)
     elif mode == "mse":
         seed = (2.0 / n) * (f - y)
@@ -377,6 +381,7 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse"):
         o = int(t.op[pos])
         if o == ERC:
             g[pos] += float(np.sum(adj))
+            gabs[pos] += float(np.sum(np.abs(adj)))
             return
         if o >= FEAT0:
             return
@@ -391,7 +396,7 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse"):
 
     with np.errstate(all="ignore"):
         back(0, 0, seed)
-    return g, fit
+    return out()
 
 
 def fd_grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse",

@@ -160,9 +160,9 @@ CONFIGS = {
     "c3": dict(index=2, name="uneven-8192xh3to7-200000x10", P=8_192, h=7, h_min=3,
                funcs=FULL_SET, N=200_000, F=10, x=("uniform", -2.0, 2.0), y_h=5,
                y_funcs=FULL_SET, noise=0.0, fos=False, p_func_range=(0.2, 1.0)),
-    "c4": dict(index=3, name="diff-1024xh5-50000x6", P=1_024, h=5, funcs=FULL_SET,
+    "c4": dict(index=3, name="diff-1024xh5-50000x6", P=1_024, h=5, funcs=BASIC_SET,
                N=50_000, F=6, x=("normal",), y_h=5, y_funcs=FULL_SET, noise=0.0,
-               fos=False, erc_leaves=True),
+               fos=False, erc_leaves=True, p_func=0.9),
     "c5": dict(index=4, name="large-16384xh6-1000000x10", P=16_384, h=6, funcs=FULL_SET,
                N=1_000_000, F=10, x=("uniform", -1.0, 1.0), y_h=6, y_funcs=FULL_SET,
                noise=0.01, fos=True),
@@ -202,6 +202,8 @@ def workload(cfg: str, rep: int = 0, n_rows: int | None = None,
         heights = np.full(P, h_max)
     if "p_func_range" in c:
         p_func = r_t.uniform(c["p_func_range"][0], c["p_func_range"][1], P)
+    elif "p_func" in c:
+        p_func = np.full(P, c["p_func"])
     else:  # half "full" trees, half "grow" trees
         p_func = np.where(r_t.random(P) < 0.5, 1.0, 0.5)
     op, cval, heights = random_templates(

@@ -48,12 +48,12 @@ def grad_case(gg, w, mode="smse", sample=None):
         if fit_tally.excluded != before or not PA.intermediates_finite_f32(t, w["X"]):
             tally.excluded += 1
             continue
-        g64, _ = O.grad(t, w["X"], w["y"], mode)
+        g64, _, gabs = O.grad(t, w["X"], w["y"], mode, with_abs=True)
         if not fit64["finite"] or (mode == "smse" and fit64["b"] == 0.0):
             assert np.all(dc[p] == 0.0), p
             tally.checked += 1
             continue
-        PA.check_grad(dc[p], g64, tally, tag=f"trial {p}")
+        PA.check_grad(dc[p], g64, tally, tag=f"trial {p}", rabs=gabs)
     return tally, fit_tally
 
 
