@@ -355,8 +355,10 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs
     For mse: (2/N) sum_i (f_i - y_i) d f_i / d c_k.  READING: the gradient
     is 0 for trials with infinite fitness and (smse) for b* = 0.
     Returns (gradient float64 [stride], fitness dict); with ``with_abs``
-    also the sum over rows of the absolute row contributions to each
-    gradient entry (the scale FP32 accumulation errors are relative to)."""
+    also, per entry, sum_i s_i |d f_i / d c| with s_i = (2/N)|b*|(|a*| +
+    |b* f_i| + |y_i|) (smse) or (2/N)(|f_i| + |y_i|) (mse): the size of the
+    terms whose rounding in FP32 an FP32 gradient cannot avoid (the residual
+    a + b f - y is a difference of such terms)."""
     X = np.asarray(X)
     y = np.asarray(y, dtype=np.float64)
     vals = {}
@@ -372,30 +374,32 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs
         if fit["b"] == 0.0:
             return out()
         seed = (2.0 / n) * fit["b"] * (fit["a"] + fit["b"] * f - y)
+        scale = (2.0 / n) * abs(fit["b"]) * (abs(fit["a"]) + np.abs(fit["b"] * f) + np.abs(y))
     elif mode == "mse":
         seed = (2.0 / n) * (f - y)
+        scale = (2.0 / n) * (np.abs(f) + np.abs(y))
     else:
         raise ValueError(mode)
 
-    def back(pos, depth, adj):
+    def back(pos, depth, adj, aabs):
         o = int(t.op[pos])
         if o == ERC:
             g[pos] += float(np.sum(adj))
-            gabs[pos] += float(np.sum(np.abs(adj)))
+            gabs[pos] += float(np.sum(aabs))
             return
         if o >= FEAT0:
             return
         l, r = t.children(pos, depth)
         if o in BINARY:
             da, db = _dapply(o, vals[l], vals[r], vals[pos])
-            back(l, depth + 1, adj * da)
-            back(r, depth + 1, adj * db)
+            back(l, depth + 1, adj * da, aabs * np.abs(da))
+            back(r, depth + 1, adj * db, aabs * np.abs(db))
         else:
             da, _ = _dapply(o, vals[l], None, vals[pos])
-            back(l, depth + 1, adj * da)
+            back(l, depth + 1, adj * da, aabs * np.abs(da))
 
     with np.errstate(all="ignore"):
-        back(0, 0, seed)
+        back(0, 0, seed, scale)
     return out()
 
 

@@ -5,7 +5,8 @@ Tolerances (from the accuracy targets of this evaluator):
   per row   |g - r| <= 1e-5 (|r| + rms(r))      rms over the trial's rows
   smse      |g - r| <= 1e-4 r + 1e-8 Var(y)
   mse       |g - r| <= 1e-4 r + 1e-8 (mean y^2 + mean f^2)
-  gradient  |g - r| <= 1e-3 (|r| + 1e-3 max_k |r_k|) + 1e-5 sum_i |row term_i|
+  gradient  |g - r| <= 1e-3 (|r| + 1e-3 max_k |r_k|) + 1e-6 G_k, G_k the
+            oracle's scale of the FP32 row terms (oracle.grad with_abs)
 A row is ill-conditioned in FP32, and excluded, when its FP32-emulated
 oracle value or the first-order bound on the effect of relative errors of
 4 FP32 units in the last place at every function node
@@ -160,10 +161,10 @@ def intermediates_finite_f32(t, X):
         return all(np.all(np.isfinite(v)) for v in store.values())
 
 
-#: FP32 floor of the gradient test, relative to the sum of the absolute row
-#: contributions: a gradient that is 0 by an invariance (an ERC that only
-#: scales or shifts the output) is a cancelling FP32 sum of such terms
-GRAD_FLOOR = 1e-5
+#: FP32 floor of the gradient test, relative to the size of the terms the
+#: FP32 residual a + b f - y is made of: a gradient that is 0 (or small) by
+#: an invariance is a cancelling FP32 sum of such terms
+GRAD_FLOOR = 1e-6
 
 
 def check_grad(g, r, tally, tag="", rabs=None):
