@@ -232,6 +232,39 @@ ggeval_status ggeval_pack_host(const ggeval_batch* batch, int32_t index, int32_t
                                uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
                                int32_t* len);
 
+/* Evaluation that allocates nothing.  Some callers cannot call cudaMalloc
+ * while they evaluate: code running inside a CUDA stream capture (the
+ * allocator is not allowed there), latency-critical loops that cannot take
+ * the device-wide synchronisation cudaMalloc implies, and processes whose
+ * device memory is budgeted up front.  ggeval_eval_batch may grow its
+ * workspace on such a call; this entry point never does.  It computes the
+ * same outputs as ggeval_eval_batch (same definitions, same error rules)
+ * for a device batch on an existing dataset, using as scratch one static
+ * device array of GGEVAL_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until the process exits.  (The paper has no counterpart:
+ * it is a deployment form of the batched evaluation, not part of the
+ * method.)
+ *  - Limits: n <= GGEVAL_NOALLOC_MAX_TRIALS, max_height <=
+ *    GGEVAL_NOALLOC_MAX_HEIGHT, and the dataset's rows must fit in at most
+ *    GGEVAL_NOALLOC_MAX_TILES row tiles that fit in shared memory; larger
+ *    requests return GGEVAL_ERR_UNSUPPORTED with a message and launch
+ *    nothing.  Host-memory batches return GGEVAL_ERR_ARG.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  Later calls only launch kernels and one
+ *    memset, so they may be captured.
+ *  - Every call on a device shares the one array and it keeps the previous
+ *    call's contents (the call zeroes what must start at zero).  Calls whose
+ *    GPU work overlaps (different streams, or different datasets on the
+ *    same device without ordering) race on it: order them on one stream. */
+#define GGEVAL_NOALLOC_MAX_TRIALS 4096
+#define GGEVAL_NOALLOC_MAX_HEIGHT 6
+#define GGEVAL_NOALLOC_MAX_TILES 64
+#define GGEVAL_NOALLOC_SCRATCH_BYTES (4096u * 128u * 8u + 4096u * 4u + 4096u * 64u * 40u + 256u)
+ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const ggeval_batch* batch,
+                                        float* smse, float* a, float* b, float* mse,
+                                        void* stream);
+
 /* Library version string. */
 const char* ggeval_version(void);
 

@@ -899,3 +899,107 @@ ggeval_status ggeval_pack_host(const ggeval_batch* b, int32_t index, int32_t n_f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ggeval_eval_batch_noalloc: the batched evaluation with its scratch (packed
+// programs, instruction counts, per-tile partial sums, work counter) in one
+// file-scope device array instead of the dataset's growable workspace.
+namespace {
+constexpr size_t NA_PROG_BYTES =
+    (size_t)GGEVAL_NOALLOC_MAX_TRIALS * ((1u << (GGEVAL_NOALLOC_MAX_HEIGHT + 1)) * 8u);
+constexpr size_t NA_LEN_OFF = NA_PROG_BYTES;
+constexpr size_t NA_PART_OFF = NA_LEN_OFF + (size_t)GGEVAL_NOALLOC_MAX_TRIALS * 4u;
+constexpr size_t NA_CNT_OFF =
+    NA_PART_OFF + (size_t)GGEVAL_NOALLOC_MAX_TRIALS * GGEVAL_NOALLOC_MAX_TILES * gg::NPART * 8u;
+constexpr size_t NA_BYTES = NA_CNT_OFF + 256u;
+static_assert(NA_BYTES == GGEVAL_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
+static_assert(NA_LEN_OFF % 256 == 0 && NA_PART_OFF % 256 == 0 && NA_CNT_OFF % 256 == 0,
+              "scratch sub-arrays must stay aligned");
+}  // namespace
+
+// The scratch itself.  In host code this name is only a host-side stand-in
+// for the device array: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+namespace {
+// device address of g_noalloc_scratch, looked up once per device
+ggeval_status noalloc_scratch(int device, unsigned char** out) {
+  static std::mutex mu;
+  static std::map<int, unsigned char*> addr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = addr.find(device);
+  if (it != addr.end()) {
+    *out = it->second;
+    return GGEVAL_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(GGEVAL_ERR_CUDA, "cudaGetSymbolAddress(noalloc scratch): %s",
+                cudaGetErrorString(e));
+  addr[device] = static_cast<unsigned char*>(p);
+  *out = static_cast<unsigned char*>(p);
+  return GGEVAL_OK;
+}
+}  // namespace
+
+extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const ggeval_batch* b,
+                                                   float* smse, float* a, float* bb, float* mse,
+                                                   void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->memory != GGEVAL_MEM_DEVICE)
+    return fail(GGEVAL_ERR_ARG, "eval_batch_noalloc needs a device batch");
+  if (b->n > GGEVAL_NOALLOC_MAX_TRIALS)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "eval_batch_noalloc: %d trials > the static limit %d",
+                b->n, GGEVAL_NOALLOC_MAX_TRIALS);
+  if (b->max_height > GGEVAL_NOALLOC_MAX_HEIGHT)
+    return fail(GGEVAL_ERR_UNSUPPORTED, "eval_batch_noalloc: max_height %d > the static limit %d",
+                b->max_height, GGEVAL_NOALLOC_MAX_HEIGHT);
+  if (b->n == 0) return GGEVAL_OK;
+  if (!smse) return fail(GGEVAL_ERR_ARG, "smse is NULL");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  GG_TRY(noalloc_scratch(ds->device, &base));
+  Cfg c = default_cfg(ds, b->n, b->max_height, 0);
+  while ((ds->N + c.tile_rows - 1) / c.tile_rows > GGEVAL_NOALLOC_MAX_TILES) c.tile_rows *= 2;
+  Plan pl;
+  if (make_plan(ds, b->n, b->max_height, c, &pl) != GGEVAL_OK)
+    return fail(GGEVAL_ERR_UNSUPPORTED,
+                "eval_batch_noalloc: %lld rows need tiles of %d rows, which do not fit in "
+                "shared memory (at most %d tiles)",
+                (long long)ds->N, c.tile_rows, GGEVAL_NOALLOC_MAX_TILES);
+  uint2* prog = reinterpret_cast<uint2*>(base);
+  int* len = reinterpret_cast<int*>(base + NA_LEN_OFF);
+  double* part = reinterpret_cast<double*>(base + NA_PART_OFF);
+  int* counter = reinterpret_cast<int*>(base + NA_CNT_OFF);
+  gg::PackParams pp;
+  pp.op = b->op;
+  pp.cval = b->cval;
+  pp.height = b->height;
+  pp.n = b->n;
+  pp.h_max = b->max_height;
+  pp.stride = pl.stride;
+  pp.layout = b->layout;
+  pp.n_features = ds->F;
+  pp.max_slots = pl.dmax;
+  pp.lstride = pl.lstride;
+  pp.prog = prog;
+  pp.aux = nullptr;
+  pp.len = len;
+  pp.status = ds->status;
+  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + 127) / 128), dim3(128), 0, st, &pp));
+  GG_CU(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  gg::FwdParams fp = fwd_params(ds, b->n, pl);
+  fp.prog = prog;
+  fp.len = len;
+  fp.part = part;
+  fp.counter = counter;
+  GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+  gg::FinParams q = fin_params(ds, b->n, pl, smse, a, bb, mse);
+  q.part = part;
+  q.len = len;
+  q.ab = nullptr;
+  GG_TRY(launch(gg::fin_ptr(), dim3((b->n + 127) / 128), dim3(128), 0, st, &q));
+  return GGEVAL_OK;
+}

@@ -27,7 +27,7 @@ MAX_HEIGHT = 8
 SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggeval_eval_rows",
            "ggeval_eval_plain", "ggeval_grad_batch", "ggeval_adam_step", "ggeval_autotune",
            "ggeval_sync", "ggeval_last_error", "ggeval_batch_stats", "ggeval_pack_host",
-           "ggeval_version", "ggeval_profile_read")
+           "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc")
 
 
 class GGEvalError(RuntimeError):
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
         "ggeval_pack_host": [bp, i32, i32, vp, vp, vp, i32, vp],
         "ggeval_version": [],
         "ggeval_profile_read": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
+        "ggeval_eval_batch_noalloc": [vp, bp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
