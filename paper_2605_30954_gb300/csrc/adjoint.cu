@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       const int row = rb + lane;
       const bool valid = row < r_end;
       const int rr = valid ? row : r_end - 1;
-      float A[1];
+      float A[1] = {0.f};
       run_program<DMAX, 1, true>(wprog, L, p.X + rr, p.ldx, A, S, tape + lane);
       const float f = A[0];
       const float yc = p.X[(size_t)p.F * p.ldx + rr];

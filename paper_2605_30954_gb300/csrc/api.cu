@@ -58,6 +58,12 @@ struct DeviceGuard {
 };
 
 inline int stride_of(int h) { return (1 << (h + 1)) - 1; }
+// threads per block of the packing kernel: each thread keeps 2 x stride
+// bytes of scratch in shared memory, within the 48 KB default
+inline int pack_threads(int stride) {
+  int t = (49152 / (2 * stride)) & ~31;
+  return t < 32 ? 32 : (t > 128 ? 128 : t);
+}
 inline int dmax_of(int h) { return h <= 4 ? 3 : (h <= 6 ? 5 : 7); }
 inline int lstride_of(int h) { return stride_of(h) + 1; }
 
@@ -315,7 +321,9 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.aux = with_aux ? ds->aux : nullptr;
   pp.len = ds->len;
   pp.status = ds->status;
-  return launch(gg::pack_ptr(), dim3((n + 127) / 128), dim3(128), 0, st, &pp);
+  const int pt = pack_threads(pl.stride);
+  return launch(gg::pack_ptr(), dim3((n + pt - 1) / pt), dim3(pt), (size_t)pt * 2 * pl.stride, st,
+                &pp);
 }
 
 gg::FwdParams fwd_params(ggeval_dataset* ds, int n, const Plan& pl) {
@@ -384,7 +392,7 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
-  GG_TRY(launch(gg::fin_ptr(), dim3((n + 127) / 128), dim3(128), 0, st, &q));
+  GG_TRY(launch(gg::fin_ptr(), dim3((n + 3) / 4), dim3(128), 0, st, &q));
   return GGEVAL_OK;
 }
 
@@ -619,9 +627,12 @@ ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint3
   if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "plain form needs a device batch");
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // one trial per launch: tiles only over rows
+  // one trial per launch: tiles only over rows, one pass per tile, two warps
+  // per CTA (one per tile buffer)
   Cfg c = default_cfg(ds, 1, b->max_height, flags);
   c.group = 1;
+  c.warps = 2;
+  c.tile_rows = 32 * gg::variant_rows(c.variant);
   Plan pl;
   GG_TRY(make_plan(ds, 1, b->max_height, c, &pl));
   GG_TRY(ensure_ws(ds, b->n, pl, false));
@@ -640,7 +651,7 @@ ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint3
     q.part = fp.part;
     q.len = fp.len;
     q.ab = nullptr;
-    GG_TRY(launch(gg::fin_ptr(), dim3(1), dim3(32), 0, st, &q));
+    GG_TRY(launch(gg::fin_ptr(), dim3(1), dim3(32), 0, st, &q));  // one warp, one trial
   }
   return GGEVAL_OK;
 }
@@ -848,6 +859,7 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
   const int stride = stride_of(b->max_height);
   std::vector<uint32_t> w(stride + 1);
   std::vector<float> c(stride + 1);
+  std::vector<uint8_t> d1(stride), nd(stride);
   for (int t = 0; t < b->n; ++t) {
     const int h = b->height ? b->height[t] : b->max_height;
     int64_t* o = out + (size_t)t * GGEVAL_NSTAT;
@@ -858,7 +870,8 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
     }
     const gg::PackResult r =
         gg::pack_tree(b->op + (size_t)t * stride, b->cval + (size_t)t * stride, h, b->layout,
-                      n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, nullptr, stride);
+                      n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, nullptr, stride,
+                      d1.data(), nd.data());
     if (r.status) {
       o[0] = -1;
       continue;
@@ -885,9 +898,11 @@ ggeval_status ggeval_pack_host(const ggeval_batch* b, int32_t index, int32_t n_f
   std::vector<uint32_t> w(stride + 1);
   std::vector<float> c(stride + 1);
   std::vector<gg::Aux> ax(stride + 1);
+  std::vector<uint8_t> d1(stride), nd(stride);
   const gg::PackResult r =
       gg::pack_tree(b->op + (size_t)index * stride, b->cval + (size_t)index * stride, h, b->layout,
-                    n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, ax.data(), stride);
+                    n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, ax.data(), stride,
+                    d1.data(), nd.data());
   if (r.status) return fail(GGEVAL_ERR_TEMPLATE, "trial %d: invalid template", index);
   for (int k = 0; k < r.len; ++k) {
     words[k] = w[k];
@@ -988,7 +1003,9 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   pp.aux = nullptr;
   pp.len = len;
   pp.status = ds->status;
-  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + 127) / 128), dim3(128), 0, st, &pp));
+  const int pt = pack_threads(pl.stride);
+  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + pt - 1) / pt), dim3(pt), (size_t)pt * 2 * pl.stride,
+                st, &pp));
   GG_CU(cudaMemsetAsync(counter, 0, sizeof(int), st));
   gg::FwdParams fp = fwd_params(ds, b->n, pl);
   fp.prog = prog;
@@ -1000,6 +1017,6 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   q.part = part;
   q.len = len;
   q.ab = nullptr;
-  GG_TRY(launch(gg::fin_ptr(), dim3((b->n + 127) / 128), dim3(128), 0, st, &q));
+  GG_TRY(launch(gg::fin_ptr(), dim3((b->n + 3) / 4), dim3(128), 0, st, &q));
   return GGEVAL_OK;
 }

@@ -67,25 +67,24 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v
 // same individual, avoiding divergence).  The slot operand of each
 // instruction is part of its opcode, so S[] is indexed with constants and
 // stays in registers.
-// S is the caller's slot file (kept in registers across calls); the first
-// instruction of every program is a push into A.
-// With TAPE (R == 1 only) the value of A after instruction k is stored at
-// tape[32 k] (the caller offsets `tape` by its lane): the forward half of
-// the adjoint.
-template <int DMAX, int R, bool TAPE = false>
+// A and S are the caller's registers (initialised once, kept across calls);
+// the first instruction of every program is a push into A.  With PRESCALED
+// the feature field of each word already holds the feature's offset in
+// floats (feature x ts), as the batched kernel rewrites it when it stages a
+// program.  With TAPE (R == 1 only) the value of A after instruction k is
+// stored at tape[32 k] (the caller offsets `tape` by its lane): the forward
+// half of the adjoint.
+template <int DMAX, int R, bool TAPE = false, bool PRESCALED = false>
 __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
                                             const float* __restrict__ xs, int ts,
                                             float (&A)[R], float (&S)[DMAX][R],
                                             float* __restrict__ tape = nullptr) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) A[r] = 0.f;
-
   uint2 ins = prog[0];
   for (int k = 0; k < L; ++k) {
     const uint2 nxt = prog[k + 1];
     const uint32_t opc = ins.x & 0xffu;
     const float c = __uint_as_float(ins.y);
-    const float* xf = xs + (ins.x >> 8) * ts;
+    const float* xf = PRESCALED ? xs + (ins.x >> 8) : xs + (ins.x >> 8) * ts;
     float t[R];
 
 #define GG_ROWS _Pragma("unroll") for (int r = 0; r < R; ++r)
@@ -175,8 +174,8 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
       GG_PUSH(5)
       GG_PUSH(6)
       GG_PUSH(7)
-      default:
-        break;
+      default:  // the packer emits only the opcodes above
+        __builtin_unreachable();
     }
 #undef GG_ROWS
 #undef GG_UN

@@ -130,17 +130,19 @@ GG_HD void children(int layout, int h, int pos, int depth, int* l, int* r) {
 // either layout), pass 3 emits the program by an explicit-stack post-order
 // walk.  words/consts have room for cap+1 entries at stride `ws`; entry
 // [len] is set to NOP so the interpreter may prefetch one instruction ahead.
+// `depth1` and `need` are caller scratch of at least 2^(h+1)-1 bytes each
+// (shared memory in the packing kernel).
 GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layout,
                            int n_features, int max_slots, uint32_t* words, float* consts,
-                           int ws, Aux* aux, int cap) {
+                           int ws, Aux* aux, int cap, uint8_t* depth1, uint8_t* need) {
   PackResult res;
   res.len = 0;
   res.slots = 0;
   res.status = 0;
   for (int i = 0; i < 10; ++i) res.counts[i] = 0;
   const int n = (1 << (h + 1)) - 1;
-  uint8_t depth1[MAX_NODES];  // depth + 1 of active nodes, 0 = intron
-  uint8_t need[MAX_NODES];    // slots needed by the active subtree
+  // depth1[i]: depth + 1 of an active node, 0 for an intron;
+  // need[i]: slots the active subtree at i needs
   for (int i = 0; i < n; ++i) depth1[i] = 0;
   depth1[0] = 1;
   // pass 1: active set + validation (Section 3.1 / Fig. 1)

@@ -51,8 +51,10 @@ struct FwdParams {
 
 constexpr int NPART = 5;
 
+// two tile buffers, one program buffer per warp, two mbarriers, two
+// 4-int control blocks
 __host__ __device__ inline size_t fwd_smem_bytes(int F, int tile_rows, int warps, int lstride) {
-  return (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * lstride * 8 + 16;
+  return 2 * (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * lstride * 8 + 16 + 32;
 }
 
 template <int R, bool MASK>
@@ -103,79 +105,118 @@ __device__ __forceinline__ void accumulate_pairwise(const float (&A)[R], const f
   acc_add(s3h, s3l, c[0]);
 }
 
+// Claim the next work item for tile buffer `s` and start loading it: run by
+// one whole warp.  The X tile and the centred target rows go to shared
+// memory with one TMA bulk copy per feature row, completing on bar[s]; a
+// ragged last tile has its tail zeroed first.  Past the last item the
+// barrier is completed without a copy so that waiting warps see the end.
+__device__ __forceinline__ void produce_tile(const FwdParams& p, int s, float* xs, uint64_t* bar,
+                                             int* ctl, int lane) {
+  int item = 0;
+  if (lane == 0) item = atomicAdd(p.counter, 1);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  if (item < p.n_items) {
+    const int tile = item % p.n_tiles;
+    const int row0 = tile * p.tile_rows;
+    const int nrows = min(p.tile_rows, p.N - row0);
+    const int ncopy = (nrows + 3) & ~3;
+    if (ncopy < p.tile_rows) {
+      const int tail = p.tile_rows - ncopy;
+      for (int i = lane; i < (p.F + 1) * tail; i += 32) {
+        const int f = i / tail;
+        xs[(size_t)f * p.tile_rows + ncopy + (i - f * tail)] = 0.f;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      ctl[0] = item;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, (uint32_t)((p.F + 1) * ncopy * 4));
+      for (int f = 0; f <= p.F; ++f)
+        bulk_g2s(xs + (size_t)f * p.tile_rows, p.X + (size_t)f * p.ldx + row0,
+                 (uint32_t)(ncopy * 4), bar);
+    }
+  } else if (lane == 0) {
+    ctl[0] = item;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+  }
+}
+
+// Two tile buffers form a pipeline: while the warps work on one tile, the
+// other is being loaded.  Each buffer s has a control block ctl[4 s ..]:
+// [0] its work item, [1] the next trial of the item's group to hand out,
+// [2] how many warps are done with it.  The warp that finishes a buffer
+// last resets [1], [2] and refills the buffer with the next item; no warp
+// ever waits for the others except for the tile it is about to use.
 template <int DMAX, int R, bool EXACT, bool ROWS>
 __global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  float* xs = reinterpret_cast<float*>(smem);
-  uint2* wprog = reinterpret_cast<uint2*>(xs + (size_t)(p.F + 1) * p.tile_rows) +
-                 (size_t)warp * p.lstride;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint2*>(
-                      xs + (size_t)(p.F + 1) * p.tile_rows) + (size_t)nw * p.lstride);
-  int* ctl = reinterpret_cast<int*>(bar + 1);
+  const size_t tile_floats = (size_t)(p.F + 1) * p.tile_rows;
+  float* xsb = reinterpret_cast<float*>(smem);  // two tile buffers
+  uint2* wprog = reinterpret_cast<uint2*>(xsb + 2 * tile_floats) + (size_t)warp * p.lstride;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint2*>(xsb + 2 * tile_floats) +
+                                              (size_t)nw * p.lstride);
+  int* ctl = reinterpret_cast<int*>(bar + 2);
 
-  if (threadIdx.x == 0) mbar_init(bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    for (int i = 0; i < 8; ++i) ctl[i] = 0;
+  }
   __syncthreads();
+  if (warp == 0) {
+    produce_tile(p, 0, xsb, &bar[0], ctl, lane);
+    produce_tile(p, 1, xsb + tile_floats, &bar[1], ctl + 4, lane);
+  }
 
   float S[DMAX][R];
+  float A[R];
 #pragma unroll
-  for (int j = 0; j < DMAX; ++j)
+  for (int r = 0; r < R; ++r) {
+    A[r] = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) S[j][r] = 0.f;
+    for (int j = 0; j < DMAX; ++j) S[j][r] = 0.f;
+  }
 
   constexpr int RPP = 32 * R;  // rows per pass of a warp
-  uint32_t parity = 0;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      ctl[0] = atomicAdd(p.counter, 1);
-      ctl[1] = 0;
-    }
-    __syncthreads();
-    const int item = ctl[0];
+  uint32_t parity = 0;         // bit s: phase parity of bar[s] this warp waits for next
+  for (int s = 0;; s ^= 1) {
+    if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u, p.status, WAIT_LIMIT)) return;
+    parity ^= 1u << s;
+    int* c = ctl + 4 * s;
+    const int item = *reinterpret_cast<volatile int*>(&c[0]);
     if (item >= p.n_items) break;
+    const float* xs = xsb + s * tile_floats;
     const int g = item / p.n_tiles;
     const int tile = item - g * p.n_tiles;
     const int row0 = tile * p.tile_rows;
     const int nrows = min(p.tile_rows, p.N - row0);
-    const int ncopy = (nrows + 3) & ~3;
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, (uint32_t)((p.F + 1) * ncopy * 4));
-      for (int f = 0; f <= p.F; ++f)
-        bulk_g2s(xs + (size_t)f * p.tile_rows, p.X + (size_t)f * p.ldx + row0,
-                 (uint32_t)(ncopy * 4), bar);
-    }
-    if (ncopy < p.tile_rows) {  // zero the tail of a ragged tile
-      const int tail = p.tile_rows - ncopy;
-      for (int i = threadIdx.x; i < (p.F + 1) * tail; i += blockDim.x) {
-        const int f = i / tail;
-        xs[(size_t)f * p.tile_rows + ncopy + (i - f * tail)] = 0.f;
-      }
-    }
-    const bool ok = mbar_wait_bounded(bar, parity, p.status, WAIT_LIMIT);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) return;
-
     const int npass = (nrows + RPP - 1) / RPP;
     for (;;) {
       int t = 0;
-      if (lane == 0) t = atomicAdd(&ctl[1], 1);
+      if (lane == 0) t = atomicAdd(&c[1], 1);
       t = __shfl_sync(0xffffffffu, t, 0);
       const int trial = g * p.group + t;
       if (t >= p.group || trial >= p.P) break;
       const int L = p.len[trial];
       if (L <= 0) continue;
+      // stage the program with each feature field scaled to its tile offset
       const uint2* src = p.prog + (size_t)trial * p.lstride;
-      for (int k = lane; k <= L; k += 32) wprog[k] = src[k];
+      for (int k = lane; k <= L; k += 32) {
+        uint2 w = src[k];
+        w.x = (w.x & 0xffu) | (((w.x >> 8) * (uint32_t)p.tile_rows) << 8);
+        wprog[k] = w;
+      }
       __syncwarp();
 
       float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
-        float A[R];
-        run_program<DMAX, R>(wprog, L, xs + r0, p.tile_rows, A, S);
+        run_program<DMAX, R, false, true>(wprog, L, xs + r0, p.tile_rows, A, S);
         const int valid = nrows - r0;  // rows of this lane inside the tile
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
@@ -184,20 +225,20 @@ __global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
             if (r < valid) out[r] = A[r];
         }
         if (ps == 0) {  // shift: mean of f over the first pass's rows
-          float s = 0.f;
+          float sm = 0.f;
           int cnt = 0;
 #pragma unroll
           for (int r = 0; r < R; ++r)
             if (r < valid) {
-              s += A[r];
+              sm += A[r];
               ++cnt;
             }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
           }
-          cs = s / (float)cnt;
+          cs = sm / (float)cnt;
         }
         float yv[R];
         load_rows<R>(xs + (size_t)p.F * p.tile_rows + r0, yv);
@@ -229,7 +270,19 @@ __global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
       }
       __syncwarp();
     }
-    __syncthreads();
+    // this warp is done with buffer s; the last one refills it
+    __threadfence_block();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&c[2], 1) == nw - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      if (lane == 0) {
+        c[1] = 0;
+        c[2] = 0;
+      }
+      __syncwarp();
+      produce_tile(p, s, xsb + s * tile_floats, &bar[s], c, lane);
+    }
   }
 }
 

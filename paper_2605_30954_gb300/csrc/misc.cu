@@ -6,8 +6,11 @@ namespace gg {
 
 // One thread per trial: linearise its template (Section 3.2, Fig. 1).
 __global__ void pack_kernel(const PackParams p) {
+  extern __shared__ unsigned char pk_smem[];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.n) return;
+  uint8_t* depth1 = pk_smem + (size_t)threadIdx.x * 2 * p.stride;
+  uint8_t* need = depth1 + p.stride;
   const int h = p.height ? (int)p.height[t] : p.h_max;
   uint2* prog = p.prog + (size_t)t * p.lstride;
   int L = -1;
@@ -17,7 +20,7 @@ __global__ void pack_kernel(const PackParams p) {
                                    reinterpret_cast<uint32_t*>(prog),
                                    reinterpret_cast<float*>(prog) + 1, 2,
                                    p.aux ? p.aux + (size_t)t * p.lstride : nullptr,
-                                   p.lstride - 1);
+                                   p.lstride - 1, depth1, need);
     if (r.status == 0) L = r.len;
   }
   p.len[t] = L;
@@ -26,18 +29,22 @@ __global__ void pack_kernel(const PackParams p) {
 
 
 __global__ void fin_kernel(const FinParams p) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (t >= p.P) return;
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
   double smse, a, b, mse, ac = 0.0, bo = 0.0;
-  if (p.len[t] <= 0) {
+  const bool valid = p.len[t] > 0;
+  if (!valid) {
     smse = a = b = mse = nan;
   } else {
+    // lanes take tiles lane, lane + 32, ...; the shuffle tree below fixes
+    // the summation order, so the result is deterministic
     const double* q = p.part + (size_t)t * p.n_tiles * NPART;
     const double cst = q[0];
     double sd = 0.0, sdd = 0.0, sdy = 0.0, fm = 0.0;
-    for (int i = 0; i < p.n_tiles; ++i) {
+    for (int i = lane; i < p.n_tiles; i += 32) {
       const double* u = q + (size_t)i * NPART;
       const long long r0 = (long long)i * p.tile_rows;
       const long long r1 = min(p.N, r0 + p.tile_rows);
@@ -48,6 +55,13 @@ __global__ void fin_kernel(const FinParams p) {
       sdd += u[2] + 2.0 * del * u[1] + n * del * del;
       sdy += u[3] + del * syt;
       fm = fmax(fm, u[4]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+      sdd += __shfl_xor_sync(0xffffffffu, sdd, o);
+      sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
+      fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
     }
     const double N = (double)p.N;
     const bool finite = isfinite(sd) && isfinite(sdd) && isfinite(sdy) && isfinite(cst) &&
@@ -69,6 +83,7 @@ __global__ void fin_kernel(const FinParams p) {
       bo = b;
     }
   }
+  if (lane != 0) return;
   if (p.smse) p.smse[t] = (float)smse;
   if (p.a) p.a[t] = (float)a;
   if (p.b) p.b[t] = (float)b;
@@ -76,7 +91,7 @@ __global__ void fin_kernel(const FinParams p) {
   if (p.ab) {
     p.ab[4 * t] = ac;
     p.ab[4 * t + 1] = bo;
-    p.ab[4 * t + 2] = (p.len[t] > 0 && isfinite(smse)) ? 1.0 : 0.0;
+    p.ab[4 * t + 2] = (valid && isfinite(smse)) ? 1.0 : 0.0;
     p.ab[4 * t + 3] = 0.0;
   }
 }
