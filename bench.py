@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="eval", choices=["eval", "grad", "sweep"],
+                    help="eval: one batched FOS-step evaluation per step (the headline); "
+                         "grad: fitness + adjoint + one Adam step per step; "
+                         "sweep: a whole FOS sweep on the device per step")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -125,10 +129,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(step_ms_total, steps, nodes, trials, rows, allreduce, ops):
+    """Whole-job numbers over all ranks: the step time is the MAX over ranks
+    (the slowest rank bounds the job), the work is the SUM (every rank
+    evaluates its own FOS step of trials; no data moves between ranks)."""
+    t_max = allreduce(float(step_ms_total), ops["max"])
+    n_sum = allreduce(float(nodes), ops["sum"])
+    p_sum = allreduce(float(trials), ops["sum"])
+    ms = t_max / steps
+    return {"ms_per_step": ms, "node_row_evals_per_s": n_sum * rows / (ms * 1e-3),
+            "trial_evals_per_s": p_sum / (ms * 1e-3), "nodes": n_sum, "trials": p_sum}
+
+
 def make_workload(cfg, rep, gg, torch, device):
     """Seeded workload; the target comes from the library's own per-row
     evaluation of the first usable generator tree."""
     w = synth.workload(cfg, rep)
+    if "y" in w:  # a closed-form target
+        return w
     X = torch.from_numpy(w["X"])
     dummy = torch.zeros(w["N"], dtype=torch.float32)
     probe = gg.Dataset(X, dummy, device=device)
@@ -230,10 +248,118 @@ def run_reference(a):
     }))
 
 
+def fos_csr(stride):
+    """One FOS subset per template node: the node and its children."""
+    subsets = [[i] + [c for c in (2 * i + 1, 2 * i + 2) if c < stride] for i in range(stride)]
+    off = np.cumsum([0] + [len(x) for x in subsets]).astype(np.int32)
+    return off, np.concatenate(subsets).astype(np.int32)
+
+
+def run_extra_mode(a, gg, torch):
+    """--mode grad / sweep on one GPU (documentation lines, not the headline)."""
+    dev = 0
+    torch.cuda.set_device(dev)
+    w = make_workload(a.config, 0, gg, torch, dev)
+    nodes, _, _, valid, _ = node_counts(gg, torch, w)
+    N, P = w["N"], w["P"]
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
+    op = torch.from_numpy(w["op"]).cuda(dev)
+    cv = torch.from_numpy(w["cval"]).cuda(dev)
+    hs = torch.from_numpy(w["heights"]).cuda(dev) if "h_min" in synth.CONFIGS[a.config] else None
+    ds.autotune(op, cv, hs)
+    st = torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "trials_per_step": P, "rows": N,
+                       "active_nodes": nodes, "mode": a.mode}}
+    if a.mode == "grad":
+        m = torch.zeros_like(cv)
+        v = torch.zeros_like(cv)
+        smse = torch.empty(P, device="cuda")
+        dc = torch.empty_like(cv)
+
+        def step(t):
+            ds.grad_batch(op, cv, hs, stream=st, smse=smse, dcval=dc)
+            gg.adam_step(op, cv, dc, m, v, t, lr=0.05, stream=st)
+        with torch.cuda.stream(st):
+            s0 = ds.eval_batch(op, cv, hs, stream=st)[0].clone()
+            for t in range(1, a.warmup + 1):
+                step(t)
+        st.synchronize()
+        e0, e1 = ev(), ev()
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for t in range(a.warmup + 1, a.warmup + 1 + a.steps):
+                step(t)
+            e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        s1 = ds.eval_batch(op, cv, hs)[0]
+        ds.sync()
+        fin = torch.isfinite(s0) & torch.isfinite(s1)
+        line.update(value=nodes * N / (ms * 1e-3), ms_per_step=ms,
+                    gradient_trial_evals_per_s=P / (ms * 1e-3),
+                    note="node-row evals of the forward pass; each step also runs the "
+                         "adjoint (forward recompute + reverse sweep) and one Adam step",
+                    tuning={"adam_steps": a.warmup + a.steps,
+                            "trials_improved": int((s1[fin] < s0[fin]).sum().item()),
+                            "median_smse_ratio": float((s1[fin & (s0 > 0)] / s0[fin & (s0 > 0)])
+                                                       .median().item())})
+    else:  # sweep
+        stride = op.shape[1]
+        off, fnodes = fos_csr(stride)
+        rng = np.random.default_rng(1)
+        order = torch.from_numpy(np.argsort(rng.random((stride, P)), axis=0).astype(np.int32)).cuda()
+        donors = torch.from_numpy(rng.integers(0, P, (stride, P)).astype(np.int32)).cuda()
+        off_d, nodes_d = torch.from_numpy(off).cuda(), torch.from_numpy(fnodes).cuda()
+        pop_op, pop_cv = op.clone(), cv.clone()
+        O_op, O_cv, B_op, B_cv = op.clone(), cv.clone(), op.clone(), cv.clone()
+        f_b = ds.eval_batch(O_op, O_cv, hs)[0].clone()
+        f_new = torch.empty(P, device="cuda")
+        changed_total = torch.zeros((), dtype=torch.int64, device="cuda")
+
+        def sweep():
+            for i in range(stride):
+                gg.gom_donate(O_op, O_cv, pop_op, pop_cv, donors[i], order[i], off_d, nodes_d,
+                              stream=st)
+                ch = gg.gom_changed(O_op, O_cv, B_op, B_cv, w["F"], hs, stream=st)
+                changed_total.add_(ch.sum())
+                ds.eval_batch_masked(O_op, O_cv, ch, hs, stream=st, out=[f_new, None, None, None])
+                gg.gom_accept(O_op, O_cv, B_op, B_cv, f_new, f_b, ch, stream=st)
+        with torch.cuda.stream(st):
+            sweep()
+        st.synchronize()
+        changed_total.zero_()
+        e0, e1 = ev(), ev()
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(a.steps):
+                sweep()
+            e1.record(st)
+        st.synchronize()
+        ds.sync(st)
+        ms = e0.elapsed_time(e1) / a.steps
+        evals = changed_total.item() / a.steps
+        line.update(value=evals * (nodes / P) * N / (ms * 1e-3), ms_per_step=ms,
+                    fos_steps_per_s=stride / (ms * 1e-3),
+                    changed_trial_evals_per_s=evals / (ms * 1e-3),
+                    note="one step = a full FOS sweep (%d subsets) on the device: donor copy, "
+                         "changed test, masked evaluation of the changed trials, accept or "
+                         "revert; value counts node-rows of the evaluated trials with the "
+                         "batch's mean active size" % stride)
+    ds.close()
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.mode != "eval":
+        import torch
+        import paper_2605_30954_gb300 as gg
+        return run_extra_mode(a, gg, torch)
     import torch
     import paper_2605_30954_gb300 as gg
 
@@ -257,6 +383,8 @@ def main():
         t = torch.tensor([x], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=op)
         return t.item()
+
+    ops = {"max": pg.ReduceOp.MAX if pg else None, "sum": pg.ReduceOp.SUM if pg else None}
 
     w = make_workload(a.config, rank, gg, torch, dev)
     nodes, fp32_ops, sfu_ops, valid, instrs = node_counts(gg, torch, w)
@@ -302,12 +430,11 @@ def main():
     st.synchronize()
     clocks = Clocks(dev)
     tot_ms, ck = timed(graph_step, a.steps, clocks, "timed_graph")
-    tot_ms = allreduce(tot_ms, pg.ReduceOp.MAX if pg else None)
-    ms_step = tot_ms / a.steps
-    all_nodes = allreduce(float(nodes), pg.ReduceOp.SUM if pg else None)
-    all_trials = allreduce(float(P), pg.ReduceOp.SUM if pg else None)
-    value = all_nodes * N / (ms_step * 1e-3)
-    trial_rate = all_trials / (ms_step * 1e-3)
+    agg = aggregate(tot_ms, a.steps, nodes, P, N, allreduce, ops)
+    ms_step = agg["ms_per_step"]
+    all_nodes, all_trials = agg["nodes"], agg["trials"]
+    value = agg["node_row_evals_per_s"]
+    trial_rate = agg["trial_evals_per_s"]
     ds.sync(st)
 
     # ---- forward kernel alone: live CUDA events around it (roofline) ----
@@ -338,7 +465,7 @@ def main():
         plain_step()
     st.synchronize()
     plain_ms, _ = timed(plain_step, a.plain_steps, name="timed_plain")
-    plain_step_ms = allreduce(plain_ms, pg.ReduceOp.MAX if pg else None) / a.plain_steps
+    plain_step_ms = allreduce(plain_ms, ops["max"]) / a.plain_steps
     plain_trials = all_trials / (plain_step_ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
@@ -354,7 +481,7 @@ def main():
             e2e_step()
     st.synchronize()
     e2e_ms, _ = timed(e2e_step, a.steps, name="timed_e2e")
-    e2e_ms = allreduce(e2e_ms, pg.ReduceOp.MAX if pg else None) / a.steps
+    e2e_ms = allreduce(e2e_ms, ops["max"]) / a.steps
     h2d = w["op"].nbytes + w["cval"].nbytes + (w["heights"].nbytes if hs is not None else 0)
     ds.sync(st)
 

@@ -192,9 +192,11 @@ ggeval_status ggeval_adam_step(const ggeval_batch* batch, float* cval, const flo
                                float beta2, float eps, void* stream);
 
 /* Time candidate tile shapes (rows per tile, trials per work item, rows per
- * lane) on this batch and keep the fastest for batches of the same shape
- * (n, max_height, layout, flags).  Synchronises the stream; runs the
- * evaluation several times.  Device batches only. */
+ * lane, register budget) on this batch and keep the fastest for batches of
+ * the same shape (n, max_height, layout, flags).  Synchronises the stream;
+ * runs the evaluation several times.  Device batches only.  With the
+ * environment variable GGEVAL_VERBOSE set (not "0") every candidate's time
+ * and the choice are printed to stderr. */
 ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* batch,
                               uint32_t flags, void* stream);
 
@@ -231,6 +233,63 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* batch, int32_t n_features,
 ggeval_status ggeval_pack_host(const ggeval_batch* batch, int32_t index, int32_t n_features,
                                uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
                                int32_t* len);
+
+/* Evaluate only the trials whose mask byte is nonzero: Evaluate(O[changed])
+ * of Algorithm 1.  mask is uint8 [n] in device memory (device batches only);
+ * the outputs of masked-out trials are left untouched.  Otherwise as
+ * ggeval_eval_batch (GGEVAL_F_GRAPH replays read the mask's current
+ * contents). */
+ggeval_status ggeval_eval_batch_masked(ggeval_dataset* ds, const ggeval_batch* batch,
+                                       const uint8_t* mask, uint32_t flags, float* smse,
+                                       float* a, float* b, float* mse, void* stream);
+
+/* One GOM step over a FOS index on the device (Algorithm 1's inner loop),
+ * so that a whole FOS sweep runs without host round trips.  All arrays are
+ * device memory, row-major [n][stride] with stride = 2^(max_height+1)-1.
+ *
+ * ggeval_gom_donate: for every offspring j, copy the nodes (op and constant)
+ * of FOS subset subset[j] from population member donor[j]:
+ * O_j[FOS[s]] <- P_donor[FOS[s]].  The FOS is given in CSR form: the nodes
+ * of subset s are fos_nodes[fos_offsets[s] .. fos_offsets[s+1]).  An
+ * out-of-range donor, subset or node leaves the offspring unchanged. */
+ggeval_status ggeval_gom_donate(int32_t n, int32_t max_height, uint8_t* op, float* cval,
+                                const uint8_t* pop_op, const float* pop_cval, int32_t n_pop,
+                                const int32_t* donor, const int32_t* subset,
+                                const int32_t* fos_offsets, const int32_t* fos_nodes,
+                                int32_t n_fos, void* stream);
+
+/* changed[j] = 1 when offspring j differs from its backup at a node that is
+ * active in either (opcode, or the constant of an ERC node): the paper
+ * evaluates an offspring only if an actively used part of its template
+ * changed (Section 3.1).  The offspring batch gives n, heights and layout;
+ * the backup has the same shape. */
+ggeval_status ggeval_gom_changed(const ggeval_batch* offspring, const uint8_t* backup_op,
+                                 const float* backup_cval, int32_t n_features,
+                                 uint8_t* changed, void* stream);
+
+/* Accept or revert (Algorithm 1): offspring j is accepted when it is
+ * unchanged, or when f_new[j] <= f_backup[j] (not worse; a NaN never
+ * replaces a number and a number always replaces a NaN); then its backup
+ * becomes a copy of it and, if changed, f_backup[j] = f_new[j].  Otherwise
+ * the offspring is reverted to its backup.  changed may be NULL (all
+ * changed); accepted (uint8 [n]) may be NULL. */
+ggeval_status ggeval_gom_accept(int32_t n, int32_t max_height, uint8_t* op, float* cval,
+                                uint8_t* backup_op, float* backup_cval, const uint8_t* changed,
+                                const float* f_new, float* f_backup, uint8_t* accepted,
+                                void* stream);
+
+/* Active size of every trial: size[j] = number of active nodes (int32 [n],
+ * batch memory must be device), the size objective of an error + size
+ * (multi-objective) search.  -1 for a trial whose height is out of range.
+ * The active set follows the same rule as the evaluation. */
+ggeval_status ggeval_trial_sizes(const ggeval_batch* batch, int32_t n_features, int32_t* size,
+                                 void* stream);
+
+/* The dataset's shape and target statistics: rows, features, mean(y) and
+ * the population variance Var(y) (1/N), both in FP64 from the stored target.
+ * NMSE (Eq. 2) = mse / Var(y).  Any output pointer may be NULL. */
+ggeval_status ggeval_dataset_info(const ggeval_dataset* ds, int64_t* n_rows,
+                                  int32_t* n_features, double* y_mean, double* y_var);
 
 /* Evaluation that allocates nothing.  Some callers cannot call cudaMalloc
  * while they evaluate: code running inside a CUDA stream capture (the

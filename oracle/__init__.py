@@ -19,10 +19,13 @@ What it computes (plain definitions, slow on purpose):
 * the reverse-mode FP64 gradient of (scaled) MSE with respect to every ERC
   constant, and central finite differences of the same quantity;
 * an FP32-emulating evaluator (every node rounded to float32, float32 libm)
-  that the tests use only to flag rows and trials whose FP32 value is
-  ill-conditioned.
+  and a first-order condition bound, which the tests use only to flag rows
+  and trials whose FP32 value is ill-conditioned;
+* one GOM step of Algorithm 1 (donor copy, the "changed" test, accept or
+  revert) in ``oracle.gom``.
 
 Parity pins (tests/test_oracle_pins.py) tie every function here to the
 paper's worked example, closed forms, library special cases and brute force.
 """
 from .gp import *  # noqa: F401,F403
+from . import gom  # noqa: F401

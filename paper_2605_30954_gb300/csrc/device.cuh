@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gmath.cuh"
 #include "isa.h"
 
 namespace gg {
@@ -38,6 +39,60 @@ __device__ __forceinline__ float unop(float a) {
   if constexpr (U == U_LOG) return logf(a);
   if constexpr (U == U_SQRT) return sqrtf(a);
   return 0.f;
+}
+
+// A unary operator on the R rows of a lane.  When the branch-free forms of
+// gmath.cuh are selected, one test over the R rows sends an argument
+// outside their domain (|x| > 2^17 for sin and cos; zero, subnormal,
+// infinite or NaN for sqrt) to the CUDA library function on a cold path, so
+// the common path has no per-row branch.
+// By default every operator uses the CUDA library functions: at the
+// 64-register budget of the fastest kernel variant the branch-free forms
+// cost more in registers than they save in instructions (measured on the
+// FOS-step workload).  -DGG_OWN_TRIG and -DGG_OWN_SQRT select them; they pay
+// off for kernels with 8 rows per lane, whose code then fits the
+// instruction cache.
+template <int U, int R>
+__device__ __forceinline__ void unop_rows(float (&A)[R]) {
+#ifdef GG_OWN_TRIG
+  constexpr bool own_trig = true;
+#else
+  constexpr bool own_trig = false;
+#endif
+#ifdef GG_OWN_SQRT
+  constexpr bool own = true;
+#else
+  constexpr bool own = false;
+#endif
+  if constexpr (own_trig && (U == U_SIN || U == U_COS)) {
+    bool big = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) big |= fabsf(A[r]) > TRIG_RANGE;
+    if (__builtin_expect(big, 0)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sinf(A[r]) : cosf(A[r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sin_reduced(A[r]) : cos_reduced(A[r]);
+    }
+  } else if constexpr (own && (U == U_SQRT_ABS || U == U_SQRT)) {
+    bool special = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float v = U == U_SQRT_ABS ? fabsf(A[r]) : A[r];
+      special |= !(v >= SQRT_MIN && v <= SQRT_MAX);
+    }
+    if (__builtin_expect(special, 0)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = sqrtf(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = sqrt_newton(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[r] = unop<U>(A[r]);
+  }
 }
 
 // ------------------------------------------------------------ interpreter
@@ -90,7 +145,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
 #define GG_ROWS _Pragma("unroll") for (int r = 0; r < R; ++r)
 #define GG_UN(u)                                   \
   case I_UN + u:                                   \
-    GG_ROWS A[r] = unop<u>(A[r]);                  \
+    unop_rows<u, R>(A);                            \
     break;
 #define GG_BIN(kd)                                                    \
   case I_BF + kd:                                                     \

@@ -16,8 +16,9 @@ struct PackParams {
   int n, h_max, stride, layout, n_features, max_slots, lstride;
   uint2* prog;           // [n][lstride] (word, const bits)
   Aux* aux;              // nullable, [n][lstride]
-  int* len;              // [n] instruction count, -1 for an invalid trial
+  int* len;              // [n] instruction count, -1 for an invalid trial, 0 masked out
   unsigned* status;
+  const uint8_t* mask;   // nullable: evaluate only trials with a nonzero byte
 };
 
 // pack_kernel (defined in misc.cu): one thread per trial.
@@ -72,11 +73,13 @@ __device__ __forceinline__ void accumulate_exact(const float (&A)[R], const floa
   }
 }
 
+// Pairwise sums of the pass's R rows are added to plain FP32 group sums
+// (m1..m3); the caller folds the group sums into the error-free (hi, lo)
+// accumulators every GROUP passes (fold_group).
 template <int R, bool MASK>
 __device__ __forceinline__ void accumulate_pairwise(const float (&A)[R], const float (&yv)[R],
-                                                    float cs, int valid, float& s1h, float& s1l,
-                                                    float& s2h, float& s2l, float& s3h, float& s3l,
-                                                    float& fm) {
+                                                    float cs, int valid, float& m1, float& m2,
+                                                    float& m3, float& fm) {
   float d[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -100,9 +103,20 @@ __device__ __forceinline__ void accumulate_pairwise(const float (&A)[R], const f
       c[i] = c[2 * i] + c[2 * i + 1];
     }
   }
-  acc_add(s1h, s1l, a[0]);
-  acc_add(s2h, s2l, b[0]);
-  acc_add(s3h, s3l, c[0]);
+  m1 += a[0];
+  m2 += b[0];
+  m3 += c[0];
+}
+
+constexpr int GROUP = 4;  // passes per plain FP32 group sum
+
+__device__ __forceinline__ void fold_group(float& m1, float& m2, float& m3, float& s1h,
+                                           float& s1l, float& s2h, float& s2l, float& s3h,
+                                           float& s3l) {
+  acc_add(s1h, s1l, m1);
+  acc_add(s2h, s2l, m2);
+  acc_add(s3h, s3l, m3);
+  m1 = m2 = m3 = 0.f;
 }
 
 // Claim the next work item for tile buffer `s` and start loading it: run by
@@ -148,8 +162,10 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int s, float* x
 // [2] how many warps are done with it.  The warp that finishes a buffer
 // last resets [1], [2] and refills the buffer with the next item; no warp
 // ever waits for the others except for the tile it is about to use.
-template <int DMAX, int R, bool EXACT, bool ROWS>
-__global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
+// MINB is the launch-bounds occupancy target: 1 lets the compiler use up to
+// 128 registers per thread, 2 caps it at 64 (two 512-thread CTAs per SM).
+template <int DMAX, int R, bool EXACT, bool ROWS, int MINB>
+__global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -213,6 +229,7 @@ __global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
       __syncwarp();
 
       float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
+      float m1 = 0.f, m2 = 0.f, m3 = 0.f;
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
@@ -250,9 +267,11 @@ __global__ void __launch_bounds__(512) fwd_kernel(const FwdParams p) {
             accumulate_exact<R, true>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
         } else {
           if (full)
-            accumulate_pairwise<R, false>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+            accumulate_pairwise<R, false>(A, yv, cs, valid, m1, m2, m3, fm);
           else
-            accumulate_pairwise<R, true>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
+            accumulate_pairwise<R, true>(A, yv, cs, valid, m1, m2, m3, fm);
+          if ((ps & (GROUP - 1)) == GROUP - 1 || ps == npass - 1)
+            fold_group(m1, m2, m3, s1h, s1l, s2h, s2l, s3h, s3l);
         }
       }
       warp_dd_sum(s1h, s1l);
@@ -313,12 +332,13 @@ constexpr double VAR_TOL = 1e-12;
 
 // kernel pointers, one table per translation unit (fwd_d3.cu, fwd_d5.cu,
 // fwd_d7.cu): variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
-// pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values
-constexpr int NVARIANT = 4;
+// pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
+// variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers
+constexpr int NVARIANT = 7;
 const void* fwd_ptr_d3(int variant);
 const void* fwd_ptr_d5(int variant);
 const void* fwd_ptr_d7(int variant);
-inline int variant_rows(int v) { return v == 0 ? 8 : 4; }
-inline bool variant_exact(int v) { return v >= 2; }
+inline int variant_rows(int v) { return (v == 0 || v == 4) ? 8 : 4; }
+inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
 
 }  // namespace gg

@@ -11,6 +11,10 @@ __global__ void pack_kernel(const PackParams p) {
   if (t >= p.n) return;
   uint8_t* depth1 = pk_smem + (size_t)threadIdx.x * 2 * p.stride;
   uint8_t* need = depth1 + p.stride;
+  if (p.mask && !p.mask[t]) {  // not evaluated in this call
+    p.len[t] = 0;
+    return;
+  }
   const int h = p.height ? (int)p.height[t] : p.h_max;
   uint2* prog = p.prog + (size_t)t * p.lstride;
   int L = -1;
@@ -31,7 +35,7 @@ __global__ void pack_kernel(const PackParams p) {
 __global__ void fin_kernel(const FinParams p) {
   const int lane = threadIdx.x & 31;
   const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (t >= p.P) return;
+  if (t >= p.P || p.len[t] == 0) return;  // 0: masked out, outputs untouched
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
   double smse, a, b, mse, ac = 0.0, bo = 0.0;

@@ -27,7 +27,9 @@ MAX_HEIGHT = 8
 SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggeval_eval_rows",
            "ggeval_eval_plain", "ggeval_grad_batch", "ggeval_adam_step", "ggeval_autotune",
            "ggeval_sync", "ggeval_last_error", "ggeval_batch_stats", "ggeval_pack_host",
-           "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc")
+           "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc",
+           "ggeval_eval_batch_masked", "ggeval_gom_donate", "ggeval_gom_changed",
+           "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info")
 
 
 class GGEvalError(RuntimeError):
@@ -67,6 +69,13 @@ def load_library(path: str = LIB_PATH):
         "ggeval_version": [],
         "ggeval_profile_read": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
         "ggeval_eval_batch_noalloc": [vp, bp, vp, vp, vp, vp, vp],
+        "ggeval_eval_batch_masked": [vp, bp, vp, u32, vp, vp, vp, vp, vp],
+        "ggeval_gom_donate": [i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, i32, vp],
+        "ggeval_gom_changed": [bp, vp, vp, i32, vp, vp],
+        "ggeval_gom_accept": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "ggeval_trial_sizes": [bp, i32, vp, vp],
+        "ggeval_dataset_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -206,12 +215,34 @@ class Dataset:
                                        _stream_handle(stream)))
         return smse, dcval
 
+    def eval_batch_masked(self, op, cval, mask, heights=None, layout=LAYOUT_HEAP, flags=0,
+                          stream=None, out=None):
+        """Evaluate only trials with mask != 0 (uint8 device tensor); the
+        other entries of ``out`` are left as they are."""
+        b = make_batch(op, cval, heights, layout=layout)
+        outs = out if out is not None else self._outs(b.n, op, (True, True, True, True))
+        _check(lib().ggeval_eval_batch_masked(self._h, ctypes.byref(b), _ptr(mask), flags,
+                                              *map(_ptr, outs), _stream_handle(stream)))
+        return outs
+
     def autotune(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None):
         b = make_batch(op, cval, heights, layout=layout)
         _check(lib().ggeval_autotune(self._h, ctypes.byref(b), flags, _stream_handle(stream)))
 
     def sync(self, stream=None):
         _check(lib().ggeval_sync(self._h, _stream_handle(stream)))
+
+    def info(self):
+        """(rows, features, mean y, Var y) of the stored dataset."""
+        n, f = ctypes.c_int64(), ctypes.c_int32()
+        m, v = ctypes.c_double(), ctypes.c_double()
+        _check(lib().ggeval_dataset_info(self._h, ctypes.byref(n), ctypes.byref(f),
+                                         ctypes.byref(m), ctypes.byref(v)))
+        return n.value, f.value, m.value, v.value
+
+    def nmse(self, mse):
+        """NMSE (Eq. 2) from MSE values: mse / Var(y)."""
+        return mse / self.info()[3]
 
     def profile_read(self):
         """(total forward-kernel ms, launches) since the last read."""
@@ -227,6 +258,48 @@ def adam_step(op, cval, grad, m, v, t, lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8
     b = make_batch(op, cval)
     _check(lib().ggeval_adam_step(ctypes.byref(b), _ptr(cval), _ptr(grad), _ptr(m), _ptr(v),
                                   int(t), lr, beta1, beta2, eps, _stream_handle(stream)))
+
+
+def gom_donate(op, cval, pop_op, pop_cval, donor, subset, fos_offsets, fos_nodes, stream=None):
+    """O_j[FOS[subset_j]] <- P_donor_j[FOS[subset_j]], in place (device tensors;
+    donor, subset, fos_offsets, fos_nodes int32)."""
+    n, stride = op.shape
+    h = (stride + 1).bit_length() - 2
+    _check(lib().ggeval_gom_donate(n, h, _ptr(op), _ptr(cval), _ptr(pop_op), _ptr(pop_cval),
+                                   pop_op.shape[0], _ptr(donor), _ptr(subset), _ptr(fos_offsets),
+                                   _ptr(fos_nodes), fos_offsets.numel() - 1,
+                                   _stream_handle(stream)))
+
+
+def gom_changed(op, cval, bop, bcval, n_features, heights=None, layout=LAYOUT_HEAP,
+                stream=None):
+    """uint8 [n]: 1 where an active part of the offspring differs from its backup."""
+    b = make_batch(op, cval, heights, layout=layout)
+    changed = torch.empty(b.n, dtype=torch.uint8, device=op.device)
+    _check(lib().ggeval_gom_changed(ctypes.byref(b), _ptr(bop), _ptr(bcval), n_features,
+                                    _ptr(changed), _stream_handle(stream)))
+    return changed
+
+
+def gom_accept(op, cval, bop, bcval, f_new, f_old, changed=None, stream=None):
+    """Accept (backup <- offspring, f_old <- f_new) or revert (offspring <-
+    backup) every trial in place; returns the uint8 accepted flags."""
+    n, stride = op.shape
+    h = (stride + 1).bit_length() - 2
+    acc = torch.empty(n, dtype=torch.uint8, device=op.device)
+    _check(lib().ggeval_gom_accept(n, h, _ptr(op), _ptr(cval), _ptr(bop), _ptr(bcval),
+                                   _ptr(changed), _ptr(f_new), _ptr(f_old), _ptr(acc),
+                                   _stream_handle(stream)))
+    return acc
+
+
+def trial_sizes(op, cval, n_features, heights=None, layout=LAYOUT_HEAP, stream=None):
+    """int32 [n]: active node count of every trial (device batch)."""
+    b = make_batch(op, cval, heights, layout=layout)
+    size = torch.empty(b.n, dtype=torch.int32, device=op.device)
+    _check(lib().ggeval_trial_sizes(ctypes.byref(b), n_features, _ptr(size),
+                                    _stream_handle(stream)))
+    return size
 
 
 def batch_stats(op, cval, heights=None, layout=LAYOUT_HEAP, n_features=223):

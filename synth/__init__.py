@@ -42,6 +42,28 @@ BASIC_SET = (ADD, SUB, MUL, AQ)
 FULL_SET = (ADD, SUB, MUL, AQ, SIN, COS, EXP, LOG_ABS, SQRT_ABS)
 #: the paper's Table 2 operator set for Experiments I/II, minus pow
 PAPER_SET = (ADD, SUB, MUL, DIV, SIN, COS, SQUARE, SQRT, EXP, LOG)
+#: the paper's Table 2 operator set for Experiment III
+EXP3_SET = (ADD, SUB, MUL, DIV, SQUARE, SQRT)
+
+
+def _ladder_targets():
+    """Ground-truth expressions of the Experiment III datasets (Table 1), as
+    functions of X [N, 9]: the workload's target function, not a tree."""
+    def s(x, *k):
+        return sum(x[:, i] for i in k)
+    return {
+        "addition": lambda x: s(x, *range(9)),
+        "division": lambda x: s(x, 0, 1, 2) / s(x, 3, 4, 5, 6, 7, 8),
+        "subtraction": lambda x: s(x, 0, 1, 2) / (x[:, 4] - x[:, 3] + x[:, 6] - x[:, 5]
+                                                 + x[:, 8] - x[:, 7]),
+        "multiplication": lambda x: x[:, 0] * x[:, 1] * x[:, 2] / (
+            x[:, 4] - x[:, 3] + x[:, 6] - x[:, 5] + x[:, 8] - x[:, 7]),
+        "squaring": lambda x: x[:, 0] * x[:, 1] * x[:, 2] / (
+            (x[:, 4] - x[:, 3]) ** 2 + (x[:, 6] - x[:, 5]) ** 2 + (x[:, 8] - x[:, 7]) ** 2),
+    }
+
+
+LADDER = _ladder_targets()
 
 
 def n_nodes(h: int) -> int:
@@ -167,6 +189,14 @@ CONFIGS = {
                N=1_000_000, F=10, x=("uniform", -1.0, 1.0), y_h=6, y_funcs=FULL_SET,
                noise=0.01, fos=True),
 }
+# Experiment III ladder (Table 1): 100,000 x 9, depth-6 templates over the
+# Experiment III operators, the starting population of 2,000; X ~ U[1, 5]
+# (the paper does not state the sampling distribution)
+for _i, _name in enumerate(("addition", "division", "subtraction", "multiplication",
+                            "squaring")):
+    CONFIGS["l_" + _name[:3]] = dict(
+        index=5 + _i, name=f"ladder-{_name}-2000xh6-100000x9", P=2_000, h=6, funcs=EXP3_SET,
+        N=100_000, F=9, x=("uniform", 1.0, 5.0), target=_name, noise=0.0, fos=False)
 
 
 def seed_of(cfg: str, rep: int = 0) -> int:
@@ -225,9 +255,12 @@ def workload(cfg: str, rep: int = 0, n_rows: int | None = None,
             gop, gcv, _ = random_templates(r_y, 1, c["y_h"], c["y_h"], c["y_funcs"], F, pf)
             yield gop[0], gcv[0], c["y_h"]
 
-    return dict(cfg=cfg, name=c["name"], X=X, op=op, cval=cval, heights=heights,
-                h_max=h_max, layout=layout, y_cands=y_cands, z=z,
-                noise=float(c["noise"]), N=N, P=P, F=F)
+    out = dict(cfg=cfg, name=c["name"], X=X, op=op, cval=cval, heights=heights,
+               h_max=h_max, layout=layout, y_cands=y_cands if "target" not in c else None,
+               z=z, noise=float(c["noise"]), N=N, P=P, F=F)
+    if "target" in c:  # a closed-form target (Table 1), given directly
+        out["y"] = LADDER[c["target"]](X.astype(np.float64)).astype(np.float32)
+    return out
 
 
 def make_target(f_gen: np.ndarray, z: np.ndarray, noise: float) -> np.ndarray:

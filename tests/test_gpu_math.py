@@ -1,0 +1,85 @@
+"""Accuracy of the interpreter's sin, cos and sqrt against FP64 (per-row values
+through the C ABI), in FP32 units in the last place of the exact result.
+Arguments cover the reduction's range (|x| <= 2^17), the neighbourhoods of
+multiples of pi/2, the library fallback beyond it, and the special values."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from fixtures import heap_template
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_30954_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def ulp32(v):
+    v = np.abs(np.asarray(v, dtype=np.float64)).astype(np.float32)
+    return np.spacing(np.maximum(v, np.float32(1.17549435e-38))).astype(np.float64)
+
+
+def rows_of(gg, tok, x):
+    X = torch.from_numpy(x.astype(np.float32)[:, None])
+    ds = gg.Dataset(X, torch.zeros(x.size))
+    op, cv = heap_template([tok, "x0", "x0"], 1)
+    f = ds.eval_rows(torch.from_numpy(op[None]).cuda(), torch.from_numpy(cv[None]).cuda())
+    ds.sync()
+    ds.close()
+    return f[0].cpu().numpy()
+
+
+def trig_args():
+    rng = np.random.default_rng(0)
+    k = np.arange(-80000, 80001, 37)
+    near = (k * (np.pi / 2)).astype(np.float32)
+    near = np.concatenate([near, np.nextafter(near, np.float32(np.inf)),
+                           np.nextafter(near, np.float32(-np.inf))])
+    return np.concatenate([rng.uniform(-4, 4, 20000), rng.uniform(-2 ** 17, 2 ** 17, 20000),
+                           10.0 ** rng.uniform(-30, 5, 5000), near]).astype(np.float32)
+
+
+@pytest.mark.parametrize("tok,fn", [("sin", np.sin), ("cos", np.cos)])
+def test_trig_within_two_ulp_in_range(gg, tok, fn):
+    x = trig_args()
+    x = x[np.abs(x) <= 2 ** 17]
+    got = rows_of(gg, tok, x).astype(np.float64)
+    want = fn(x.astype(np.float64))
+    err = np.abs(got - want) / ulp32(want)
+    assert err.max() <= 2.0, (x[np.argmax(err)], got[np.argmax(err)], want[np.argmax(err)])
+
+
+@pytest.mark.parametrize("tok,fn", [("sin", np.sin), ("cos", np.cos)])
+def test_trig_large_and_special_arguments(gg, tok, fn):
+    x = np.array([2.0 ** 17 + 1, 3e5, -7.5e6, 1e30, -3.4e38, np.inf, -np.inf, np.nan, 0.0, -0.0],
+                 dtype=np.float32)
+    got = rows_of(gg, tok, x).astype(np.float64)
+    want = fn(x.astype(np.float64))
+    fin = np.isfinite(x)
+    assert np.all(np.isnan(got[~fin]))
+    assert np.all(np.abs(got[fin] - want[fin]) <= 2.0 * ulp32(want[fin]))
+
+
+@pytest.mark.parametrize("tok", ["sqrtabs", "sqrt"])
+def test_sqrt_within_one_ulp(gg, tok):
+    rng = np.random.default_rng(1)
+    x = np.concatenate([10.0 ** rng.uniform(-45, 38, 30000), rng.uniform(0, 10, 10000),
+                        [0.0, 1e-45, 1e-40, 1.17549435e-38, 3.4e38, np.inf]]).astype(np.float32)
+    if tok == "sqrtabs":
+        x = np.concatenate([x, -x])
+    got = rows_of(gg, tok, x).astype(np.float64)
+    want = np.sqrt(np.abs(x.astype(np.float64)))
+    fin = np.isfinite(want)
+    err = np.abs(got[fin] - want[fin]) / ulp32(want[fin])
+    assert err.max() <= 1.0
+    assert np.all(np.isinf(got[~fin]))
+    if tok == "sqrt":
+        assert np.isnan(rows_of(gg, "sqrt", np.array([-1.0, -1e-30], np.float32))).all()

@@ -1,0 +1,94 @@
+"""Size objective, NMSE, and the Experiment III ladder workloads on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from fixtures import heap_template
+import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_30954_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def test_trial_sizes_match_active_sets(gg):
+    w = synth.workload("c3", 2, n_rows=10, n_trials=300)
+    size = gg.trial_sizes(torch.from_numpy(w["op"]).cuda(), torch.from_numpy(w["cval"]).cuda(),
+                          w["F"], torch.from_numpy(w["heights"]).cuda()).cpu().numpy()
+    want = [int(O.active_mask(PA.template(w, p)).sum()) for p in range(300)]
+    np.testing.assert_array_equal(size, want)
+
+
+def test_nmse_and_dataset_info(gg):
+    w = PA.build("c2", 5000, 30)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    n, f, ym, yv = ds.info()
+    y = w["y"].astype(np.float64)
+    assert (n, f) == (5000, 8)
+    np.testing.assert_allclose([ym, yv], [y.mean(), y.var()], rtol=1e-6)
+    mse = ds.eval_batch(torch.from_numpy(w["op"]).cuda(), torch.from_numpy(w["cval"]).cuda())[3]
+    nmse = ds.nmse(mse).cpu().numpy()
+    ds.sync()
+    ds.close()
+    checked = 0
+    for p in range(30):
+        t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
+        if not fit64["finite"] or not np.isfinite(nmse[p]) or bounds is None:
+            continue
+        if bounds[1] > 1e-6 * fit64["mse"]:
+            continue
+        checked += 1
+        assert abs(nmse[p] - fit64["nmse"]) <= 2e-4 * fit64["nmse"] + 1e-8
+    assert checked >= 10
+
+
+@pytest.mark.parametrize("cfg", ["l_add", "l_squ", "l_sub"])
+def test_ladder_parity(gg, cfg):
+    w = PA.build(cfg, 4000, 40)
+    X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
+    ds = gg.Dataset(X, y)
+    smse, a, b, mse = (t.cpu().numpy() for t in
+                       ds.eval_batch(torch.from_numpy(w["op"]).cuda(),
+                                     torch.from_numpy(w["cval"]).cuda()))
+    ds.sync()
+    ds.close()
+    tf = PA.Tally()
+    var_y = float(np.var(w["y"].astype(np.float64)))
+    mean_y2 = float(np.mean(w["y"].astype(np.float64) ** 2))
+    for p in range(w["P"]):
+        t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
+        PA.check_fit(float(smse[p]), float(mse[p]), fit64, fit32, var_y, mean_y2, tf,
+                     tag=f"trial {p}", bounds=bounds)
+    assert tf.failed == 0, repr(tf)
+    assert tf.checked >= 20, repr(tf)
+
+
+def test_feynman_squaring_expression_scores_zero(gg):
+    """Table 1's Feynman I.9.18 expression, written as a template, scores a
+    scaled MSE at the FP32 noise floor on its own dataset (Section 4.4:
+    NMSE 1e-6 is the FP32 precision level)."""
+    w = synth.workload("l_squ", 0, n_rows=20_000, n_trials=1)
+    # (x0 x1 x2) / ((x4 - x3)^2 + (x6 - x5)^2 + (x8 - x7)^2), heap layout, height 5
+    tree = {0: "/", 1: "*", 2: "+", 3: "*", 4: "x2", 7: "x0", 8: "x1",
+            5: "+", 6: "sq", 11: "sq", 12: "sq", 23: "-", 24: None, 25: "-",
+            13: "-", 27: "x8", 28: "x7", 47: "x4", 48: "x3", 51: "x6", 52: "x5"}
+    op, cv = heap_template(tree, 5)
+    t = O.Template(op, cv, 5, n_features=9)
+    np.testing.assert_allclose(O.eval_tree(t, w["X"]), synth.LADDER["squaring"](
+        w["X"].astype(np.float64)), rtol=1e-6)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    smse, a, b, mse = (x.item() for x in ds.eval_batch(torch.from_numpy(op[None]).cuda(),
+                                                          torch.from_numpy(cv[None]).cuda()))
+    ds.sync()
+    var_y = float(np.var(w["y"].astype(np.float64)))
+    assert smse <= 1e-6 * var_y and abs(b - 1) < 1e-3 and mse / var_y <= 1e-6
+    ds.close()

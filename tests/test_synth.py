@@ -14,9 +14,13 @@ def test_workload_small_is_deterministic(cfg):
     c = synth.CONFIGS[cfg]
     assert a["X"].shape == (300, c["F"]) and a["X"].dtype == np.float32
     assert a["op"].shape == (40, synth.n_nodes(c["h"]))
-    ga = next(a["y_cands"]())
-    gb = next(b["y_cands"]())
-    np.testing.assert_array_equal(ga[0], gb[0])
+    if a["y_cands"] is None:  # closed-form target (Experiment III ladder)
+        np.testing.assert_array_equal(a["y"], b["y"])
+        assert a["y"].shape == (300,) and np.all(np.isfinite(a["y"]))
+    else:
+        ga = next(a["y_cands"]())
+        gb = next(b["y_cands"]())
+        np.testing.assert_array_equal(ga[0], gb[0])
 
 
 def test_heights_and_padding():
@@ -61,3 +65,14 @@ def test_make_target_noise():
     y = synth.make_target(f, z, 0.01)
     assert y.dtype == np.float32
     np.testing.assert_allclose(np.std(y.astype(float) - f), 0.01 * np.std(f) * np.std(z), rtol=1e-3)
+
+
+def test_ladder_targets_are_the_table_expressions():
+    # hand-evaluated rows of the Table 1 expressions
+    x = np.array([[1, 2, 3, 4, 5, 6, 7, 8, 9], [2, 1, 1, 3, 1, 2, 4, 5, 2]], np.float64)
+    L = synth.LADDER
+    np.testing.assert_allclose(L["addition"](x), [45, 21])
+    np.testing.assert_allclose(L["division"](x), [6 / 39, 4 / 17])
+    np.testing.assert_allclose(L["subtraction"](x), [6 / 3, 4 / (1 - 3 + 4 - 2 + 2 - 5)])
+    np.testing.assert_allclose(L["multiplication"](x), [6 / 3, 2 / -3])
+    np.testing.assert_allclose(L["squaring"](x), [6 / 3, 2 / (4 + 4 + 9)])
