@@ -48,6 +48,10 @@ OPS_FP32 = {"term": 0, "addsubmul": 1, "aq": 2, "div": 1, "sincos": 2, "exp": 1,
 OPS_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, "log": 1,
            "sqrt": 1, "square": 0}
 ACC_FP32 = 4
+# DRAM bytes (read + write) of one batched-forward launch from the ncu
+# capture summarised in profiles/fwd_kernel_fos-step-4096xh4-100000x8.md;
+# None for a workload without a capture of the current kernel
+NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4276992 + 9728}
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9}
 
@@ -503,7 +507,7 @@ def main():
                 "trial_evals_per_s": all_trials / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(4 * P)},
         "roofline": {"bound": "alu", "achieved": ach_fp32, "peak": peak_fp32, "unit": "Gop/s",
-                     "frac": ach_fp32 / peak_fp32, "traffic": None,
+                     "frac": ach_fp32 / peak_fp32, "traffic": NCU_TRAFFIC.get(w["name"]),
                      "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
                      "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
                                    "(sampled SM clock)",

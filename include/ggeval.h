@@ -319,7 +319,7 @@ ggeval_status ggeval_dataset_info(const ggeval_dataset* ds, int64_t* n_rows,
 #define GGEVAL_NOALLOC_MAX_TRIALS 4096
 #define GGEVAL_NOALLOC_MAX_HEIGHT 6
 #define GGEVAL_NOALLOC_MAX_TILES 64
-#define GGEVAL_NOALLOC_SCRATCH_BYTES (4096u * 128u * 8u + 4096u * 4u + 4096u * 64u * 40u + 256u)
+#define GGEVAL_NOALLOC_SCRATCH_BYTES (4096u * 128u * 8u + 4096u * 4u + 4096u * 64u * 32u + 256u)
 ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const ggeval_batch* batch,
                                         float* smse, float* a, float* b, float* mse,
                                         void* stream);

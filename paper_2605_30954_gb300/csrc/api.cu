@@ -139,7 +139,7 @@ struct ggeval_dataset {
   size_t cap_aux = 0;
   int* len = nullptr;
   size_t cap_len = 0;
-  double* part = nullptr;
+  float* part = nullptr;
   size_t cap_part = 0;
   double* ab = nullptr;
   size_t cap_ab = 0;
@@ -1037,7 +1037,7 @@ constexpr size_t NA_PROG_BYTES =
 constexpr size_t NA_LEN_OFF = NA_PROG_BYTES;
 constexpr size_t NA_PART_OFF = NA_LEN_OFF + (size_t)GGEVAL_NOALLOC_MAX_TRIALS * 4u;
 constexpr size_t NA_CNT_OFF =
-    NA_PART_OFF + (size_t)GGEVAL_NOALLOC_MAX_TRIALS * GGEVAL_NOALLOC_MAX_TILES * gg::NPART * 8u;
+    NA_PART_OFF + (size_t)GGEVAL_NOALLOC_MAX_TRIALS * GGEVAL_NOALLOC_MAX_TILES * gg::NPART * 4u;
 constexpr size_t NA_BYTES = NA_CNT_OFF + 256u;
 static_assert(NA_BYTES == GGEVAL_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
 static_assert(NA_LEN_OFF % 256 == 0 && NA_PART_OFF % 256 == 0 && NA_CNT_OFF % 256 == 0,
@@ -1098,7 +1098,7 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
                 (long long)ds->N, c.tile_rows, GGEVAL_NOALLOC_MAX_TILES);
   uint2* prog = reinterpret_cast<uint2*>(base);
   int* len = reinterpret_cast<int*>(base + NA_LEN_OFF);
-  double* part = reinterpret_cast<double*>(base + NA_PART_OFF);
+  float* part = reinterpret_cast<float*>(base + NA_PART_OFF);
   int* counter = reinterpret_cast<int*>(base + NA_CNT_OFF);
   gg::PackParams pp{};
   pp.op = b->op;

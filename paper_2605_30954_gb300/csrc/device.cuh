@@ -278,12 +278,18 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float h2, float l2)
   lo = e - (hi - s);
 }
 
+// Sum (hi, lo) over the warp: TwoSum on the high parts at every level, the
+// low parts and the TwoSum errors added plainly (their size is ~2^-24 of
+// the high part, so no renormalisation is needed over 5 levels).
 __device__ __forceinline__ void warp_dd_sum(float& hi, float& lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    dd_add(hi, lo, h2, l2);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = lo + l2 + e;
   }
 }
 

@@ -33,8 +33,8 @@ struct PackParams {
 // d = f - c, d^2 and d * yc, where c is the mean of f over the tile's first
 // pass (a shift that keeps the sums well conditioned).  The warp combines
 // its lanes' sums in double-float arithmetic and writes one partial record
-// {c, S_d, S_dd, S_dy, max|f|} per (trial, tile) in FP64; fin_kernel merges
-// them.  (Section 3.2 accumulates squared errors per thread in registers
+// {c, S_d, S_dd, S_dy, max|f|} per (trial, tile), the sums as FP32 (hi, lo)
+// pairs; fin_kernel merges them in FP64.  (Section 3.2 accumulates squared errors per thread in registers
 // and reduces them per block; here the tile of rows is shared by many
 // trials so X is read from HBM once per group instead of once per trial.)
 struct FwdParams {
@@ -44,13 +44,15 @@ struct FwdParams {
   const int* len;      // [P]
   int lstride, P;
   int tile_rows, n_tiles, group, n_items;
-  double* part;        // [P][n_tiles][5]
+  float* part;         // [P][n_tiles][NPART]
   int* counter;        // work-item counter, zero at launch
   unsigned* status;
   float* rows_out;     // [P][N] per-row values (ROWS variant only)
 };
 
-constexpr int NPART = 5;
+// partial record of one (trial, tile): the shift c, (hi, lo) of S_d, S_dd and
+// S_dy, and max |f|, all FP32; the finaliser combines them in FP64
+constexpr int NPART = 8;
 
 // two tile buffers, one program buffer per warp, two mbarriers, two
 // 4-int control blocks
@@ -243,19 +245,12 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
         }
         if (ps == 0) {  // shift: mean of f over the first pass's rows
           float sm = 0.f;
-          int cnt = 0;
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            if (r < valid) {
-              sm += A[r];
-              ++cnt;
-            }
+            if (r < valid) sm += A[r];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            sm += __shfl_xor_sync(0xffffffffu, sm, o);
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-          }
-          cs = sm / (float)cnt;
+          for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+          cs = sm / (float)min(nrows, RPP);
         }
         float yv[R];
         load_rows<R>(xs + (size_t)p.F * p.tile_rows + r0, yv);
@@ -280,12 +275,9 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
       if (lane == 0) {
-        double* q = p.part + ((size_t)trial * p.n_tiles + tile) * NPART;
-        q[0] = (double)cs;
-        q[1] = (double)s1h + (double)s1l;
-        q[2] = (double)s2h + (double)s2l;
-        q[3] = (double)s3h + (double)s3l;
-        q[4] = (double)fm;
+        float4* q = reinterpret_cast<float4*>(p.part + ((size_t)trial * p.n_tiles + tile) * NPART);
+        q[0] = make_float4(cs, s1h, s1l, s2h);
+        q[1] = make_float4(s2l, s3h, s3l, fm);
       }
       __syncwarp();
     }
@@ -313,7 +305,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
 //   smse  = (Syy_N - b* cov_N)/N   (the least-squares residual, Eq. 1 with
 //   the optimal affine map), mse = (1/N) sum (d - yc + c* - ybar)^2.
 struct FinParams {
-  const double* part;
+  const float* part;
   const int* len;
   int P, n_tiles, tile_rows;
   long long N;

@@ -45,20 +45,23 @@ __global__ void fin_kernel(const FinParams p) {
   } else {
     // lanes take tiles lane, lane + 32, ...; the shuffle tree below fixes
     // the summation order, so the result is deterministic
-    const double* q = p.part + (size_t)t * p.n_tiles * NPART;
+    const float* q = p.part + (size_t)t * p.n_tiles * NPART;
     const double cst = q[0];
     double sd = 0.0, sdd = 0.0, sdy = 0.0, fm = 0.0;
     for (int i = lane; i < p.n_tiles; i += 32) {
-      const double* u = q + (size_t)i * NPART;
+      const float* u = q + (size_t)i * NPART;
       const long long r0 = (long long)i * p.tile_rows;
       const long long r1 = min(p.N, r0 + p.tile_rows);
       const double n = (double)(r1 - r0);
-      const double del = u[0] - cst;
+      const double del = (double)u[0] - cst;
       const double syt = p.pref[r1] - p.pref[r0];
-      sd += u[1] + n * del;
-      sdd += u[2] + 2.0 * del * u[1] + n * del * del;
-      sdy += u[3] + del * syt;
-      fm = fmax(fm, u[4]);
+      const double a1 = (double)u[1] + (double)u[2];
+      const double a2 = (double)u[3] + (double)u[4];
+      const double a3 = (double)u[5] + (double)u[6];
+      sd += a1 + n * del;
+      sdd += a2 + 2.0 * del * a1 + n * del * del;
+      sdy += a3 + del * syt;
+      fm = fmax(fm, (double)u[7]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
