@@ -4,23 +4,28 @@
 // Work item = (trial, chunk of rows); warps claim items from a global
 // counter.  For 32 rows at a time (one per lane) a warp re-runs the trial's
 // program forward, storing the value of every instruction in a shared-memory
-// tape, seeds the output adjoint with
+// array V, seeds the output adjoint with
 //   w_i = (2 b*/N) (a* + b* f_i - y_i)          (scaled MSE; envelope theorem)
 //   w_i = (2/N) (f_i - y_i)                     (plain MSE)
 // and sweeps the program backwards.  Every instruction's value has exactly
-// one consumer (the program is a tree), so each adjoint is written once by
-// its consumer and read once.  The contribution of an ERC (pushed, or fused
-// into its parent) is summed over the warp's 32 rows with shuffles and added
-// into a per-warp FP64 accumulator; at the end of the item the accumulators
-// go to the trial's FP64 gradient row with atomics.  Node values live only
-// in shared memory for 32 rows at a time: nothing of size rows x nodes is
-// stored in HBM, so any dataset size works (recomputation instead of
-// storage).  The paper evaluates fitness only; this kernel is an addition.
+// one consumer (the program is a tree), so when the sweep reaches an
+// instruction it reads its operands' values from V and overwrites them with
+// their adjoints; by the time an operand instruction is reached, V holds its
+// adjoint while its own operands still hold values.  The operators whose
+// derivative uses their own output (exp, sqrt, division) recompute it from
+// the operands.  The contribution of an ERC (pushed, or fused into its
+// parent) is summed over the warp's 32 rows with shuffles and added into a
+// per-warp error-free FP32 (hi, lo) accumulator; at the end of the item the
+// accumulators go to the trial's FP64 gradient row with atomics.  Node
+// values live only in shared memory for 32 rows at a time: nothing of size
+// rows x nodes is stored in HBM, so any dataset size works (recomputation
+// instead of storage).  The paper evaluates fitness only; this kernel is an
+// addition.
 #include "misc.cuh"
 
 namespace gg {
 
-__device__ __forceinline__ void dbin(int kind, float a, float b, float out, float& da, float& db) {
+__device__ __forceinline__ void dbin(int kind, float a, float b, float& da, float& db) {
   switch (kind) {
     case K_ADD: da = 1.f; db = 1.f; break;
     case K_SUB: da = 1.f; db = -1.f; break;
@@ -31,24 +36,24 @@ __device__ __forceinline__ void dbin(int kind, float a, float b, float out, floa
       db = -a * b * q * q * q;
       break;
     }
-    default: {  // K_DIV
+    default: {  // K_DIV: d/da = 1/b, d/db = -(a/b)/b
       da = 1.f / b;
-      db = -out / b;
+      db = -(a / b) / b;
       break;
     }
   }
 }
 
-__device__ __forceinline__ float dun(int u, float x, float out) {
+__device__ __forceinline__ float dun(int u, float x) {
   switch (u) {
     case U_SIN: return cosf(x);
     case U_COS: return -sinf(x);
-    case U_EXP: return out;
+    case U_EXP: return expf(x);
     case U_LOG_ABS:
     case U_LOG: return 1.f / x;
-    case U_SQRT_ABS: return x == 0.f ? 0.f : copysignf(0.5f / out, x);
+    case U_SQRT_ABS: return x == 0.f ? 0.f : copysignf(0.5f / sqrtf(fabsf(x)), x);
     case U_SQUARE: return 2.f * x;
-    default: return 0.5f / out;  // U_SQRT
+    default: return 0.5f / sqrtf(x);  // U_SQRT
   }
 }
 
@@ -60,9 +65,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   unsigned char* base = smem + (size_t)warp * p.lstride * ADJ_WARP_BYTES_PER_INSTR;
   uint2* wprog = reinterpret_cast<uint2*>(base);
   Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
-  double* wg = reinterpret_cast<double*>(waux + p.lstride);
-  float* tape = reinterpret_cast<float*>(wg + p.lstride);  // [lstride][32]
-  float* adj = tape + (size_t)p.lstride * 32;              // [lstride][32]
+  float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per instruction
+  float* V = reinterpret_cast<float*>(wg + p.lstride);      // [lstride][32]
 
   float S[DMAX][1];
 #pragma unroll
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
     for (int k = lane; k <= L; k += 32) {
       wprog[k] = src[k];
       waux[k] = asrc[k];
-      wg[k] = 0.0;
+      wg[k] = make_float2(0.f, 0.f);
     }
     __syncwarp();
 
@@ -99,11 +103,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       const bool valid = row < r_end;
       const int rr = valid ? row : r_end - 1;
       float A[1] = {0.f};
-      run_program<DMAX, 1, true>(wprog, L, p.X + rr, p.ldx, A, S, tape + lane);
+      run_program<DMAX, 1, true>(wprog, L, p.X + rr, p.ldx, A, S, V + lane);
       const float f = A[0];
       const float yc = p.X[(size_t)p.F * p.ldx + rr];
       float w = p.mse_mode ? two_n * (f - ybar - yc) : two_n * bb * (a_c + bb * f - yc);
-      adj[32 * (L - 1) + lane] = valid ? w : 0.f;
+      V[32 * (L - 1) + lane] = valid ? w : 0.f;  // the output's value becomes its adjoint
       __syncwarp();
       for (int k = L - 1; k >= 0; --k) {
         const uint2 ins = wprog[k];
@@ -111,8 +115,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
         const uint32_t opc = ins.x & 0xffu;
         const int feat = (int)(ins.x >> 8);
         const float c = __uint_as_float(ins.y);
-        const float g = adj[32 * k + lane];
-        float ge = 0.f;       // contribution to this instruction's ERC
+        const float g = V[32 * k + lane];  // adjoint of instruction k
+        float ge = 0.f;                    // contribution to this instruction's ERC
         bool has_erc = false;
         if (opc == I_LDF0 || (opc >= I_LDF && opc < I_LDF + 8)) {
           // feature push: nothing to propagate
@@ -120,27 +124,26 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
           ge = g;
           has_erc = true;
         } else if (opc >= I_UN && opc < I_UN + NUNARY) {
-          const float x = tape[32 * ax.src_l + lane];
-          adj[32 * ax.src_l + lane] = g * dun((int)(opc - I_UN), x, tape[32 * k + lane]);
+          float* vx = &V[32 * ax.src_l + lane];
+          *vx = g * dun((int)(opc - I_UN), *vx);
         } else if (opc >= I_BF && opc < I_BS) {
           const int grp = (int)(opc - I_BF) / NKIND;  // 0 BF, 1 BC, 2 LF, 3 LC
           const int kind = (int)(opc - I_BF) % NKIND;
-          const float out = tape[32 * k + lane];
-          float a, b, da, db;
+          float da, db;
           if (grp <= 1) {
-            a = tape[32 * ax.src_l + lane];
-            b = grp == 0 ? p.X[(size_t)feat * p.ldx + rr] : c;
-            dbin(kind, a, b, out, da, db);
-            adj[32 * ax.src_l + lane] = g * da;
+            float* va = &V[32 * ax.src_l + lane];
+            const float b = grp == 0 ? p.X[(size_t)feat * p.ldx + rr] : c;
+            dbin(kind, *va, b, da, db);
+            *va = g * da;
             if (grp == 1) {
               ge = g * db;
               has_erc = true;
             }
           } else {
-            a = grp == 2 ? p.X[(size_t)feat * p.ldx + rr] : c;
-            b = tape[32 * ax.src_r + lane];
-            dbin(kind, a, b, out, da, db);
-            adj[32 * ax.src_r + lane] = g * db;
+            float* vb = &V[32 * ax.src_r + lane];
+            const float a = grp == 2 ? p.X[(size_t)feat * p.ldx + rr] : c;
+            dbin(kind, a, *vb, da, db);
+            *vb = g * db;
             if (grp == 3) {
               ge = g * da;
               has_erc = true;
@@ -148,18 +151,22 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
           }
         } else if (opc >= I_BS && opc < I_LDF) {
           const int kind = (int)((opc - (opc < I_RS ? I_BS : I_RS)) / 8u);
-          const float a = tape[32 * ax.src_l + lane];
-          const float b = tape[32 * ax.src_r + lane];
+          float* va = &V[32 * ax.src_l + lane];
+          float* vb = &V[32 * ax.src_r + lane];
           float da, db;
-          dbin(kind, a, b, tape[32 * k + lane], da, db);
-          adj[32 * ax.src_l + lane] = g * da;
-          adj[32 * ax.src_r + lane] = g * db;
+          dbin(kind, *va, *vb, da, db);
+          *va = g * da;
+          *vb = g * db;
         }
         if (has_erc) {  // warp-uniform: the same instruction on every lane
-          float s = valid ? ge : 0.f;
+          float sm = valid ? ge : 0.f;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) wg[k] += (double)s;
+          for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+          if (lane == 0) {
+            float2 acc = wg[k];
+            acc_add(acc.x, acc.y, sm);
+            wg[k] = acc;
+          }
         }
         __syncwarp();
       }
@@ -171,8 +178,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       if (opc == I_LDC0 || (opc >= I_LDC && opc < I_LDC + 8)) tp = waux[k].tpos;
       else if ((opc >= I_BC && opc < I_BC + NKIND) || (opc >= I_LC && opc < I_LC + NKIND))
         tp = waux[k].tpos_fused;
-      if (tp >= 0 && tp != NONE16 && wg[k] != 0.0)
-        atomicAdd(p.gacc + (size_t)trial * p.stride + tp, wg[k]);
+      const double gk = (double)wg[k].x + (double)wg[k].y;
+      if (tp >= 0 && tp != NONE16 && gk != 0.0)
+        atomicAdd(p.gacc + (size_t)trial * p.stride + tp, gk);
     }
     __syncwarp();
   }

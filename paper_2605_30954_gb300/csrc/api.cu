@@ -703,13 +703,21 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   // adjoint
   const void* afn = gg::adj_ptr(pl.dmax);
   GG_TRY(prepare_kernel(ds->device, afn));
-  int warps = (int)((ds->smem_optin - 64) / ((size_t)pl.lstride * gg::ADJ_WARP_BYTES_PER_INSTR));
-  if (warps > 8) warps = 8;
-  if (warps < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
+  // Each warp holds its own copy of the program and 32 rows of values, so
+  // shared memory bounds the resident warps: take the CTA size (1..8 warps)
+  // that keeps the most warps resident per SM, the larger CTA on a tie.
+  int warps = 0, nb = 0;
+  const int wmax = (int)((ds->smem_optin - 64) / ((size_t)pl.lstride * gg::ADJ_WARP_BYTES_PER_INSTR));
+  for (int w = wmax < 8 ? wmax : 8; w >= 1; --w) {
+    int n = 0;
+    GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, afn, w * 32, gg::adj_smem_bytes(w, pl.lstride)));
+    if (n * w > nb * warps) {
+      warps = w;
+      nb = n;
+    }
+  }
+  if (warps < 1 || nb < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
   const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride);
-  int nb = 0;
-  GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, afn, warps * 32, asmem));
-  if (nb < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "adjoint does not fit on an SM");
   const long long slots = (long long)nb * ds->sms * warps;
   long long n_chunks = (8 * slots + b->n - 1) / b->n;
   const long long max_chunks = (ds->N + 31) / 32;

@@ -47,7 +47,9 @@ struct TransposeParams {
   int N, F, ldx;
 };
 
-constexpr int ADJ_WARP_BYTES_PER_INSTR = 8 + 8 + 2 * 32 * 4 + 8;
+// per warp and program instruction: word, side information, (hi, lo)
+// gradient accumulator, and one value or adjoint for each of 32 rows
+constexpr int ADJ_WARP_BYTES_PER_INSTR = 8 + 8 + 8 + 32 * 4;
 
 inline size_t adj_smem_bytes(int warps, int lstride) {
   return (size_t)warps * lstride * ADJ_WARP_BYTES_PER_INSTR + 16;
