@@ -12,7 +12,7 @@ import numpy as np
 
 __all__ = [
     "ADD", "SUB", "MUL", "AQ", "SIN", "COS", "EXP", "LOG_ABS", "SQRT_ABS", "DIV",
-    "SQUARE", "LOG", "SQRT", "ERC", "FEAT0", "PAD", "BINARY", "UNARY", "BIG",
+    "SQUARE", "LOG", "SQRT", "POW", "ERC", "FEAT0", "PAD", "BINARY", "UNARY", "BIG",
     "VAR_TOL", "InvalidTemplate", "Template", "active_mask", "rpn", "paper_encoding",
     "eval_tree", "eval_tree_f32", "eval_tree_perturbed", "condition_bound", "fitness", "grad",
     "fd_grad", "eval_batch",
@@ -21,11 +21,11 @@ __all__ = [
 # Template opcodes: the library's documented interface values.
 ADD, SUB, MUL, AQ = 0, 1, 2, 3
 SIN, COS, EXP, LOG_ABS, SQRT_ABS = 4, 5, 6, 7, 8
-DIV, SQUARE, LOG, SQRT = 9, 10, 11, 12
+DIV, SQUARE, LOG, SQRT, POW = 9, 10, 11, 12, 13
 ERC = 31
 FEAT0 = 32
 PAD = 255
-BINARY = (ADD, SUB, MUL, AQ, DIV)
+BINARY = (ADD, SUB, MUL, AQ, DIV, POW)
 UNARY = (SIN, COS, EXP, LOG_ABS, SQRT_ABS, SQUARE, LOG, SQRT)
 
 #: READING: a trial whose output exceeds this magnitude at any row (or is
@@ -152,9 +152,13 @@ def paper_encoding(t: Template):
 def _apply(o, a, b=None, xp=np):
     """One function node.  AQ(a, b) = a / sqrt(1 + b^2) (analytic quotient,
     Ni, Drieberg and Rockett 2013); log|x| and sqrt|x| are the protected
-    forms of the function set; DIV, SQUARE, LOG and SQRT are the paper's
-    Table 2 operators (plain division, square, unprotected log and sqrt).
-    Binary operands in template order: op(left, right)."""
+    forms of the function set; DIV, SQUARE, LOG, SQRT and POW are the paper's
+    Table 2 operators (plain division, square, unprotected log and sqrt,
+    power).  READING: pow(a, b) = a^b with the IEEE 754 / C99 pow special
+    cases (Table 2 names pow without a definition): a negative base with a
+    non-integer exponent gives NaN, 0 to a negative power gives inf, and
+    x^0 = 1 for every x.  Binary operands in template order: op(left,
+    right), so the left child is the base."""
     if o == ADD:
         return a + b
     if o == SUB:
@@ -166,6 +170,8 @@ def _apply(o, a, b=None, xp=np):
         return a / np.sqrt(one + b * b)
     if o == DIV:
         return a / b
+    if o == POW:
+        return np.power(a, b)
     if o == SIN:
         return np.sin(a)
     if o == COS:
@@ -314,7 +320,10 @@ def fitness(f: np.ndarray, y: np.ndarray) -> dict:
 
 def _dapply(o, a, b, out):
     """Local partial derivatives of one function node at its inputs (a, b)
-    and its output ``out``.  READING at kinks: d sqrt|x| / dx = 0 at x = 0."""
+    and its output ``out``.  READING at kinks: d sqrt|x| / dx = 0 at x = 0.
+    READING for pow: d a^b / da = b a^(b-1); d a^b / db = a^b ln|a|, which
+    for a < 0 (integer b) is the real part of the derivative of the
+    principal complex power, and 0 where a^b = 0."""
     one = 1.0
     if o == ADD:
         return np.ones_like(a), np.ones_like(b)
@@ -327,6 +336,8 @@ def _dapply(o, a, b, out):
         return q, -a * b * q * q * q
     if o == DIV:
         return one / b, -a / (b * b)
+    if o == POW:
+        return b * np.power(a, b - one), np.where(out == 0, 0.0, out * np.log(np.abs(a)))
     if o == SIN:
         return np.cos(a), None
     if o == COS:

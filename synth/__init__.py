@@ -28,20 +28,20 @@ import numpy as np
 # ---- template opcodes (interface values) ---------------------------------
 ADD, SUB, MUL, AQ = 0, 1, 2, 3
 SIN, COS, EXP, LOG_ABS, SQRT_ABS = 4, 5, 6, 7, 8
-DIV, SQUARE, LOG, SQRT = 9, 10, 11, 12
+DIV, SQUARE, LOG, SQRT, POW = 9, 10, 11, 12, 13
 ERC = 31
 FEAT0 = 32
 PAD = 255
 
-BINARY = (ADD, SUB, MUL, AQ, DIV)
+BINARY = (ADD, SUB, MUL, AQ, DIV, POW)
 UNARY = (SIN, COS, EXP, LOG_ABS, SQRT_ABS, SQUARE, LOG, SQRT)
 
 #: function set of the small plain-evaluation workload
 BASIC_SET = (ADD, SUB, MUL, AQ)
 #: the full function set {+, -, *, AQ, sin, cos, exp, log|x|, sqrt|x|}
 FULL_SET = (ADD, SUB, MUL, AQ, SIN, COS, EXP, LOG_ABS, SQRT_ABS)
-#: the paper's Table 2 operator set for Experiments I/II, minus pow
-PAPER_SET = (ADD, SUB, MUL, DIV, SIN, COS, SQUARE, SQRT, EXP, LOG)
+#: the paper's Table 2 operator set for Experiments I/II
+PAPER_SET = (ADD, SUB, MUL, DIV, SIN, COS, SQUARE, SQRT, EXP, LOG, POW)
 #: the paper's Table 2 operator set for Experiment III
 EXP3_SET = (ADD, SUB, MUL, DIV, SQUARE, SQRT)
 
@@ -189,6 +189,12 @@ CONFIGS = {
                N=1_000_000, F=10, x=("uniform", -1.0, 1.0), y_h=6, y_funcs=FULL_SET,
                noise=0.01, fos=True),
 }
+# The FOS-step shape over the paper's Experiments I/II operator set
+# (Table 2, with pow); positive features so that log, sqrt and pow of a
+# feature are defined
+CONFIGS["t2"] = dict(index=10, name="table2-ops-4096xh4-100000x8", P=4_096, h=4,
+                     funcs=PAPER_SET, N=100_000, F=8, x=("uniform", 0.5, 3.0), y_h=4,
+                     y_funcs=PAPER_SET, noise=0.01, fos=True)
 # Experiment III ladder (Table 1): 100,000 x 9, depth-6 templates over the
 # Experiment III operators, the starting population of 2,000; X ~ U[1, 5]
 # (the paper does not state the sampling distribution)
@@ -217,6 +223,7 @@ def workload(cfg: str, rep: int = 0, n_rows: int | None = None,
              values are finite with nonzero variance
     z        float64 [N] standard-normal draws for the target noise
     noise    noise fraction (sigma = noise * std(f_gen))
+    uses_pow whether the trials' function set has pow
     """
     c = CONFIGS[cfg]
     ss = np.random.SeedSequence(seed_of(cfg, rep))
@@ -257,7 +264,7 @@ def workload(cfg: str, rep: int = 0, n_rows: int | None = None,
 
     out = dict(cfg=cfg, name=c["name"], X=X, op=op, cval=cval, heights=heights,
                h_max=h_max, layout=layout, y_cands=y_cands if "target" not in c else None,
-               z=z, noise=float(c["noise"]), N=N, P=P, F=F)
+               z=z, noise=float(c["noise"]), N=N, P=P, F=F, uses_pow=POW in c["funcs"])
     if "target" in c:  # a closed-form target (Table 1), given directly
         out["y"] = LADDER[c["target"]](X.astype(np.float64)).astype(np.float32)
     return out

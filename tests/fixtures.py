@@ -11,12 +11,12 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 # interface opcodes, written out as in the header
 ADD, SUB, MUL, AQ = 0, 1, 2, 3
 SIN, COS, EXP, LOG_ABS, SQRT_ABS = 4, 5, 6, 7, 8
-DIV, SQUARE, LOG, SQRT = 9, 10, 11, 12
+DIV, SQUARE, LOG, SQRT, POW = 9, 10, 11, 12, 13
 ERC, FEAT0, PAD = 31, 32, 255
 
 TOKENS = {"+": ADD, "-": SUB, "*": MUL, "aq": AQ, "sin": SIN, "cos": COS,
           "exp": EXP, "logabs": LOG_ABS, "sqrtabs": SQRT_ABS, "/": DIV,
-          "sq": SQUARE, "log": LOG, "sqrt": SQRT}
+          "sq": SQUARE, "log": LOG, "sqrt": SQRT, "pow": POW}
 
 
 def token_to_node(tok):

@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import synth
-from fixtures import (ADD, AQ, COS, DIV, ERC, EXP, FEAT0, LOG, LOG_ABS, MUL, PAD,
+from fixtures import (ADD, AQ, COS, DIV, ERC, EXP, FEAT0, LOG, LOG_ABS, MUL, PAD, POW,
                       SIN, SQRT, SQRT_ABS, SQUARE, SUB, fig1, heap_template)
 
 
@@ -73,6 +73,7 @@ X2 = np.array([[2.0, 5.0], [3.0, 4.0], [6.0, 3.0], [-3.0, 0.0]])
     ("*", [10.0, 12.0, 18.0, -0.0]),
     ("aq", [2 / math.sqrt(26), 3 / math.sqrt(17), 6 / math.sqrt(10), -3.0]),
     ("/", [0.4, 0.75, 2.0, -math.inf]),
+    ("pow", [32.0, 81.0, 216.0, 1.0]),
 ])
 def test_binary_hand_values(tok, want):
     t = T([tok, "x0", "x1"], 1)
@@ -97,6 +98,32 @@ def test_unprotected_log_sqrt_nan_and_protected_zero():
     assert np.isnan(O.eval_tree(T(["sqrt", "x0", "x1"], 1), X)[0])
     assert O.eval_tree(T(["logabs", "x1", "x0"], 1), X)[0] == -math.inf
     assert O.eval_tree(T(["sqrtabs", "x1", "x0"], 1), X)[0] == 0.0
+
+
+def test_pow_special_cases_and_reductions():
+    """pow(a, b) follows C99 pow: a negative base with an integer exponent is
+    defined, with a non-integer exponent it is NaN (so the fitness is +inf),
+    0 to a negative power is inf; x^2 and x^0.5 reduce to the square and the
+    square root."""
+    t = T(["pow", "x0", "x1"], 1)
+    got = O.eval_tree(t, np.array([[-2.0, 3.0], [-2.0, 0.5], [0.0, -1.0], [4.0, -0.5]]))
+    assert got[0] == -8.0 and np.isnan(got[1]) and got[2] == math.inf and got[3] == 0.5
+    assert not O.fitness(got, np.arange(4.0))["finite"]
+    X = np.random.default_rng(4).uniform(0.1, 3.0, (64, 1))
+    np.testing.assert_allclose(O.eval_tree(T(["pow", "x0", "2"], 1), X), X[:, 0] ** 2, rtol=1e-15)
+    np.testing.assert_allclose(O.eval_tree(T(["pow", "x0", "0.5"], 1), X), np.sqrt(X[:, 0]),
+                               rtol=1e-15)
+
+
+def test_pow_exponent_derivative_at_negative_base():
+    """READING: d a^b / db at a < 0 and integer b is the real part of the
+    derivative of the principal complex power, a^b (ln|a| + i pi)."""
+    a = np.array([-2.0, -0.5, -3.0])
+    b = np.array([3.0, 2.0, -1.0])
+    out = np.power(a, b)
+    _, db = O.gp._dapply(POW, a, b, out)
+    want = np.real(np.power(a.astype(complex), b) * np.log(a.astype(complex)))
+    np.testing.assert_allclose(db, want, rtol=1e-14)
 
 
 def test_height2_hand_value():
@@ -254,6 +281,10 @@ OP_TREES = [
     ["+", "sq", "x0", "-", None, None, None, "x1", "0.6"],
     ["+", "log", "x2", "+", None, None, None, "x0", "4.5"],
     ["+", "sqrt", "x2", "+", None, None, None, "x1", "4.5"],
+    ["pow", "sqrtabs", "+", "x0", None, "x1", "0.5"],
+    ["pow", "1.3", "sin", None, None, "x0"],
+    ["pow", "sqrtabs", "0.8", "x2"],
+    ["pow", "exp", "+", "*", None, "x1", "x2", "x0", "0.3"],
 ]
 
 
@@ -363,7 +394,7 @@ PINS = [test_fig1_rpn_and_encoding, test_fig1_value_is_printed_expression,
         lambda: test_reverse_mode_matches_central_fd("smse"),
         lambda: [test_binary_hand_values(k, w) for k, w in [
             ("-", [-3.0, -1.0, 3.0, -3.0]), ("aq", [2 / math.sqrt(26), 3 / math.sqrt(17), 6 / math.sqrt(10), -3.0]),
-            ("/", [0.4, 0.75, 2.0, -math.inf])]],
+            ("/", [0.4, 0.75, 2.0, -math.inf]), ("pow", [32.0, 81.0, 216.0, 1.0])]],
         lambda: test_unary_hand_values_use_left_child("sin", math.pi / 6, 0.5),
         test_intron_invariance_random_trees]
 
@@ -386,6 +417,8 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         "aq drops the +1": lambda o, a, b=None, xp=np: (a / np.sqrt(b * b)) if o == AQ else real_apply(o, a, b),
         "div transposed": lambda o, a, b=None, xp=np: (b / a) if o == DIV else real_apply(o, a, b),
         "mul as add": lambda o, a, b=None, xp=np: (a + b) if o == MUL else real_apply(o, a, b),
+        "pow operands swapped": lambda o, a, b=None, xp=np: (np.power(b, a)) if o == POW
+        else real_apply(o, a, b),
     }
     for name, fn in mistakes.items():
         monkeypatch.setattr(gp, "_apply", fn)
