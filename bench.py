@@ -42,18 +42,19 @@ UNIT = "node-row evals/s"
 CFG = "c2"
 SMS, FP32_LANES, SFU_LANES = 152, 128, 16
 # algorithmic FP32 / SFU operations per evaluated node (by class) and per
-# row-trial for the fitness sums (shift, sum d, sum d^2, sum d*y)
+# row-trial for the fitness sums (shift, sum d, sum d^2, sum d*y); pow counts
+# as 2^(b log2 a): one multiply, two SFU operations
 OPS_FP32 = {"term": 0, "addsubmul": 1, "aq": 2, "div": 1, "sincos": 2, "exp": 1, "log": 1,
-            "sqrt": 0, "square": 1}
+            "sqrt": 0, "square": 1, "pow": 1}
 OPS_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, "log": 1,
-           "sqrt": 1, "square": 0}
+           "sqrt": 1, "square": 0, "pow": 2}
 ACC_FP32 = 4
 # DRAM bytes (read + write) of one batched-forward launch from the ncu
 # capture summarised in profiles/fwd_kernel_fos-step-4096xh4-100000x8.md;
 # None for a workload without a capture of the current kernel
 NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4275200 + 9472}
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
-             "sqrt": 8, "square": 9}
+             "sqrt": 8, "square": 9, "pow": 12}
 
 
 def parse():
@@ -264,13 +265,14 @@ def run_extra_mode(a, gg, torch):
     dev = 0
     torch.cuda.set_device(dev)
     w = make_workload(a.config, 0, gg, torch, dev)
+    PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
     nodes, _, _, valid, _ = node_counts(gg, torch, w)
     N, P = w["N"], w["P"]
     ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
     op = torch.from_numpy(w["op"]).cuda(dev)
     cv = torch.from_numpy(w["cval"]).cuda(dev)
     hs = torch.from_numpy(w["heights"]).cuda(dev) if "h_min" in synth.CONFIGS[a.config] else None
-    ds.autotune(op, cv, hs)
+    ds.autotune(op, cv, hs, flags=PF)
     st = torch.cuda.Stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
@@ -284,10 +286,10 @@ def run_extra_mode(a, gg, torch):
         dc = torch.empty_like(cv)
 
         def step(t):
-            ds.grad_batch(op, cv, hs, stream=st, smse=smse, dcval=dc)
+            ds.grad_batch(op, cv, hs, flags=PF, stream=st, smse=smse, dcval=dc)
             gg.adam_step(op, cv, dc, m, v, t, lr=0.05, stream=st)
         with torch.cuda.stream(st):
-            s0 = ds.eval_batch(op, cv, hs, stream=st)[0].clone()
+            s0 = ds.eval_batch(op, cv, hs, flags=PF, stream=st)[0].clone()
             for t in range(1, a.warmup + 1):
                 step(t)
         st.synchronize()
@@ -299,7 +301,7 @@ def run_extra_mode(a, gg, torch):
             e1.record(st)
         st.synchronize()
         ms = e0.elapsed_time(e1) / a.steps
-        s1 = ds.eval_batch(op, cv, hs)[0]
+        s1 = ds.eval_batch(op, cv, hs, flags=PF)[0]
         ds.sync()
         fin = torch.isfinite(s0) & torch.isfinite(s1)
         line.update(value=nodes * N / (ms * 1e-3), ms_per_step=ms,
@@ -319,7 +321,7 @@ def run_extra_mode(a, gg, torch):
         off_d, nodes_d = torch.from_numpy(off).cuda(), torch.from_numpy(fnodes).cuda()
         pop_op, pop_cv = op.clone(), cv.clone()
         O_op, O_cv, B_op, B_cv = op.clone(), cv.clone(), op.clone(), cv.clone()
-        f_b = ds.eval_batch(O_op, O_cv, hs)[0].clone()
+        f_b = ds.eval_batch(O_op, O_cv, hs, flags=PF)[0].clone()
         f_new = torch.empty(P, device="cuda")
         changed_total = torch.zeros((), dtype=torch.int64, device="cuda")
 
@@ -329,7 +331,8 @@ def run_extra_mode(a, gg, torch):
                               stream=st)
                 ch = gg.gom_changed(O_op, O_cv, B_op, B_cv, w["F"], hs, stream=st)
                 changed_total.add_(ch.sum())
-                ds.eval_batch_masked(O_op, O_cv, ch, hs, stream=st, out=[f_new, None, None, None])
+                ds.eval_batch_masked(O_op, O_cv, ch, hs, flags=PF, stream=st,
+                                     out=[f_new, None, None, None])
                 gg.gom_accept(O_op, O_cv, B_op, B_cv, f_new, f_b, ch, stream=st)
         with torch.cuda.stream(st):
             sweep()
@@ -391,20 +394,21 @@ def main():
     ops = {"max": pg.ReduceOp.MAX if pg else None, "sum": pg.ReduceOp.SUM if pg else None}
 
     w = make_workload(a.config, rank, gg, torch, dev)
+    PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
     nodes, fp32_ops, sfu_ops, valid, instrs = node_counts(gg, torch, w)
     N, P = w["N"], w["P"]
     ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
     op = torch.from_numpy(w["op"]).cuda(dev)
     cv = torch.from_numpy(w["cval"]).cuda(dev)
     hs = torch.from_numpy(w["heights"]).cuda(dev) if "h_min" in synth.CONFIGS[a.config] else None
-    ds.autotune(op, cv, hs)
+    ds.autotune(op, cv, hs, flags=PF)
     st = torch.cuda.Stream(dev)
     outs = [torch.empty(P, device=f"cuda:{dev}") for _ in range(4)]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     torch.cuda.synchronize()
 
     def graph_step():
-        ds.eval_batch(op, cv, hs, flags=gg.F_GRAPH, stream=st, out=outs)
+        ds.eval_batch(op, cv, hs, flags=gg.F_GRAPH | PF, stream=st, out=outs)
 
     def timed(fn, steps, clocks=None, name="timed"):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -443,7 +447,7 @@ def main():
 
     # ---- forward kernel alone: live CUDA events around it (roofline) ----
     def prof_step():
-        ds.eval_batch(op, cv, hs, flags=gg.F_PROFILE, stream=st, out=outs)
+        ds.eval_batch(op, cv, hs, flags=gg.F_PROFILE | PF, stream=st, out=outs)
     for _ in range(2):
         with torch.cuda.stream(st):
             prof_step()
@@ -464,7 +468,7 @@ def main():
 
     # ---- plain form: one launch per trial ----
     def plain_step():
-        ds.eval_plain(op, cv, hs, stream=st, out=outs)
+        ds.eval_plain(op, cv, hs, flags=PF, stream=st, out=outs)
     with torch.cuda.stream(st):
         plain_step()
     st.synchronize()
@@ -479,7 +483,7 @@ def main():
     hout = [torch.empty(P, dtype=torch.float32).pin_memory(), None, None, None]
 
     def e2e_step():
-        ds.eval_batch(hop, hcv, hhs, stream=st, out=hout)
+        ds.eval_batch(hop, hcv, hhs, flags=PF, stream=st, out=hout)
     for _ in range(a.warmup):
         with torch.cuda.stream(st):
             e2e_step()

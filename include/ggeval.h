@@ -72,9 +72,11 @@ enum { GGEVAL_MEM_DEVICE = 0, GGEVAL_MEM_HOST = 1 };
 /* Template node opcodes (one uint8 per node).
  * Functions: binary operands are (left child, right child); a unary
  * function reads its left child and its right subtree is an intron.
- * AQ(a, b) = a / sqrt(1 + b^2) (analytic quotient).  DIV, SQUARE, LOG and
- * SQRT are the paper's Table 2 operators (plain division, x^2, unprotected
- * log and sqrt).  Terminals: ERC reads the node's constant from cval;
+ * AQ(a, b) = a / sqrt(1 + b^2) (analytic quotient).  DIV, SQUARE, LOG,
+ * SQRT and POW are the paper's Table 2 operators (plain division, x^2,
+ * unprotected log and sqrt, and pow(left, right) = left^right with the C99
+ * powf special cases: NaN, so +inf fitness, for a negative base and a
+ * non-integer exponent).  Terminals: ERC reads the node's constant from cval;
  * FEATURE0 + k reads feature k (k < n_features).  The root is active; the
  * children of an active function are active (only the left child of a
  * unary one); a terminal's subtree is an intron.  Introns may hold any
@@ -86,6 +88,7 @@ enum {
   GGEVAL_OP_SIN = 4, GGEVAL_OP_COS = 5, GGEVAL_OP_EXP = 6,
   GGEVAL_OP_LOG_ABS = 7, GGEVAL_OP_SQRT_ABS = 8,
   GGEVAL_OP_DIV = 9, GGEVAL_OP_SQUARE = 10, GGEVAL_OP_LOG = 11, GGEVAL_OP_SQRT = 12,
+  GGEVAL_OP_POW = 13,
   GGEVAL_OP_ERC = 31,
   GGEVAL_OP_FEATURE0 = 32,
   GGEVAL_OP_PAD = 255
@@ -120,9 +123,15 @@ enum {
                                  default picks them for small row counts   */
   GGEVAL_F_GRAD_MSE = 1u << 2,/* ggeval_grad_batch: gradient of plain MSE
                                  instead of scaled MSE                     */
-  GGEVAL_F_PROFILE = 1u << 3  /* record CUDA events around the batched
+  GGEVAL_F_PROFILE = 1u << 3, /* record CUDA events around the batched
                                  forward kernel (not with GGEVAL_F_GRAPH);
                                  read them with ggeval_profile_read        */
+  GGEVAL_F_POW = 1u << 4      /* the batch may hold active POW nodes: run
+                                 the kernel builds that include pow.
+                                 Without it an active POW node is an
+                                 invalid template (GGEVAL_ERR_TEMPLATE); the
+                                 other kernels leave the pow code out
+                                 because it costs them registers and speed */
 };
 
 /* Create a dataset from X (n_rows x n_features, float32, row-major when
@@ -159,7 +168,8 @@ ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* batch,
 
 /* Per-row values f_i of every trial (float [n][n_rows], batch memory), the
  * quantity each "sub-evaluation" of Section 3.2 squares.  For checking and
- * for building targets; not the fast path. */
+ * for building targets; not the fast path (it accepts POW nodes without a
+ * flag). */
 ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* batch,
                                float* f, void* stream);
 
@@ -217,9 +227,10 @@ const char* ggeval_last_error(void);
  * of active nodes by class.  out is int64 [n][GGEVAL_NSTAT] host memory:
  * [0] active nodes, [1] terminals, [2] +/-/x, [3] AQ, [4] DIV,
  * [5] sin/cos, [6] exp, [7] log, [8] sqrt, [9] square; [10] interpreter
- * instructions after fusion; [11] stack slots used.  An invalid trial has
- * -1 in [0].  Host batches only; runs on the CPU, no dataset needed. */
-#define GGEVAL_NSTAT 12
+ * instructions after fusion; [11] stack slots used; [12] pow.  An invalid
+ * trial has -1 in [0].  Host batches only; runs on the CPU, no dataset
+ * needed. */
+#define GGEVAL_NSTAT 13
 ggeval_status ggeval_batch_stats(const ggeval_batch* batch, int32_t n_features,
                                  int64_t* out);
 
@@ -297,8 +308,8 @@ ggeval_status ggeval_dataset_info(const ggeval_dataset* ds, int64_t* n_rows,
  * the device-wide synchronisation cudaMalloc implies, and processes whose
  * device memory is budgeted up front.  ggeval_eval_batch may grow its
  * workspace on such a call; this entry point never does.  It computes the
- * same outputs as ggeval_eval_batch (same definitions, same error rules)
- * for a device batch on an existing dataset, using as scratch one static
+ * same outputs as ggeval_eval_batch with flags 0 (same definitions, same
+ * error rules; so no POW nodes) for a device batch on an existing dataset, using as scratch one static
  * device array of GGEVAL_NOALLOC_SCRATCH_BYTES that every GPU loading this
  * library holds until the process exits.  (The paper has no counterpart:
  * it is a deployment form of the batched evaluation, not part of the

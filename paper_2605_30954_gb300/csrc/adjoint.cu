@@ -36,6 +36,12 @@ __device__ __forceinline__ void dbin(int kind, float a, float b, float& da, floa
       db = -a * b * q * q * q;
       break;
     }
+    case K_POW: {  // d/da = b a^(b-1); d/db = a^b ln|a| (0 where a^b = 0)
+      const float out = powf(a, b);
+      da = b * powf(a, b - 1.f);
+      db = out == 0.f ? 0.f : out * logf(fabsf(a));
+      break;
+    }
     default: {  // K_DIV: d/da = 1/b, d/db = -(a/b)/b
       da = 1.f / b;
       db = -(a / b) / b;
@@ -57,7 +63,7 @@ __device__ __forceinline__ float dun(int u, float x) {
   }
 }
 
-template <int DMAX>
+template <int DMAX, bool POW>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       const bool valid = row < r_end;
       const int rr = valid ? row : r_end - 1;
       float A[1] = {0.f};
-      run_program<DMAX, 1, true>(wprog, L, p.X + rr, p.ldx, A, S, V + lane);
+      run_program<DMAX, 1, true, false, POW>(wprog, L, p.X + rr, p.ldx, A, S, V + lane);
       const float f = A[0];
       const float yc = p.X[(size_t)p.F * p.ldx + rr];
       float w = p.mse_mode ? two_n * (f - ybar - yc) : two_n * bb * (a_c + bb * f - yc);
@@ -126,9 +132,10 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
         } else if (opc >= I_UN && opc < I_UN + NUNARY) {
           float* vx = &V[32 * ax.src_l + lane];
           *vx = g * dun((int)(opc - I_UN), *vx);
-        } else if (opc >= I_BF && opc < I_BS) {
-          const int grp = (int)(opc - I_BF) / NKIND;  // 0 BF, 1 BC, 2 LF, 3 LC
-          const int kind = (int)(opc - I_BF) % NKIND;
+        } else if ((opc >= I_BF && opc < I_BS) || (POW && opc >= I_PW && opc < I_PWS)) {
+          const bool pw = POW && opc >= I_PW;
+          const int grp = pw ? (int)(opc - I_PW) : (int)(opc - I_BF) / NKIND;  // 0 BF, 1 BC, 2 LF, 3 LC
+          const int kind = pw ? K_POW : (int)(opc - I_BF) % NKIND;
           float da, db;
           if (grp <= 1) {
             float* va = &V[32 * ax.src_l + lane];
@@ -149,8 +156,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
               has_erc = true;
             }
           }
-        } else if (opc >= I_BS && opc < I_LDF) {
-          const int kind = (int)((opc - (opc < I_RS ? I_BS : I_RS)) / 8u);
+        } else if ((opc >= I_BS && opc < I_LDF) || (POW && opc >= I_PWS && opc < I_COUNT)) {
+          const int kind =
+              POW && opc >= I_PWS ? K_POW : (int)((opc - (opc < I_RS ? I_BS : I_RS)) / 8u);
           float* va = &V[32 * ax.src_l + lane];
           float* vb = &V[32 * ax.src_r + lane];
           float da, db;
@@ -176,7 +184,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       const uint32_t opc = wprog[k].x & 0xffu;
       int tp = -1;
       if (opc == I_LDC0 || (opc >= I_LDC && opc < I_LDC + 8)) tp = waux[k].tpos;
-      else if ((opc >= I_BC && opc < I_BC + NKIND) || (opc >= I_LC && opc < I_LC + NKIND))
+      else if ((opc >= I_BC && opc < I_BC + NKIND) || (opc >= I_LC && opc < I_LC + NKIND) ||
+               (POW && (opc == I_PW + 1 || opc == I_PW + 3)))
         tp = waux[k].tpos_fused;
       const double gk = (double)wg[k].x + (double)wg[k].y;
       if (tp >= 0 && tp != NONE16 && gk != 0.0)
@@ -186,11 +195,14 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   }
 }
 
-const void* adj_ptr(int dmax) {
+const void* adj_ptr(int dmax, bool pow) {
   switch (dmax) {
-    case 3: return reinterpret_cast<const void*>(&adjoint_kernel<3>);
-    case 5: return reinterpret_cast<const void*>(&adjoint_kernel<5>);
-    case 7: return reinterpret_cast<const void*>(&adjoint_kernel<7>);
+    case 3: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<3, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<3, false>);
+    case 5: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<5, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<5, false>);
+    case 7: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<7, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<7, false>);
     default: return nullptr;
   }
 }

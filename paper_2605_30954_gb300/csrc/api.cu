@@ -69,13 +69,16 @@ inline int pack_threads(int stride) {
 inline int dmax_of(int h) { return h <= 4 ? 3 : (h <= 6 ? 5 : 7); }
 inline int lstride_of(int h) { return stride_of(h) + 1; }
 
-const void* fwd_ptr(int dmax, int variant) {
+const void* fwd_ptr(int dmax, int variant, bool pow) {
   switch (dmax) {
-    case 3: return gg::fwd_ptr_d3(variant);
-    case 5: return gg::fwd_ptr_d5(variant);
-    default: return gg::fwd_ptr_d7(variant);
+    case 3: return pow ? gg::fwd_ptr_d3_pow(variant) : gg::fwd_ptr_d3(variant);
+    case 5: return pow ? gg::fwd_ptr_d5_pow(variant) : gg::fwd_ptr_d5(variant);
+    default: return pow ? gg::fwd_ptr_d7_pow(variant) : gg::fwd_ptr_d7(variant);
   }
 }
+
+// GGEVAL_F_POW selects the kernels that run pow instructions.
+inline bool has_pow(uint32_t flags) { return (flags & GGEVAL_F_POW) != 0; }
 
 // Raise the dynamic shared-memory limit of a kernel once per device.
 ggeval_status prepare_kernel(int device, const void* fn) {
@@ -100,6 +103,7 @@ struct Cfg {
 
 struct Plan {
   Cfg cfg;
+  bool pow = false;  // kernels with the pow instructions; the packer accepts pow
   int dmax = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
   size_t smem = 0;
   const void* fn = nullptr;
@@ -222,12 +226,14 @@ Cfg default_cfg(const ggeval_dataset* ds, int n, int h_max, uint32_t flags) {
   return c;
 }
 
-ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Plan* pl) {
+ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Plan* pl,
+                        bool pow) {
   pl->cfg = cfg;
+  pl->pow = pow;
   pl->dmax = dmax_of(h_max);
   pl->stride = stride_of(h_max);
   pl->lstride = lstride_of(h_max);
-  pl->fn = fwd_ptr(pl->dmax, cfg.variant);
+  pl->fn = fwd_ptr(pl->dmax, cfg.variant, pow);
   if (!pl->fn) return fail(GGEVAL_ERR_ARG, "no kernel for variant %d", cfg.variant);
   const int rpp = 32 * gg::variant_rows(cfg.variant);
   if (cfg.tile_rows < rpp || cfg.tile_rows % rpp || cfg.group < 1 || cfg.warps < 1 ||
@@ -251,7 +257,8 @@ ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Pl
 }
 
 Cfg pick_cfg(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags) {
-  auto it = ds->tuned.find({b->n, b->max_height, b->layout, (int)(flags & GGEVAL_F_EXACT)});
+  auto it = ds->tuned.find(
+      {b->n, b->max_height, b->layout, (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW))});
   if (it != ds->tuned.end()) return it->second;
   return default_cfg(ds, b->n, b->max_height, flags);
 }
@@ -326,6 +333,7 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.len = ds->len;
   pp.status = ds->status;
   pp.mask = mask;
+  pp.allow_pow = pl.pow ? 1 : 0;
   const int pt = pack_threads(pl.stride);
   return launch(gg::pack_ptr(), dim3((n + pt - 1) / pt), dim3(pt), (size_t)pt * 2 * pl.stride, st,
                 &pp);
@@ -564,7 +572,7 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan pl;
-  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl));
+  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl, has_pow(flags)));
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   DevBatch db;
@@ -628,7 +636,7 @@ ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* b, float*
   Cfg c = default_cfg(ds, b->n, b->max_height, GGEVAL_F_EXACT);
   c.variant = 3;
   Plan pl;
-  GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl));
+  GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl, true));  // an inspection path: any operator
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   const size_t fbytes = (size_t)b->n * ds->N * 4;
@@ -660,7 +668,7 @@ ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint3
   c.warps = 2;
   c.tile_rows = 32 * gg::variant_rows(c.variant);
   Plan pl;
-  GG_TRY(make_plan(ds, 1, b->max_height, c, &pl));
+  GG_TRY(make_plan(ds, 1, b->max_height, c, &pl, has_pow(flags)));
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   DevBatch db{b->op, b->cval, b->height};
   GG_TRY(enqueue_pack(ds, db, b->n, b->max_height, b->layout, pl, false, st));
@@ -690,7 +698,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan pl;
-  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl));
+  GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl, has_pow(flags)));
   GG_TRY(ensure_ws(ds, b->n, pl, true));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   const size_t gcount = (size_t)b->n * pl.stride;
@@ -701,7 +709,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   float* ds_smse = smse ? (host ? dg + gcount : smse) : nullptr;
   GG_TRY(enqueue_eval(ds, db, b, pl, ds_smse, nullptr, nullptr, nullptr, true, st));
   // adjoint
-  const void* afn = gg::adj_ptr(pl.dmax);
+  const void* afn = gg::adj_ptr(pl.dmax, pl.pow);
   GG_TRY(prepare_kernel(ds->device, afn));
   // Each warp holds its own copy of the program and 32 rows of values, so
   // shared memory bounds the resident warps: take the CTA size (1..8 warps)
@@ -828,7 +836,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   ggeval_status result = GGEVAL_OK;
   for (const Cfg& c : cands) {
     Plan pl;
-    if (make_plan(ds, b->n, b->max_height, c, &pl) != GGEVAL_OK) continue;
+    if (make_plan(ds, b->n, b->max_height, c, &pl, has_pow(flags)) != GGEVAL_OK) continue;
     if ((result = ensure_ws(ds, b->n, pl, false)) != GGEVAL_OK) break;
     if ((result = enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st)) !=
         GGEVAL_OK)
@@ -860,7 +868,8 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   cudaEventDestroy(e1);
   cudaFree(out);
   if (result != GGEVAL_OK) return result;
-  ds->tuned[{b->n, b->max_height, b->layout, (int)(flags & GGEVAL_F_EXACT)}] = best;
+  ds->tuned[{b->n, b->max_height, b->layout, (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW))}] =
+      best;
   drop_graph(ds);
   return GGEVAL_OK;
 }
@@ -999,6 +1008,7 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
     for (int i = 0; i < 10; ++i) o[i] = r.counts[i];
     o[10] = r.len;
     o[11] = r.slots;
+    o[12] = r.counts[10];
   }
   return GGEVAL_OK;
 }
@@ -1099,7 +1109,7 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   Cfg c = default_cfg(ds, b->n, b->max_height, 0);
   while ((ds->N + c.tile_rows - 1) / c.tile_rows > GGEVAL_NOALLOC_MAX_TILES) c.tile_rows *= 2;
   Plan pl;
-  if (make_plan(ds, b->n, b->max_height, c, &pl) != GGEVAL_OK)
+  if (make_plan(ds, b->n, b->max_height, c, &pl, false) != GGEVAL_OK)
     return fail(GGEVAL_ERR_UNSUPPORTED,
                 "eval_batch_noalloc: %lld rows need tiles of %d rows, which do not fit in "
                 "shared memory (at most %d tiles)",

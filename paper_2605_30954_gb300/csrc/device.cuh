@@ -17,7 +17,8 @@ constexpr float OUT_BIG = 1125899906842624.0f;
 
 // ------------------------------------------------------------ the operators
 // AQ(a, b) = a / sqrt(1 + b^2): one FMA, one reciprocal square root (SFU),
-// one multiply.  Division is IEEE (no fast-math).
+// one multiply.  Division is IEEE (no fast-math).  pow(a, b) = a^b with the
+// C99 special cases (NaN for a negative base and a non-integer exponent).
 template <int K>
 __device__ __forceinline__ float binop(float a, float b) {
   if constexpr (K == K_ADD) return a + b;
@@ -25,6 +26,7 @@ __device__ __forceinline__ float binop(float a, float b) {
   if constexpr (K == K_MUL) return a * b;
   if constexpr (K == K_AQ) return a * rsqrtf(fmaf(b, b, 1.0f));
   if constexpr (K == K_DIV) return a / b;
+  if constexpr (K == K_POW) return powf(a, b);
   return 0.f;
 }
 
@@ -128,8 +130,9 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v
 // floats (feature x ts), as the batched kernel rewrites it when it stages a
 // program.  With TAPE (R == 1 only) the value of A after instruction k is
 // stored at tape[32 k] (the caller offsets `tape` by its lane): the forward
-// half of the adjoint.
-template <int DMAX, int R, bool TAPE = false, bool PRESCALED = false>
+// half of the adjoint.  POW adds the pow instructions; without it the
+// program must not contain them.
+template <int DMAX, int R, bool TAPE = false, bool PRESCALED = false, bool POW = false>
 __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
                                             const float* __restrict__ xs, int ts,
                                             float (&A)[R], float (&S)[DMAX][R],
@@ -179,6 +182,23 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
   GG_SLOT_BIN(K_MUL, j)  \
   GG_SLOT_BIN(K_AQ, j)   \
   GG_SLOT_BIN(K_DIV, j)
+// pow (POW kernels only): every form moves its operands into (A = base,
+// t = exponent) and one shared body follows, so the library pow is
+// expanded once.
+#define GG_SLOT_POW(j)                                                \
+  case I_PWS + j:                                                     \
+    if (j < DMAX) {                                                   \
+      GG_ROWS {                                                       \
+        t[r] = A[r];                                                  \
+        A[r] = S[j < DMAX ? j : 0][r];                                \
+      }                                                               \
+    }                                                                 \
+    break;                                                            \
+  case I_PWR + j:                                                     \
+    if (j < DMAX) {                                                   \
+      GG_ROWS t[r] = S[j < DMAX ? j : 0][r];                          \
+    }                                                                 \
+    break;
 #define GG_PUSH(j)                                                    \
   case I_LDF + j:                                                     \
     if (j < DMAX) {                                                   \
@@ -229,14 +249,48 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
       GG_PUSH(5)
       GG_PUSH(6)
       GG_PUSH(7)
-      default:  // the packer emits only the opcodes above
-        __builtin_unreachable();
+      default:
+        if constexpr (POW) {
+          switch (opc) {
+            case I_PW + 0:
+              load_rows<R>(xf, t);
+              break;
+            case I_PW + 1:
+              GG_ROWS t[r] = c;
+              break;
+            case I_PW + 2:
+              GG_ROWS t[r] = A[r];
+              load_rows<R>(xf, A);
+              break;
+            case I_PW + 3:
+              GG_ROWS {
+                t[r] = A[r];
+                A[r] = c;
+              }
+              break;
+            GG_SLOT_POW(0)
+            GG_SLOT_POW(1)
+            GG_SLOT_POW(2)
+            GG_SLOT_POW(3)
+            GG_SLOT_POW(4)
+            GG_SLOT_POW(5)
+            GG_SLOT_POW(6)
+            GG_SLOT_POW(7)
+            default:  // the packer emits only the opcodes above
+              __builtin_unreachable();
+          }
+          GG_ROWS A[r] = binop<K_POW>(A[r], t[r]);
+        } else {
+          // the packer emits only the opcodes above (pow only for POW kernels)
+          __builtin_unreachable();
+        }
     }
 #undef GG_ROWS
 #undef GG_UN
 #undef GG_BIN
 #undef GG_SLOT_BIN
 #undef GG_SLOT_KINDS
+#undef GG_SLOT_POW
 #undef GG_PUSH
     if constexpr (TAPE) tape[32 * k] = A[0];
     ins = nxt;

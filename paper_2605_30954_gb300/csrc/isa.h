@@ -17,6 +17,9 @@
 //   LF/LC(kind)        A = kind(X[f] / c, A)     left child a terminal
 //   BS(kind, j)        A = kind(S[j], A)         left subtree evaluated first
 //   RS(kind, j)        A = kind(A, S[j])         right subtree evaluated first
+// pow (Table 2) has the same forms in opcodes of its own, appended after the
+// others (PW + BF/BC/LF/LC group, PWS(j), PWR(j)), so the numbering of the
+// other instructions does not depend on it.
 // A binary node whose children are both subtrees evaluates first the child
 // that needs more slots (Sethi-Ullman order); a tree of height h then needs
 // at most h-1 slots.  Every RPN node of the paper's linearisation appears
@@ -36,11 +39,13 @@ namespace gg {
 enum : int {
   T_ADD = 0, T_SUB = 1, T_MUL = 2, T_AQ = 3, T_SIN = 4, T_COS = 5, T_EXP = 6,
   T_LOG_ABS = 7, T_SQRT_ABS = 8, T_DIV = 9, T_SQUARE = 10, T_LOG = 11, T_SQRT = 12,
-  T_ERC = 31, T_FEAT0 = 32, T_PAD = 255
+  T_POW = 13, T_ERC = 31, T_FEAT0 = 32, T_PAD = 255
 };
 
 // binary kinds and unary kinds used by the interpreter
-enum : int { K_ADD = 0, K_SUB = 1, K_MUL = 2, K_AQ = 3, K_DIV = 4, NKIND = 5 };
+// NKIND counts the kinds of the regular BF..RS opcode groups; K_POW has
+// the appended PW/PWS/PWR opcodes.
+enum : int { K_ADD = 0, K_SUB = 1, K_MUL = 2, K_AQ = 3, K_DIV = 4, NKIND = 5, K_POW = 5 };
 enum : int {
   U_SIN = 0, U_COS = 1, U_EXP = 2, U_LOG_ABS = 3, U_SQRT_ABS = 4, U_SQUARE = 5,
   U_LOG = 6, U_SQRT = 7, NUNARY = 8
@@ -63,8 +68,23 @@ enum : uint32_t {
   I_LDF = 110,                     // + j          (110..117)
   I_LDC = 118,                     // + j          (118..125)
   I_NOP = 126,
-  I_COUNT = 127
+  I_PW = 127,                      // + group BF/BC/LF/LC (127..130)
+  I_PWS = 131,                     // + j (131..138): A = pow(S[j], A)
+  I_PWR = 139,                     // + j (139..146): A = pow(A, S[j])
+  I_COUNT = 147
 };
+
+// Opcode of a binary node with a fused terminal: group 0 BF, 1 BC, 2 LF, 3 LC.
+GG_HD uint32_t fused_opcode(int group, int kind) {
+  return kind == K_POW ? I_PW + (uint32_t)group : I_BF + (uint32_t)(group * NKIND + kind);
+}
+
+// Opcode of a binary node over two subtrees: the left one evaluated first
+// (BS) or the right one (RS), with the first result in slot j.
+GG_HD uint32_t slot_opcode(bool right_first, int kind, int j) {
+  if (kind == K_POW) return (right_first ? I_PWR : I_PWS) + (uint32_t)j;
+  return (right_first ? I_RS : I_BS) + (uint32_t)kind * 8u + (uint32_t)j;
+}
 
 // node classes
 enum : int { C_BAD = 0, C_TERM_F = 1, C_TERM_C = 2, C_UNARY = 3, C_BINARY = 4 };
@@ -76,6 +96,7 @@ GG_HD int classify(int op, int n_features, int* kind) {
     case T_MUL: *kind = K_MUL; return C_BINARY;
     case T_AQ: *kind = K_AQ; return C_BINARY;
     case T_DIV: *kind = K_DIV; return C_BINARY;
+    case T_POW: *kind = K_POW; return C_BINARY;
     case T_SIN: *kind = U_SIN; return C_UNARY;
     case T_COS: *kind = U_COS; return C_UNARY;
     case T_EXP: *kind = U_EXP; return C_UNARY;
@@ -108,7 +129,7 @@ struct PackResult {
   int len;        // instructions emitted (> 0) or 0 on error
   int slots;      // stack slots used
   int status;     // 0 ok, 1 invalid template, 2 needs more slots than allowed
-  int counts[10]; // active nodes by class, see ggeval_batch_stats
+  int counts[11]; // active nodes by class, see ggeval_batch_stats ([10]: pow)
 };
 
 // Children of the node at `pos` (depth `depth`) in a template of height h.
@@ -131,15 +152,17 @@ GG_HD void children(int layout, int h, int pos, int depth, int* l, int* r) {
 // walk.  words/consts have room for cap+1 entries at stride `ws`; entry
 // [len] is set to NOP so the interpreter may prefetch one instruction ahead.
 // `depth1` and `need` are caller scratch of at least 2^(h+1)-1 bytes each
-// (shared memory in the packing kernel).
+// (shared memory in the packing kernel).  With allow_pow false an active
+// pow node makes the template invalid (for interpreters built without pow).
 GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layout,
                            int n_features, int max_slots, uint32_t* words, float* consts,
-                           int ws, Aux* aux, int cap, uint8_t* depth1, uint8_t* need) {
+                           int ws, Aux* aux, int cap, uint8_t* depth1, uint8_t* need,
+                           bool allow_pow = true) {
   PackResult res;
   res.len = 0;
   res.slots = 0;
   res.status = 0;
-  for (int i = 0; i < 10; ++i) res.counts[i] = 0;
+  for (int i = 0; i < 11; ++i) res.counts[i] = 0;
   const int n = (1 << (h + 1)) - 1;
   // depth1[i]: depth + 1 of an active node, 0 for an intron;
   // need[i]: slots the active subtree at i needs
@@ -151,7 +174,8 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
     const int d = depth1[pos] - 1;
     int kind;
     const int cls = classify(op[pos], n_features, &kind);
-    if (cls == C_BAD || ((cls == C_UNARY || cls == C_BINARY) && d >= h)) {
+    if (cls == C_BAD || ((cls == C_UNARY || cls == C_BINARY) && d >= h) ||
+        (cls == C_BINARY && kind == K_POW && !allow_pow)) {
       res.status = 1;
       return res;
     }
@@ -165,7 +189,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
     depth1[l] = (uint8_t)(d + 2);
     if (cls == C_BINARY) {
       depth1[r] = (uint8_t)(d + 2);
-      res.counts[kind == K_AQ ? 3 : kind == K_DIV ? 4 : 2]++;
+      res.counts[kind == K_AQ ? 3 : kind == K_DIV ? 4 : kind == K_POW ? 10 : 2]++;
     } else {
       res.counts[kind == U_SIN || kind == U_COS ? 5
                  : kind == U_EXP                 ? 6
@@ -281,8 +305,8 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
         c.phase = 0; c.order = 0; c.c1 = -1;
       } else {
         const bool feat = ct == C_TERM_F;
-        uint32_t base = rt ? (feat ? I_BF : I_BC) : (feat ? I_LF : I_LC);
-        ret = emit(base + (uint32_t)kind, feat ? kt : 0, feat ? 0.f : cval[term],
+        const int group = rt ? (feat ? 0 : 1) : (feat ? 2 : 3);
+        ret = emit(fused_opcode(group, kind), feat ? kt : 0, feat ? 0.f : cval[term],
                    rt ? ret : -1, rt ? -1 : ret, f.pos, term);
         if (ret < 0) { res.status = 2; return res; }
         --sp;
@@ -304,7 +328,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       c.live = 1; c.phase = 0; c.order = 0; c.c1 = -1;
     } else {
       if (basis >= max_slots) { res.status = 2; return res; }
-      const uint32_t opc = (f.order ? I_RS : I_BS) + (uint32_t)kind * 8u + (uint32_t)basis;
+      const uint32_t opc = slot_opcode(f.order != 0, kind, basis);
       const int sl = f.order ? ret : f.c1;
       const int sr = f.order ? f.c1 : ret;
       ret = emit(opc, 0, 0.f, sl, sr, f.pos, -1);

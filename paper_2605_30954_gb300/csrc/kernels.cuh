@@ -19,6 +19,7 @@ struct PackParams {
   int* len;              // [n] instruction count, -1 for an invalid trial, 0 masked out
   unsigned* status;
   const uint8_t* mask;   // nullable: evaluate only trials with a nonzero byte
+  int allow_pow;         // 0: an active pow node makes the trial invalid
 };
 
 // pack_kernel (defined in misc.cu): one thread per trial.
@@ -166,7 +167,7 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int s, float* x
 // ever waits for the others except for the tile it is about to use.
 // MINB is the launch-bounds occupancy target: 1 lets the compiler use up to
 // 128 registers per thread, 2 caps it at 64 (two 512-thread CTAs per SM).
-template <int DMAX, int R, bool EXACT, bool ROWS, int MINB>
+template <int DMAX, int R, bool EXACT, bool ROWS, int MINB, bool POW>
 __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
-        run_program<DMAX, R, false, true>(wprog, L, xs + r0, p.tile_rows, A, S);
+        run_program<DMAX, R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, S);
         const int valid = nrows - r0;  // rows of this lane inside the tile
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
@@ -322,14 +323,33 @@ constexpr double VAR_TOL = 1e-12;
 
 // fin_kernel is defined in misc.cu.
 
-// kernel pointers, one table per translation unit (fwd_d3.cu, fwd_d5.cu,
-// fwd_d7.cu): variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
+// Kernel pointers: variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
 // pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
-// variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers
+// variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers.
+// One table per translation unit (fwd_d3.cu ... fwd_d7_pow.cu) so that the
+// instantiations compile in parallel; the _pow tables hold the kernels that
+// also run pow instructions (kept apart because the pow code costs the other
+// kernels registers and instruction-cache locality).
 constexpr int NVARIANT = 7;
+template <int D, bool P>
+const void* fwd_table(int variant) {
+  switch (variant) {
+    case 0: return reinterpret_cast<const void*>(&fwd_kernel<D, 8, false, false, 1, P>);
+    case 1: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, false, false, 1, P>);
+    case 2: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, false, 1, P>);
+    case 3: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, true, 1, P>);
+    case 4: return reinterpret_cast<const void*>(&fwd_kernel<D, 8, false, false, 2, P>);
+    case 5: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, false, false, 2, P>);
+    case 6: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, false, 2, P>);
+    default: return nullptr;
+  }
+}
 const void* fwd_ptr_d3(int variant);
 const void* fwd_ptr_d5(int variant);
 const void* fwd_ptr_d7(int variant);
+const void* fwd_ptr_d3_pow(int variant);
+const void* fwd_ptr_d5_pow(int variant);
+const void* fwd_ptr_d7_pow(int variant);
 inline int variant_rows(int v) { return (v == 0 || v == 4) ? 8 : 4; }
 inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
 

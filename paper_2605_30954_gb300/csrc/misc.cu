@@ -24,7 +24,7 @@ __global__ void pack_kernel(const PackParams p) {
                                    reinterpret_cast<uint32_t*>(prog),
                                    reinterpret_cast<float*>(prog) + 1, 2,
                                    p.aux ? p.aux + (size_t)t * p.lstride : nullptr,
-                                   p.lstride - 1, depth1, need);
+                                   p.lstride - 1, depth1, need, p.allow_pow != 0);
     if (r.status == 0) L = r.len;
   }
   p.len[t] = L;

@@ -57,7 +57,7 @@ inline size_t adj_smem_bytes(int warps, int lstride) {
 
 const void* pack_ptr();
 const void* fin_ptr();
-const void* adj_ptr(int dmax);
+const void* adj_ptr(int dmax, bool pow);
 const void* gradout_ptr();
 const void* adam_ptr();
 const void* transpose_ptr();

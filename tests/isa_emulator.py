@@ -8,7 +8,8 @@ import numpy as np
 
 I_LDF0, I_LDC0, I_UN, I_BF, I_BC, I_LF, I_LC, I_BS, I_RS, I_LDF, I_LDC, I_NOP = \
     0, 1, 2, 10, 15, 20, 25, 30, 70, 110, 118, 126
-KINDS = ["+", "-", "*", "aq", "/"]
+I_PW, I_PWS, I_PWR, I_END = 127, 131, 139, 147  # pow: fused groups, then slot forms
+KINDS = ["+", "-", "*", "aq", "/", "pow"]
 UNARY = ["sin", "cos", "exp", "logabs", "sqrtabs", "sq", "log", "sqrt"]
 
 
@@ -22,6 +23,8 @@ def binop(k, a, b):
             return a * b
         if k == 3:
             return a / np.sqrt(1.0 + b * b)
+        if k == 5:
+            return np.power(a, b)
         return a / b
 
 
@@ -53,6 +56,12 @@ def decode(word):
         return ("ldf", opc - I_LDF, feat)
     if I_LDC <= opc < I_NOP:
         return ("ldc", opc - I_LDC, None)
+    if I_PW <= opc < I_PWS:
+        return (["bf", "bc", "lf", "lc"][opc - I_PW], 5, feat)
+    if I_PWS <= opc < I_PWR:
+        return ("bs", (5, opc - I_PWS), None)
+    if I_PWR <= opc < I_END:
+        return ("rs", (5, opc - I_PWR), None)
     raise ValueError(opc)
 
 

@@ -62,19 +62,30 @@ class Tally:
                 f"worst={self.worst:.3g} {self.msgs[:5]}")
 
 
+def value_class(v):
+    """0 finite, 1 NaN, 2 +inf, 3 -inf."""
+    v = np.asarray(v, dtype=np.float64)
+    return np.where(np.isnan(v), 1, np.where(v == np.inf, 2, np.where(v == -np.inf, 3, 0)))
+
+
 def check_rows(g, f64, f32, tally, tag="", cond=None):
     """Per-row values of one trial.  ``cond``: per-row error bound
-    (oracle.condition_bound) used with f32 to flag ill-conditioned rows."""
+    (oracle.condition_bound) used with f32 to flag ill-conditioned rows.
+    A row that is non-finite in the oracle's FP64 and FP32 passes alike
+    (both NaN, or the same infinity) must be that on the GPU too; a row on
+    which the two passes disagree is excluded."""
     with np.errstate(all="ignore"):
         fin = np.isfinite(f64)
         rms = math.sqrt(np.mean(f64[fin] ** 2)) if fin.any() else 0.0
         tol = ROW_TOL * (np.abs(f64) + rms)
         err32 = np.abs(f32.astype(np.float64) - f64)
-        ill = ~fin | ~np.isfinite(f32) | (err32 > COND_MARGIN * tol)
+        c64, c32, cg = value_class(f64), value_class(f32), value_class(g)
+        special = (c64 != 0) & (c64 == c32)
+        ill = ~special & (~fin | (c32 != 0) | (err32 > COND_MARGIN * tol))
         if cond is not None:
-            ill |= ~(cond <= COND_MARGIN * tol)
-        err = np.abs(g.astype(np.float64) - f64)
-        bad = ~ill & ~(err <= tol)
+            ill |= fin & ~(cond <= COND_MARGIN * tol)
+        err = np.where(special, 0.0, np.abs(g.astype(np.float64) - f64))
+        bad = ~ill & np.where(special, cg != c64, ~(err <= tol))
     tally.checked += int((~ill).sum())
     tally.excluded += int(ill.sum())
     if bad.any():

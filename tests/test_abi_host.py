@@ -49,7 +49,8 @@ def test_header_opcodes_match_interface():
     vals = dict((k, int(v)) for k, v in re.findall(r"GGEVAL_OP_([A-Z0-9_]+)\s*=\s*(\d+)", text))
     names = {"ADD": "ADD", "SUB": "SUB", "MUL": "MUL", "AQ": "AQ", "SIN": "SIN", "COS": "COS",
              "EXP": "EXP", "LOG_ABS": "LOG_ABS", "SQRT_ABS": "SQRT_ABS", "DIV": "DIV",
-             "SQUARE": "SQUARE", "LOG": "LOG", "SQRT": "SQRT", "ERC": "ERC", "FEATURE0": "FEAT0",
+             "SQUARE": "SQUARE", "LOG": "LOG", "SQRT": "SQRT", "POW": "POW", "ERC": "ERC",
+             "FEATURE0": "FEAT0",
              "PAD": "PAD"}
     for h, o in names.items():
         assert vals[h] == getattr(O, o) == getattr(synth, o), h
@@ -84,7 +85,7 @@ def test_packed_programs_compute_the_oracle_value(gg, h, layout):
     rng = np.random.default_rng(100 + h)
     nf = 5
     X = rng.uniform(-2, 2, (40, nf))
-    funcs = synth.FULL_SET + (synth.DIV, synth.SQUARE)
+    funcs = synth.FULL_SET + (synth.DIV, synth.SQUARE, synth.POW)
     for p_func in (0.5, 1.0):
         op, cv, hs = synth.random_templates(rng, 12, h, h, funcs, nf, p_func)
         if layout == "prefix":
@@ -101,7 +102,8 @@ def test_packed_programs_compute_the_oracle_value(gg, h, layout):
 
 def test_stats_count_active_nodes(gg):
     rng = np.random.default_rng(3)
-    op, cv, hs = synth.random_templates(rng, 50, rng.integers(0, 6, 50), 5, synth.FULL_SET, 4, 0.7)
+    op, cv, hs = synth.random_templates(rng, 50, rng.integers(0, 6, 50), 5,
+                                        synth.FULL_SET + (synth.POW,), 4, 0.7)
     st = gg.batch_stats(torch.from_numpy(op), torch.from_numpy(cv),
                         torch.from_numpy(hs), n_features=4).numpy()
     for p in range(50):
@@ -109,7 +111,8 @@ def test_stats_count_active_nodes(gg):
         mask = O.active_mask(t)
         assert st[p, 0] == mask.sum()
         assert st[p, 1] == np.sum(mask & (op[p] >= synth.ERC))
-        assert st[p, 0] == st[p, 1:10].sum()
+        assert st[p, 0] == st[p, 1:10].sum() + st[p, 12]
+        assert st[p, 12] == np.sum(mask & (op[p] == synth.POW))
 
 
 @pytest.mark.parametrize("tokens,h", [

@@ -36,6 +36,8 @@ def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0):
     ds = gg.Dataset(X, y)
     op, cv = dev(w["op"]), dev(w["cval"])
     hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
+    if w.get("uses_pow"):
+        flags |= gg.F_POW
     smse, a, b, mse = ds.eval_batch(op, cv, hs, layout=layout, flags=flags)
     idx = range(w["P"]) if sample is None else sample
     rows = None
@@ -80,7 +82,7 @@ def test_fig1_on_gpu(gg):
 
 @pytest.mark.parametrize("cfg,n_rows,n_trials", [
     ("c1", 1000, 256), ("c1", 3001, 97), ("c2", 5003, 64), ("c3", 4099, 48),
-    ("c4", 2500, 40), ("c5", 3000, 32),
+    ("c4", 2500, 40), ("c5", 3000, 32), ("t2", 5003, 64),
 ])
 def test_small_configs_rows_and_fitness(gg, cfg, n_rows, n_trials):
     w = PA.build(cfg, n_rows, n_trials)
@@ -243,6 +245,31 @@ def test_invalid_trial_reports_and_isolates(gg):
     ds.close()
 
 
+def test_pow_needs_its_flag(gg):
+    """An active pow node is an invalid template unless GGEVAL_F_POW selects
+    the kernels that implement pow; with the flag it evaluates to the
+    oracle's value, the plain and masked forms included."""
+    w = PA.build("c1", 2000, 8)
+    op, cv = w["op"].copy(), w["cval"].copy()
+    rows = {0: "pow", 1: "x0", 2: "+", 5: "x1", 6: "0.75"}  # x0 ^ (x1 + 0.75)
+    op[2], cv[2] = heap_template(rows, 3)
+    X = np.abs(w["X"]) + 0.25
+    ds = gg.Dataset(torch.from_numpy(X), torch.from_numpy(w["y"]))
+    smse = ds.eval_batch(dev(op), dev(cv))[0]
+    with pytest.raises(gg.GGEvalError) as e:
+        ds.sync()
+    assert e.value.status == -2
+    s0 = smse.cpu().numpy()
+    assert math.isnan(s0[2]) and np.all(np.isfinite(s0[np.arange(8) != 2]))
+    for call in (ds.eval_batch, ds.eval_plain):
+        s1 = call(dev(op), dev(cv), flags=gg.F_POW)[0].cpu().numpy()
+        ds.sync()
+        np.testing.assert_allclose(s1[np.arange(8) != 2], s0[np.arange(8) != 2], rtol=1e-5)
+        fit = O.fitness(O.eval_tree(O.Template(op[2], cv[2], 3, n_features=5), X), w["y"])
+        assert abs(s1[2] - fit["smse"]) <= 1e-4 * fit["smse"] + 1e-8 * np.var(w["y"])
+    ds.close()
+
+
 def test_bad_arguments_rejected(gg):
     X = torch.zeros((10, 2))
     y = torch.arange(10, dtype=torch.float32)
@@ -271,7 +298,7 @@ def test_max_height_and_feature_counts(gg, h, nf):
 
 
 # -------------------------------------------------------- full-size configs --
-FULL = [("c1", None), ("c2", 24), ("c3", 24), ("c4", 24), ("c5", 12)]
+FULL = [("c1", None), ("c2", 24), ("c3", 24), ("c4", 24), ("c5", 12), ("t2", 24)]
 
 
 @pytest.mark.parametrize("cfg,n_sample", FULL)
