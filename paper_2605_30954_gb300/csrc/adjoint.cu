@@ -63,20 +63,17 @@ __device__ __forceinline__ float dun(int u, float x) {
   }
 }
 
-template <int DMAX, bool POW>
+template <bool POW>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned char* base = smem + (size_t)warp * p.lstride * ADJ_WARP_BYTES_PER_INSTR;
+  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots);
   uint2* wprog = reinterpret_cast<uint2*>(base);
   Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
   float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per instruction
   float* V = reinterpret_cast<float*>(wg + p.lstride);      // [lstride][32]
-
-  float S[DMAX][1];
-#pragma unroll
-  for (int j = 0; j < DMAX; ++j) S[j][0] = 0.f;
+  float* stk = V + (size_t)p.lstride * 32 + lane;            // [slots][32], this lane
 
   for (;;) {
     int item = 0;
@@ -109,7 +106,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       const bool valid = row < r_end;
       const int rr = valid ? row : r_end - 1;
       float A[1] = {0.f};
-      run_program<DMAX, 1, true, false, POW>(wprog, L, p.X + rr, p.ldx, A, S, V + lane);
+      run_program<1, true, false, POW>(wprog, L, p.X + rr, p.ldx, A, stk, V + lane);
       const float f = A[0];
       const float yc = p.X[(size_t)p.F * p.ldx + rr];
       float w = p.mse_mode ? two_n * (f - ybar - yc) : two_n * bb * (a_c + bb * f - yc);
@@ -124,9 +121,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
         const float g = V[32 * k + lane];  // adjoint of instruction k
         float ge = 0.f;                    // contribution to this instruction's ERC
         bool has_erc = false;
-        if (opc == I_LDF0 || (opc >= I_LDF && opc < I_LDF + 8)) {
-          // feature push: nothing to propagate
-        } else if (opc == I_LDC0 || (opc >= I_LDC && opc < I_LDC + 8)) {
+        if (opc == I_LDF0 || opc == I_PSF) {
+          // feature load: nothing to propagate
+        } else if (opc == I_LDC0 || opc == I_PSC) {
           ge = g;
           has_erc = true;
         } else if (opc >= I_UN && opc < I_UN + NUNARY) {
@@ -156,9 +153,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
               has_erc = true;
             }
           }
-        } else if ((opc >= I_BS && opc < I_LDF) || (POW && opc >= I_PWS && opc < I_COUNT)) {
-          const int kind =
-              POW && opc >= I_PWS ? K_POW : (int)((opc - (opc < I_RS ? I_BS : I_RS)) / 8u);
+        } else if ((opc >= I_BS && opc < I_NOP) || (POW && opc >= I_PWS && opc < I_COUNT)) {
+          const int kind = POW && opc >= I_PWS ? K_POW : (int)(opc - (opc < I_RS ? I_BS : I_RS));
           float* va = &V[32 * ax.src_l + lane];
           float* vb = &V[32 * ax.src_r + lane];
           float da, db;
@@ -183,7 +179,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
     for (int k = lane; k < L; k += 32) {
       const uint32_t opc = wprog[k].x & 0xffu;
       int tp = -1;
-      if (opc == I_LDC0 || (opc >= I_LDC && opc < I_LDC + 8)) tp = waux[k].tpos;
+      if (opc == I_LDC0 || opc == I_PSC) tp = waux[k].tpos;
       else if ((opc >= I_BC && opc < I_BC + NKIND) || (opc >= I_LC && opc < I_LC + NKIND) ||
                (POW && (opc == I_PW + 1 || opc == I_PW + 3)))
         tp = waux[k].tpos_fused;
@@ -195,16 +191,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   }
 }
 
-const void* adj_ptr(int dmax, bool pow) {
-  switch (dmax) {
-    case 3: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<3, true>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<3, false>);
-    case 5: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<5, true>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<5, false>);
-    case 7: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<7, true>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<7, false>);
-    default: return nullptr;
-  }
+const void* adj_ptr(bool pow) {
+  return pow ? reinterpret_cast<const void*>(&adjoint_kernel<true>)
+             : reinterpret_cast<const void*>(&adjoint_kernel<false>);
 }
 
 }  // namespace gg

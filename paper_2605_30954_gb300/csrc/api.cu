@@ -66,15 +66,13 @@ inline int pack_threads(int stride) {
   int t = (49152 / (2 * stride)) & ~31;
   return t < 32 ? 32 : (t > 128 ? 128 : t);
 }
-inline int dmax_of(int h) { return h <= 4 ? 3 : (h <= 6 ? 5 : 7); }
+// stack slots of a template of height h: Sethi-Ullman order with fused
+// terminals needs at most h - 1 (the packer checks the bound)
+inline int slots_of(int h) { return h > 2 ? h - 1 : 1; }
 inline int lstride_of(int h) { return stride_of(h) + 1; }
 
-const void* fwd_ptr(int dmax, int variant, bool pow) {
-  switch (dmax) {
-    case 3: return pow ? gg::fwd_ptr_d3_pow(variant) : gg::fwd_ptr_d3(variant);
-    case 5: return pow ? gg::fwd_ptr_d5_pow(variant) : gg::fwd_ptr_d5(variant);
-    default: return pow ? gg::fwd_ptr_d7_pow(variant) : gg::fwd_ptr_d7(variant);
-  }
+const void* fwd_ptr(int variant, bool pow) {
+  return pow ? gg::fwd_ptr_pow(variant) : gg::fwd_ptr_plain(variant);
 }
 
 // GGEVAL_F_POW selects the kernels that run pow instructions.
@@ -104,7 +102,7 @@ struct Cfg {
 struct Plan {
   Cfg cfg;
   bool pow = false;  // kernels with the pow instructions; the packer accepts pow
-  int dmax = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
+  int slots = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
   size_t smem = 0;
   const void* fn = nullptr;
 };
@@ -209,7 +207,8 @@ Cfg default_cfg(const ggeval_dataset* ds, int n, int h_max, uint32_t flags) {
   const int lst = lstride_of(h_max);
   int max_tile = exact ? 2048 : 2048;
   while (max_tile > rpp &&
-         gg::fwd_smem_bytes(ds->F, max_tile, c.warps, lst) > ds->smem_optin / 2)
+         gg::fwd_smem_bytes(ds->F, max_tile, c.warps, lst, slots_of(h_max),
+                            gg::variant_rows(c.variant)) > ds->smem_optin / 2)
     max_tile /= 2;
   const double target = 16.0 * ds->sms * 2;
   double want = (double)ds->N * n / ((double)c.warps * target);
@@ -230,16 +229,17 @@ ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Pl
                         bool pow) {
   pl->cfg = cfg;
   pl->pow = pow;
-  pl->dmax = dmax_of(h_max);
+  pl->slots = slots_of(h_max);
   pl->stride = stride_of(h_max);
   pl->lstride = lstride_of(h_max);
-  pl->fn = fwd_ptr(pl->dmax, cfg.variant, pow);
+  pl->fn = fwd_ptr(cfg.variant, pow);
   if (!pl->fn) return fail(GGEVAL_ERR_ARG, "no kernel for variant %d", cfg.variant);
   const int rpp = 32 * gg::variant_rows(cfg.variant);
   if (cfg.tile_rows < rpp || cfg.tile_rows % rpp || cfg.group < 1 || cfg.warps < 1 ||
       cfg.warps > 16)
     return fail(GGEVAL_ERR_ARG, "bad tile configuration");
-  pl->smem = gg::fwd_smem_bytes(ds->F, cfg.tile_rows, cfg.warps, pl->lstride);
+  pl->smem = gg::fwd_smem_bytes(ds->F, cfg.tile_rows, cfg.warps, pl->lstride, pl->slots,
+                                gg::variant_rows(cfg.variant));
   if (pl->smem > ds->smem_optin) return fail(GGEVAL_ERR_ARG, "tile needs too much shared memory");
   pl->n_tiles = (int)((ds->N + cfg.tile_rows - 1) / cfg.tile_rows);
   const long long n_groups = (n + cfg.group - 1) / cfg.group;
@@ -326,7 +326,7 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.stride = pl.stride;
   pp.layout = layout;
   pp.n_features = ds->F;
-  pp.max_slots = pl.dmax;
+  pp.max_slots = pl.slots;
   pp.lstride = pl.lstride;
   pp.prog = ds->prog;
   pp.aux = with_aux ? ds->aux : nullptr;
@@ -353,6 +353,7 @@ gg::FwdParams fwd_params(ggeval_dataset* ds, int n, const Plan& pl) {
   fp.n_tiles = pl.n_tiles;
   fp.group = pl.cfg.group;
   fp.n_items = pl.n_items;
+  fp.slots = pl.slots;
   fp.part = ds->part;
   fp.counter = ds->counters;
   fp.status = ds->status;
@@ -709,23 +710,24 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   float* ds_smse = smse ? (host ? dg + gcount : smse) : nullptr;
   GG_TRY(enqueue_eval(ds, db, b, pl, ds_smse, nullptr, nullptr, nullptr, true, st));
   // adjoint
-  const void* afn = gg::adj_ptr(pl.dmax, pl.pow);
+  const void* afn = gg::adj_ptr(pl.pow);
   GG_TRY(prepare_kernel(ds->device, afn));
   // Each warp holds its own copy of the program and 32 rows of values, so
   // shared memory bounds the resident warps: take the CTA size (1..8 warps)
   // that keeps the most warps resident per SM, the larger CTA on a tie.
   int warps = 0, nb = 0;
-  const int wmax = (int)((ds->smem_optin - 64) / ((size_t)pl.lstride * gg::ADJ_WARP_BYTES_PER_INSTR));
+  const int wmax = (int)((ds->smem_optin - 64) / gg::adj_warp_bytes(pl.lstride, pl.slots));
   for (int w = wmax < 8 ? wmax : 8; w >= 1; --w) {
     int n = 0;
-    GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, afn, w * 32, gg::adj_smem_bytes(w, pl.lstride)));
+    GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, afn, w * 32,
+                                                        gg::adj_smem_bytes(w, pl.lstride, pl.slots)));
     if (n * w > nb * warps) {
       warps = w;
       nb = n;
     }
   }
   if (warps < 1 || nb < 1) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
-  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride);
+  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride, pl.slots);
   const long long slots = (long long)nb * ds->sms * warps;
   long long n_chunks = (8 * slots + b->n - 1) / b->n;
   const long long max_chunks = (ds->N + 31) / 32;
@@ -744,6 +746,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   ap.lstride = pl.lstride;
   ap.P = b->n;
   ap.stride = pl.stride;
+  ap.slots = pl.slots;
   ap.ab = ds->ab;
   ap.mse_mode = (flags & GGEVAL_F_GRAD_MSE) ? 1 : 0;
   ap.ybar = ds->ybar;
@@ -1127,7 +1130,7 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   pp.stride = pl.stride;
   pp.layout = b->layout;
   pp.n_features = ds->F;
-  pp.max_slots = pl.dmax;
+  pp.max_slots = pl.slots;
   pp.lstride = pl.lstride;
   pp.prog = prog;
   pp.aux = nullptr;

@@ -116,27 +116,42 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v
   }
 }
 
+// Store R consecutive rows of a lane (the counterpart of load_rows).
+template <int R>
+__device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&v)[R]) {
+  static_assert(R == 1 || R % 4 == 0, "R must be 1 or a multiple of 4");
+  if constexpr (R == 1) {
+    *p = v[0];
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < R / 4; ++q)
+    reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
 // Run one packed program on R rows per lane.  `prog` is the warp's copy of
 // the program in shared memory (word, const bits) with a NOP at [L];
 // `xs` points at row r0 of feature 0 of the tile, features `ts` floats
 // apart.  Every lane of the warp executes the same instruction sequence, so
 // the switch below is warp-uniform (Section 3.2: all threads interpret the
-// same individual, avoiding divergence).  The slot operand of each
-// instruction is part of its opcode, so S[] is indexed with constants and
-// stays in registers.
-// A and S are the caller's registers (initialised once, kept across calls);
-// the first instruction of every program is a push into A.  With PRESCALED
-// the feature field of each word already holds the feature's offset in
-// floats (feature x ts), as the batched kernel rewrites it when it stages a
-// program.  With TAPE (R == 1 only) the value of A after instruction k is
-// stored at tape[32 k] (the caller offsets `tape` by its lane): the forward
-// half of the adjoint.  POW adds the pow instructions; without it the
-// program must not contain them.
-template <int DMAX, int R, bool TAPE = false, bool PRESCALED = false, bool POW = false>
+// same individual, avoiding divergence).  The top of the stack is A (the
+// caller's registers); the values below it live in the warp's stack in
+// shared memory: `stk` is this lane's entry in slot 0 (slot j at
+// stk + 32 R j), so a push or a pop is one R-float shared-memory access per
+// lane.  The first instruction of every program loads A without a push.
+// With PRESCALED the feature field of each word already holds the
+// feature's offset in floats (feature x ts), as the batched kernel rewrites
+// it when it stages a program.  With TAPE (R == 1 only) the value of A
+// after instruction k is stored at tape[32 k] (the caller offsets `tape` by
+// its lane): the forward half of the adjoint.  POW adds the pow
+// instructions; without it the program must not contain them.
+template <int R, bool TAPE = false, bool PRESCALED = false, bool POW = false>
 __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
                                             const float* __restrict__ xs, int ts,
-                                            float (&A)[R], float (&S)[DMAX][R],
+                                            float (&A)[R], float* __restrict__ stk,
                                             float* __restrict__ tape = nullptr) {
+  constexpr int SLOT = 32 * R;  // floats per stack slot
+  float* sp = stk;              // next free slot of this lane
   uint2 ins = prog[0];
   for (int k = 0; k < L; ++k) {
     const uint2 nxt = prog[k + 1];
@@ -164,53 +179,16 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;                                                            \
   case I_LC + kd:                                                     \
     GG_ROWS A[r] = binop<kd>(c, A[r]);                                \
-    break;
-#define GG_SLOT_BIN(kd, j)                                            \
-  case I_BS + kd * 8 + j:                                             \
-    if (j < DMAX) {                                                   \
-      GG_ROWS A[r] = binop<kd>(S[j < DMAX ? j : 0][r], A[r]);         \
-    }                                                                 \
     break;                                                            \
-  case I_RS + kd * 8 + j:                                             \
-    if (j < DMAX) {                                                   \
-      GG_ROWS A[r] = binop<kd>(A[r], S[j < DMAX ? j : 0][r]);         \
-    }                                                                 \
-    break;
-#define GG_SLOT_KINDS(j) \
-  GG_SLOT_BIN(K_ADD, j)  \
-  GG_SLOT_BIN(K_SUB, j)  \
-  GG_SLOT_BIN(K_MUL, j)  \
-  GG_SLOT_BIN(K_AQ, j)   \
-  GG_SLOT_BIN(K_DIV, j)
-// pow (POW kernels only): every form moves its operands into (A = base,
-// t = exponent) and one shared body follows, so the library pow is
-// expanded once.
-#define GG_SLOT_POW(j)                                                \
-  case I_PWS + j:                                                     \
-    if (j < DMAX) {                                                   \
-      GG_ROWS {                                                       \
-        t[r] = A[r];                                                  \
-        A[r] = S[j < DMAX ? j : 0][r];                                \
-      }                                                               \
-    }                                                                 \
+  case I_BS + kd:                                                     \
+    sp -= SLOT;                                                       \
+    load_rows<R>(sp, t);                                              \
+    GG_ROWS A[r] = binop<kd>(t[r], A[r]);                             \
     break;                                                            \
-  case I_PWR + j:                                                     \
-    if (j < DMAX) {                                                   \
-      GG_ROWS t[r] = S[j < DMAX ? j : 0][r];                          \
-    }                                                                 \
-    break;
-#define GG_PUSH(j)                                                    \
-  case I_LDF + j:                                                     \
-    if (j < DMAX) {                                                   \
-      GG_ROWS S[j < DMAX ? j : 0][r] = A[r];                          \
-    }                                                                 \
-    load_rows<R>(xf, A);                                              \
-    break;                                                            \
-  case I_LDC + j:                                                     \
-    if (j < DMAX) {                                                   \
-      GG_ROWS S[j < DMAX ? j : 0][r] = A[r];                          \
-    }                                                                 \
-    GG_ROWS A[r] = c;                                                 \
+  case I_RS + kd:                                                     \
+    sp -= SLOT;                                                       \
+    load_rows<R>(sp, t);                                              \
+    GG_ROWS A[r] = binop<kd>(A[r], t[r]);                             \
     break;
 
     switch (opc) {
@@ -218,6 +196,16 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
         load_rows<R>(xf, A);
         break;
       case I_LDC0:
+        GG_ROWS A[r] = c;
+        break;
+      case I_PSF:
+        store_rows<R>(sp, A);
+        sp += SLOT;
+        load_rows<R>(xf, A);
+        break;
+      case I_PSC:
+        store_rows<R>(sp, A);
+        sp += SLOT;
         GG_ROWS A[r] = c;
         break;
       GG_UN(U_SIN)
@@ -233,24 +221,10 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
       GG_BIN(K_MUL)
       GG_BIN(K_AQ)
       GG_BIN(K_DIV)
-      GG_SLOT_KINDS(0)
-      GG_SLOT_KINDS(1)
-      GG_SLOT_KINDS(2)
-      GG_SLOT_KINDS(3)
-      GG_SLOT_KINDS(4)
-      GG_SLOT_KINDS(5)
-      GG_SLOT_KINDS(6)
-      GG_SLOT_KINDS(7)
-      GG_PUSH(0)
-      GG_PUSH(1)
-      GG_PUSH(2)
-      GG_PUSH(3)
-      GG_PUSH(4)
-      GG_PUSH(5)
-      GG_PUSH(6)
-      GG_PUSH(7)
       default:
         if constexpr (POW) {
+          // every pow form moves its operands into (A = base, t = exponent)
+          // and one shared body follows, so the library pow is expanded once
           switch (opc) {
             case I_PW + 0:
               load_rows<R>(xf, t);
@@ -268,14 +242,15 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
                 A[r] = c;
               }
               break;
-            GG_SLOT_POW(0)
-            GG_SLOT_POW(1)
-            GG_SLOT_POW(2)
-            GG_SLOT_POW(3)
-            GG_SLOT_POW(4)
-            GG_SLOT_POW(5)
-            GG_SLOT_POW(6)
-            GG_SLOT_POW(7)
+            case I_PWS:
+              sp -= SLOT;
+              GG_ROWS t[r] = A[r];
+              load_rows<R>(sp, A);
+              break;
+            case I_PWR:
+              sp -= SLOT;
+              load_rows<R>(sp, t);
+              break;
             default:  // the packer emits only the opcodes above
               __builtin_unreachable();
           }
@@ -288,10 +263,6 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
 #undef GG_ROWS
 #undef GG_UN
 #undef GG_BIN
-#undef GG_SLOT_BIN
-#undef GG_SLOT_KINDS
-#undef GG_SLOT_POW
-#undef GG_PUSH
     if constexpr (TAPE) tape[32 * k] = A[0];
     ins = nxt;
   }

@@ -3,27 +3,24 @@
 // The packer turns one template tree into the program the interpreter runs.
 // Section 3.2 of the paper linearises a tree by post-order traversal (RPN)
 // with introns skipped and evaluates it with a stack in one forward pass.
-// Here the stack is a register file: the top of stack lives in an
-// accumulator A (R rows per lane), values below it in slots S[0..DMAX).
-// Because the stack depth at every RPN position is fixed by the tree, the
-// slot each instruction touches is known when packing and is encoded in the
-// opcode, so the kernel indexes registers with compile-time constants.
+// Here the top of the stack lives in an accumulator A (R rows per lane, in
+// registers) and the values below it in a per-warp stack in shared memory
+// (one slot = R rows of each of the 32 lanes).
 //
 // Instruction forms (kind = binary op, u = unary op):
-//   LDF0 / LDC0        A = X[f] / A = c                       (stack empty)
-//   LDF(j) / LDC(j)    S[j] = A; A = X[f] / c                 (push)
+//   LDF0 / LDC0        A = X[f] / A = c                  (A holds nothing)
+//   PSF / PSC          push A; A = X[f] / c
 //   UN(u)              A = u(A)
 //   BF/BC(kind)        A = kind(A, X[f] / c)     right child a terminal
 //   LF/LC(kind)        A = kind(X[f] / c, A)     left child a terminal
-//   BS(kind, j)        A = kind(S[j], A)         left subtree evaluated first
-//   RS(kind, j)        A = kind(A, S[j])         right subtree evaluated first
-// pow (Table 2) has the same forms in opcodes of its own, appended after the
-// others (PW + BF/BC/LF/LC group, PWS(j), PWR(j)), so the numbering of the
-// other instructions does not depend on it.
+//   BS(kind)           A = kind(pop, A)          left subtree evaluated first
+//   RS(kind)           A = kind(A, pop)          right subtree evaluated first
 // A binary node whose children are both subtrees evaluates first the child
-// that needs more slots (Sethi-Ullman order); a tree of height h then needs
+// that needs more stack (Sethi-Ullman order); a tree of height h then needs
 // at most h-1 slots.  Every RPN node of the paper's linearisation appears
-// exactly once: terminals either as a push or fused into their parent.
+// exactly once: terminals either as a load or fused into their parent.
+// pow (Table 2) has the same forms in opcodes of its own (PW + BF/BC/LF/LC
+// group, PWS, PWR), run only by the kernels built with pow.
 #pragma once
 #include <stdint.h>
 
@@ -51,27 +48,27 @@ enum : int {
   U_LOG = 6, U_SQRT = 7, NUNARY = 8
 };
 
-constexpr int MAX_SLOTS = 8;      // slot index fits 3 bits
+constexpr int MAX_SLOTS = 8;      // stack slots of the deepest template
 constexpr int MAX_HEIGHT = 8;     // 511 template nodes
 constexpr int MAX_NODES = 511;
 
 enum : uint32_t {
   I_LDF0 = 0,
   I_LDC0 = 1,
-  I_UN = 2,                        // + u          (2..9)
-  I_BF = 10,                       // + kind       (10..14)
-  I_BC = 15,                       // + kind       (15..19)
-  I_LF = 20,                       // + kind       (20..24)
-  I_LC = 25,                       // + kind       (25..29)
-  I_BS = 30,                       // + kind*8 + j (30..69)
-  I_RS = 70,                       // + kind*8 + j (70..109)
-  I_LDF = 110,                     // + j          (110..117)
-  I_LDC = 118,                     // + j          (118..125)
-  I_NOP = 126,
-  I_PW = 127,                      // + group BF/BC/LF/LC (127..130)
-  I_PWS = 131,                     // + j (131..138): A = pow(S[j], A)
-  I_PWR = 139,                     // + j (139..146): A = pow(A, S[j])
-  I_COUNT = 147
+  I_PSF = 2,
+  I_PSC = 3,
+  I_UN = 4,                        // + u          (4..11)
+  I_BF = 12,                       // + kind       (12..16)
+  I_BC = 17,                       // + kind       (17..21)
+  I_LF = 22,                       // + kind       (22..26)
+  I_LC = 27,                       // + kind       (27..31)
+  I_BS = 32,                       // + kind       (32..36)
+  I_RS = 37,                       // + kind       (37..41)
+  I_NOP = 42,
+  I_PW = 43,                       // + group BF/BC/LF/LC (43..46)
+  I_PWS = 47,                      // A = pow(pop, A)
+  I_PWR = 48,                      // A = pow(A, pop)
+  I_COUNT = 49
 };
 
 // Opcode of a binary node with a fused terminal: group 0 BF, 1 BC, 2 LF, 3 LC.
@@ -80,10 +77,10 @@ GG_HD uint32_t fused_opcode(int group, int kind) {
 }
 
 // Opcode of a binary node over two subtrees: the left one evaluated first
-// (BS) or the right one (RS), with the first result in slot j.
-GG_HD uint32_t slot_opcode(bool right_first, int kind, int j) {
-  if (kind == K_POW) return (right_first ? I_PWR : I_PWS) + (uint32_t)j;
-  return (right_first ? I_RS : I_BS) + (uint32_t)kind * 8u + (uint32_t)j;
+// (BS, the left value is popped) or the right one (RS).
+GG_HD uint32_t stack_opcode(bool right_first, int kind) {
+  if (kind == K_POW) return right_first ? I_PWR : I_PWS;
+  return (right_first ? I_RS : I_BS) + (uint32_t)kind;
 }
 
 // node classes
@@ -262,7 +259,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       if (f.live) {
         if (f.occ >= max_slots) { res.status = 2; return res; }
         if (f.occ > max_slot) max_slot = f.occ;
-        opc = (feat ? I_LDF : I_LDC) + (uint32_t)f.occ;
+        opc = feat ? I_PSF : I_PSC;
       } else {
         opc = feat ? I_LDF0 : I_LDC0;
       }
@@ -328,7 +325,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       c.live = 1; c.phase = 0; c.order = 0; c.c1 = -1;
     } else {
       if (basis >= max_slots) { res.status = 2; return res; }
-      const uint32_t opc = slot_opcode(f.order != 0, kind, basis);
+      const uint32_t opc = stack_opcode(f.order != 0, kind);
       const int sl = f.order ? ret : f.c1;
       const int sr = f.order ? f.c1 : ret;
       ret = emit(opc, 0, 0.f, sl, sr, f.pos, -1);

@@ -45,6 +45,7 @@ struct FwdParams {
   const int* len;      // [P]
   int lstride, P;
   int tile_rows, n_tiles, group, n_items;
+  int slots;           // stack slots per warp (at least the deepest program's)
   float* part;         // [P][n_tiles][NPART]
   int* counter;        // work-item counter, zero at launch
   unsigned* status;
@@ -55,10 +56,12 @@ struct FwdParams {
 // S_dy, and max |f|, all FP32; the finaliser combines them in FP64
 constexpr int NPART = 8;
 
-// two tile buffers, one program buffer per warp, two mbarriers, two
-// 4-int control blocks
-__host__ __device__ inline size_t fwd_smem_bytes(int F, int tile_rows, int warps, int lstride) {
-  return 2 * (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * lstride * 8 + 16 + 32;
+// two tile buffers, one stack of `slots` x 32 lanes x R floats per warp, one
+// program buffer per warp, two mbarriers, two 4-int control blocks
+__host__ __device__ inline size_t fwd_smem_bytes(int F, int tile_rows, int warps, int lstride,
+                                                 int slots, int R) {
+  return 2 * (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * slots * 32 * R * 4 +
+         (size_t)warps * lstride * 8 + 16 + 32;
 }
 
 template <int R, bool MASK>
@@ -167,7 +170,7 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int s, float* x
 // ever waits for the others except for the tile it is about to use.
 // MINB is the launch-bounds occupancy target: 1 lets the compiler use up to
 // 128 registers per thread, 2 caps it at 64 (two 512-thread CTAs per SM).
-template <int DMAX, int R, bool EXACT, bool ROWS, int MINB, bool POW>
+template <int R, bool EXACT, bool ROWS, int MINB, bool POW>
 __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -175,9 +178,11 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   const int nw = blockDim.x >> 5;
   const size_t tile_floats = (size_t)(p.F + 1) * p.tile_rows;
   float* xsb = reinterpret_cast<float*>(smem);  // two tile buffers
-  uint2* wprog = reinterpret_cast<uint2*>(xsb + 2 * tile_floats) + (size_t)warp * p.lstride;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint2*>(xsb + 2 * tile_floats) +
-                                              (size_t)nw * p.lstride);
+  float* stacks = xsb + 2 * tile_floats;
+  float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * R;  // this lane, slot 0
+  uint2* progs = reinterpret_cast<uint2*>(stacks + (size_t)nw * p.slots * 32 * R);
+  uint2* wprog = progs + (size_t)warp * p.lstride;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(progs + (size_t)nw * p.lstride);
   int* ctl = reinterpret_cast<int*>(bar + 2);
 
   if (threadIdx.x == 0) {
@@ -191,14 +196,9 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
     produce_tile(p, 1, xsb + tile_floats, &bar[1], ctl + 4, lane);
   }
 
-  float S[DMAX][R];
   float A[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    A[r] = 0.f;
-#pragma unroll
-    for (int j = 0; j < DMAX; ++j) S[j][r] = 0.f;
-  }
+  for (int r = 0; r < R; ++r) A[r] = 0.f;
 
   constexpr int RPP = 32 * R;  // rows per pass of a warp
   uint32_t parity = 0;         // bit s: phase parity of bar[s] this warp waits for next
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
-        run_program<DMAX, R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, S);
+        run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk);
         const int valid = nrows - r0;  // rows of this lane inside the tile
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
@@ -326,30 +326,25 @@ constexpr double VAR_TOL = 1e-12;
 // Kernel pointers: variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
 // pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
 // variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers.
-// One table per translation unit (fwd_d3.cu ... fwd_d7_pow.cu) so that the
-// instantiations compile in parallel; the _pow tables hold the kernels that
-// also run pow instructions (kept apart because the pow code costs the other
-// kernels registers and instruction-cache locality).
+// fwd.cu holds the table of the kernels without pow, fwd_pow.cu the kernels
+// that also run pow instructions (kept apart because the pow code costs the
+// other kernels registers and instruction-cache locality).
 constexpr int NVARIANT = 7;
-template <int D, bool P>
+template <bool P>
 const void* fwd_table(int variant) {
   switch (variant) {
-    case 0: return reinterpret_cast<const void*>(&fwd_kernel<D, 8, false, false, 1, P>);
-    case 1: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, false, false, 1, P>);
-    case 2: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, false, 1, P>);
-    case 3: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, true, 1, P>);
-    case 4: return reinterpret_cast<const void*>(&fwd_kernel<D, 8, false, false, 2, P>);
-    case 5: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, false, false, 2, P>);
-    case 6: return reinterpret_cast<const void*>(&fwd_kernel<D, 4, true, false, 2, P>);
+    case 0: return reinterpret_cast<const void*>(&fwd_kernel<8, false, false, 1, P>);
+    case 1: return reinterpret_cast<const void*>(&fwd_kernel<4, false, false, 1, P>);
+    case 2: return reinterpret_cast<const void*>(&fwd_kernel<4, true, false, 1, P>);
+    case 3: return reinterpret_cast<const void*>(&fwd_kernel<4, true, true, 1, P>);
+    case 4: return reinterpret_cast<const void*>(&fwd_kernel<8, false, false, 2, P>);
+    case 5: return reinterpret_cast<const void*>(&fwd_kernel<4, false, false, 2, P>);
+    case 6: return reinterpret_cast<const void*>(&fwd_kernel<4, true, false, 2, P>);
     default: return nullptr;
   }
 }
-const void* fwd_ptr_d3(int variant);
-const void* fwd_ptr_d5(int variant);
-const void* fwd_ptr_d7(int variant);
-const void* fwd_ptr_d3_pow(int variant);
-const void* fwd_ptr_d5_pow(int variant);
-const void* fwd_ptr_d7_pow(int variant);
+const void* fwd_ptr_plain(int variant);
+const void* fwd_ptr_pow(int variant);
 inline int variant_rows(int v) { return (v == 0 || v == 4) ? 8 : 4; }
 inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
 

@@ -16,6 +16,7 @@ struct AdjParams {
   const Aux* aux;      // [P][lstride]
   const int* len;      // [P]
   int lstride, P, stride;
+  int slots;           // stack slots per warp
   const double* ab;    // [P][4]: a* - mean(y), b*, finite flag, unused
   int mse_mode;        // 0: d smse / d c, 1: d mse / d c
   double ybar;
@@ -48,16 +49,20 @@ struct TransposeParams {
 };
 
 // per warp and program instruction: word, side information, (hi, lo)
-// gradient accumulator, and one value or adjoint for each of 32 rows
+// gradient accumulator, and one value or adjoint for each of 32 rows; then
+// the warp's stack of `slots` x 32 floats
 constexpr int ADJ_WARP_BYTES_PER_INSTR = 8 + 8 + 8 + 32 * 4;
 
-inline size_t adj_smem_bytes(int warps, int lstride) {
-  return (size_t)warps * lstride * ADJ_WARP_BYTES_PER_INSTR + 16;
+__host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots) {
+  return (size_t)lstride * ADJ_WARP_BYTES_PER_INSTR + (size_t)slots * 32 * 4;
+}
+inline size_t adj_smem_bytes(int warps, int lstride, int slots) {
+  return (size_t)warps * adj_warp_bytes(lstride, slots) + 16;
 }
 
 const void* pack_ptr();
 const void* fin_ptr();
-const void* adj_ptr(int dmax, bool pow);
+const void* adj_ptr(bool pow);
 const void* gradout_ptr();
 const void* adam_ptr();
 const void* transpose_ptr();

@@ -6,9 +6,9 @@ import math
 
 import numpy as np
 
-I_LDF0, I_LDC0, I_UN, I_BF, I_BC, I_LF, I_LC, I_BS, I_RS, I_LDF, I_LDC, I_NOP = \
-    0, 1, 2, 10, 15, 20, 25, 30, 70, 110, 118, 126
-I_PW, I_PWS, I_PWR, I_END = 127, 131, 139, 147  # pow: fused groups, then slot forms
+I_LDF0, I_LDC0, I_PSF, I_PSC, I_UN, I_BF, I_BC, I_LF, I_LC, I_BS, I_RS, I_NOP = \
+    0, 1, 2, 3, 4, 12, 17, 22, 27, 32, 37, 42
+I_PW, I_PWS, I_PWR, I_END = 43, 47, 48, 49  # pow: fused groups, then the stack forms
 KINDS = ["+", "-", "*", "aq", "/", "pow"]
 UNARY = ["sin", "cos", "exp", "logabs", "sqrtabs", "sq", "log", "sqrt"]
 
@@ -35,49 +35,46 @@ def unop(u, a):
 
 
 def decode(word):
+    """(form, arg, feature) of one instruction word; form is ldf / ldc (with
+    arg True when the load pushes A first), un, bf, bc, lf, lc, bs or rs."""
     opc = int(word) & 0xFF
     feat = int(word) >> 8
-    if opc == I_LDF0:
-        return ("ldf", None, feat)
-    if opc == I_LDC0:
-        return ("ldc", None, None)
+    if opc in (I_LDF0, I_PSF):
+        return ("ldf", opc == I_PSF, feat)
+    if opc in (I_LDC0, I_PSC):
+        return ("ldc", opc == I_PSC, None)
     if I_UN <= opc < I_BF:
         return ("un", opc - I_UN, None)
     if I_BF <= opc < I_BS:
         grp, k = divmod(opc - I_BF, 5)
         return (["bf", "bc", "lf", "lc"][grp], k, feat)
     if I_BS <= opc < I_RS:
-        k, j = divmod(opc - I_BS, 8)
-        return ("bs", (k, j), None)
-    if I_RS <= opc < I_LDF:
-        k, j = divmod(opc - I_RS, 8)
-        return ("rs", (k, j), None)
-    if I_LDF <= opc < I_LDC:
-        return ("ldf", opc - I_LDF, feat)
-    if I_LDC <= opc < I_NOP:
-        return ("ldc", opc - I_LDC, None)
+        return ("bs", opc - I_BS, None)
+    if I_RS <= opc < I_NOP:
+        return ("rs", opc - I_RS, None)
     if I_PW <= opc < I_PWS:
         return (["bf", "bc", "lf", "lc"][opc - I_PW], 5, feat)
-    if I_PWS <= opc < I_PWR:
-        return ("bs", (5, opc - I_PWS), None)
-    if I_PWR <= opc < I_END:
-        return ("rs", (5, opc - I_PWR), None)
+    if opc == I_PWS:
+        return ("bs", 5, None)
+    if opc == I_PWR:
+        return ("rs", 5, None)
     raise ValueError(opc)
 
 
-def run(words, consts, X, max_slots=8):
-    """Evaluate a packed program over all rows of X (FP64)."""
+def run(words, consts, X):
+    """Evaluate a packed program over all rows of X (FP64); returns the
+    values and the deepest stack (slots) the program used."""
     n = X.shape[0]
     A = np.zeros(n)
-    S = [np.zeros(n) for _ in range(max_slots)]
-    used = -1
+    stack = []
+    used = 0
     for w, c in zip(words, consts):
         form, arg, feat = decode(w)
         c = float(c)
         if form in ("ldf", "ldc"):
-            if arg is not None:
-                S[arg] = A.copy()
-                used = max(used, arg)
+            if arg:
+                stack.append(A.copy())
+                used = max(used, len(stack))
             A = X[:, feat].astype(np.float64) if form == "ldf" else np.full(n, c)
         elif form == "un":
             A = unop(arg, A)
@@ -90,12 +87,11 @@ def run(words, consts, X, max_slots=8):
         elif form == "lc":
             A = binop(arg, np.full(n, c), A)
         elif form == "bs":
-            k, j = arg
-            A = binop(k, S[j], A)
+            A = binop(arg, stack.pop(), A)
         elif form == "rs":
-            k, j = arg
-            A = binop(k, A, S[j])
-    return A, used + 1
+            A = binop(arg, A, stack.pop())
+    assert not stack, "program left values on the stack"
+    return A, used
 
 
 def tokens(words, consts):
@@ -114,5 +110,5 @@ def tokens(words, consts):
         elif form in ("bc", "lc"):
             out.append(f"{form} {KINDS[arg]} {float(c):g}")
         else:
-            out.append(f"{form} {KINDS[arg[0]]} s{arg[1]}")
+            out.append(f"{form} {KINDS[arg]}")
     return out
