@@ -43,28 +43,26 @@ __device__ __forceinline__ float unop(float a) {
   return 0.f;
 }
 
-// A unary operator on the R rows of a lane.  When the branch-free forms of
-// gmath.cuh are selected, one test over the R rows sends an argument
-// outside their domain (|x| > 2^17 for sin and cos; zero, subnormal,
-// infinite or NaN for sqrt) to the CUDA library function on a cold path, so
-// the common path has no per-row branch.
-// By default every operator uses the CUDA library functions: at the
-// 64-register budget of the fastest kernel variant the branch-free forms
-// cost more in registers than they save in instructions (measured on the
-// FOS-step workload).  -DGG_OWN_TRIG and -DGG_OWN_SQRT select them; they pay
-// off for kernels with 8 rows per lane, whose code then fits the
-// instruction cache.
+// A unary operator on the R rows of a lane.  sin, cos and sqrt use the
+// branch-free forms of gmath.cuh: one test over the R rows sends an
+// argument outside their domain (|x| > 2^17 for sin and cos; zero,
+// subnormal, infinite or NaN for sqrt) to the CUDA library function on a
+// cold path, so the common path has no per-row branch and each case holds
+// one short copy of the math per row (the library functions' range
+// handling, replicated R times in every case, crowds the instruction cache:
+// measured 3 to 9 % slower per step).  -DGG_LIBM_TRIG and -DGG_LIBM_SQRT
+// select the library functions everywhere.
 template <int U, int R>
 __device__ __forceinline__ void unop_rows(float (&A)[R]) {
-#ifdef GG_OWN_TRIG
-  constexpr bool own_trig = true;
-#else
+#ifdef GG_LIBM_TRIG
   constexpr bool own_trig = false;
-#endif
-#ifdef GG_OWN_SQRT
-  constexpr bool own = true;
 #else
+  constexpr bool own_trig = true;
+#endif
+#ifdef GG_LIBM_SQRT
   constexpr bool own = false;
+#else
+  constexpr bool own = true;
 #endif
   if constexpr (own_trig && (U == U_SIN || U == U_COS)) {
     bool big = false;
