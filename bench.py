@@ -7,14 +7,18 @@ function set), X 100,000 x 8 ~ U[-3, 3], y from a seeded height-4 tree plus
 1 % noise.  Inputs are resident in HBM when the timed region starts; L2 is
 flushed (a 512 MB write) between timed steps.  Reported:
 
-  value      node-row evals/s (active nodes x rows x trials / s), graph form
+  value      node-row evals/s (active nodes x rows x trials / s), graph form;
+             the library folds each feature-free subtree into one constant
+             (bit-identical outputs), so fewer nodes run per row than the
+             active count: config.nodes_evaluated_per_row_per_step
   e2e        the same through the C ABI with pinned HOST buffers: the H2D
              copy of the trial arrays and the D2H copy of the fitness inside
              every step
   plain      the one-launch-per-trial form (multi-block per trial + a
              second-stage reduction launch per trial)
   roofline   the batched forward kernel against the FP32 issue peak
-             (152 SMs x 128 lanes x the SM clock sampled during the run)
+             (152 SMs x 128 lanes x the SM clock sampled during the run),
+             counting the operations of the folded programs
   cpu_baseline  the FP64 oracle on the host cores, on a sample of trials
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -55,6 +59,9 @@ ACC_FP32 = 4
 NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4275200 + 9472}
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}
+# the same classes after constant folding (the nodes evaluated on every row)
+EXEC_COLS = {"term": 14, "addsubmul": 15, "aq": 16, "div": 17, "sincos": 18, "exp": 19,
+             "log": 20, "sqrt": 21, "square": 22, "pow": 23}
 
 
 def parse():
@@ -172,9 +179,10 @@ def node_counts(gg, torch, w):
                         n_features=w["F"]).numpy()
     ok = st[:, 0] >= 0
     nodes = int(st[ok, 0].sum())
-    fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in STAT_COLS.items())
-    sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in STAT_COLS.items())
-    return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 10].sum())
+    # algorithmic operations of what runs per row: the program after folding
+    fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
+    sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
+    return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 13].sum())
 
 
 def cpu_baseline(w, seconds, torch):
@@ -395,7 +403,7 @@ def main():
 
     w = make_workload(a.config, rank, gg, torch, dev)
     PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
-    nodes, fp32_ops, sfu_ops, valid, instrs = node_counts(gg, torch, w)
+    nodes, fp32_ops, sfu_ops, valid, nodes_eval = node_counts(gg, torch, w)
     N, P = w["N"], w["P"]
     ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
     op = torch.from_numpy(w["op"]).cuda(dev)
@@ -499,7 +507,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "trials_per_step": P, "rows": N,
                    "features": w["F"], "template_height": w["h_max"],
-                   "active_nodes_per_step": nodes, "flush_l2": "512 MB write between steps",
+                   "active_nodes_per_step": nodes,
+                   "nodes_evaluated_per_row_per_step": nodes_eval,
+                   "flush_l2": "512 MB write between steps",
                    "form": "persistent batched kernel, CUDA graph replay, autotuned tiles",
                    "parallelism": f"replicas x{world} (independent FOS steps)"},
         "trial_evals_per_s": trial_rate,

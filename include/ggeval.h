@@ -126,12 +126,18 @@ enum {
   GGEVAL_F_PROFILE = 1u << 3, /* record CUDA events around the batched
                                  forward kernel (not with GGEVAL_F_GRAPH);
                                  read them with ggeval_profile_read        */
-  GGEVAL_F_POW = 1u << 4      /* the batch may hold active POW nodes: run
+  GGEVAL_F_POW = 1u << 4,     /* the batch may hold active POW nodes: run
                                  the kernel builds that include pow.
                                  Without it an active POW node is an
                                  invalid template (GGEVAL_ERR_TEMPLATE); the
                                  other kernels leave the pow code out
                                  because it costs them registers and speed */
+  GGEVAL_F_NO_FOLD = 1u << 5  /* evaluate constant subtrees on every row.
+                                 By default the packer folds each active
+                                 subtree without a feature into one constant,
+                                 computed once per trial with the same FP32
+                                 functions, so the outputs are bit-identical
+                                 either way; the gradient never folds      */
 };
 
 /* Create a dataset from X (n_rows x n_features, float32, row-major when
@@ -227,10 +233,12 @@ const char* ggeval_last_error(void);
  * of active nodes by class.  out is int64 [n][GGEVAL_NSTAT] host memory:
  * [0] active nodes, [1] terminals, [2] +/-/x, [3] AQ, [4] DIV,
  * [5] sin/cos, [6] exp, [7] log, [8] sqrt, [9] square; [10] interpreter
- * instructions after fusion; [11] stack slots used; [12] pow.  An invalid
- * trial has -1 in [0].  Host batches only; runs on the CPU, no dataset
- * needed. */
-#define GGEVAL_NSTAT 13
+ * instructions after fusion; [11] stack slots used; [12] pow;
+ * [13..23] the counts of [0..9] and pow ([23]) for the nodes evaluated on
+ * every row after constant folding (GGEVAL_F_NO_FOLD); [24] interpreter
+ * instructions after folding.  An invalid trial has -1 in [0].  Host
+ * batches only; runs on the CPU, no dataset needed. */
+#define GGEVAL_NSTAT 25
 ggeval_status ggeval_batch_stats(const ggeval_batch* batch, int32_t n_features,
                                  int64_t* out);
 

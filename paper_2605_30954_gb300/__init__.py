@@ -4,7 +4,7 @@ The compute path is the CUDA library built from ``csrc/`` (see
 ``include/ggeval.h``); :mod:`.ggeval` is its Python binding.
 """
 from .ggeval import (  # noqa: F401
-    F_EXACT, F_GRAD_MSE, F_GRAPH, F_POW, F_PROFILE, LAYOUT_HEAP, LAYOUT_PREFIX, Dataset, GGEvalError, ScaledMSE,
+    F_EXACT, F_GRAD_MSE, F_GRAPH, F_NO_FOLD, F_POW, F_PROFILE, LAYOUT_HEAP, LAYOUT_PREFIX, Dataset, GGEvalError, ScaledMSE,
     adam_step, batch_stats, gom_accept, gom_changed, gom_donate, lib, make_batch, pack_host,
     trial_sizes)
 from .build import build  # noqa: F401

@@ -60,11 +60,19 @@ struct DeviceGuard {
 };
 
 inline int stride_of(int h) { return (1 << (h + 1)) - 1; }
-// threads per block of the packing kernel: each thread keeps 2 x stride
-// bytes of scratch in shared memory, within the 48 KB default
+// threads per block of the kernels that mark active nodes (GOM "changed",
+// trial sizes): each thread keeps 2 x stride bytes of shared scratch, within
+// the 48 KB default
 inline int pack_threads(int stride) {
   int t = (49152 / (2 * stride)) & ~31;
   return t < 32 ? 32 : (t > 128 ? 128 : t);
+}
+// threads per block of the packing kernel (6 x stride bytes of scratch each,
+// within the 48 KB default; 16 threads for the 511-node templates)
+inline int pack_kernel_threads(int stride) {
+  int t = 49152 / (int)gg::pack_scratch_bytes(stride);
+  t = t >= 32 ? (t & ~31) : (t & ~7);
+  return t > 128 ? 128 : (t < 8 ? 8 : t);
 }
 // stack slots of a template of height h: Sethi-Ullman order with fused
 // terminals needs at most h - 1 (the packer checks the bound)
@@ -102,6 +110,7 @@ struct Cfg {
 struct Plan {
   Cfg cfg;
   bool pow = false;  // kernels with the pow instructions; the packer accepts pow
+  bool fold = true;  // the packer folds constant subtrees (not GGEVAL_F_NO_FOLD)
   int slots = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
   size_t smem = 0;
   const void* fn = nullptr;
@@ -334,8 +343,10 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.status = ds->status;
   pp.mask = mask;
   pp.allow_pow = pl.pow ? 1 : 0;
-  const int pt = pack_threads(pl.stride);
-  return launch(gg::pack_ptr(), dim3((n + pt - 1) / pt), dim3(pt), (size_t)pt * 2 * pl.stride, st,
+  pp.fold = pl.fold ? 1 : 0;
+  const int pt = pack_kernel_threads(pl.stride);
+  return launch(gg::pack_ptr(), dim3((n + pt - 1) / pt), dim3(pt),
+                (size_t)pt * gg::pack_scratch_bytes(pl.stride), st,
                 &pp);
 }
 
@@ -574,6 +585,7 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan pl;
   GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl, has_pow(flags)));
+  pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   DevBatch db;
@@ -670,6 +682,7 @@ ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint3
   c.tile_rows = 32 * gg::variant_rows(c.variant);
   Plan pl;
   GG_TRY(make_plan(ds, 1, b->max_height, c, &pl, has_pow(flags)));
+  pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   DevBatch db{b->op, b->cval, b->height};
   GG_TRY(enqueue_pack(ds, db, b->n, b->max_height, b->layout, pl, false, st));
@@ -700,6 +713,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan pl;
   GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl, has_pow(flags)));
+  pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
   GG_TRY(ensure_ws(ds, b->n, pl, true));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   const size_t gcount = (size_t)b->n * pl.stride;
@@ -806,7 +820,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   const Cfg base = default_cfg(ds, b->n, b->max_height, flags);
   std::vector<int> variants;
   if (base.variant == 2) variants = {2, 6};
-  else variants = {5, 1, 4};
+  else variants = {5, 1, 4, 0};
   std::vector<Cfg> cands;
   for (int v : variants)
     for (int warps : {8, 16})
@@ -840,6 +854,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   for (const Cfg& c : cands) {
     Plan pl;
     if (make_plan(ds, b->n, b->max_height, c, &pl, has_pow(flags)) != GGEVAL_OK) continue;
+    pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
     if ((result = ensure_ws(ds, b->n, pl, false)) != GGEVAL_OK) break;
     if ((result = enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st)) !=
         GGEVAL_OK)
@@ -982,6 +997,14 @@ ggeval_status ggeval_profile_read(ggeval_dataset* ds, double* fwd_ms, int64_t* l
   return GGEVAL_OK;
 }
 
+// Folding structure without values: lengths and node counts of the folded
+// program on the host (the device computes the folded constants).
+struct ShapeFold {
+  static constexpr bool on = true;
+  float un(int, float) const { return 0.f; }
+  float bin(int, float, float) const { return 0.f; }
+};
+
 ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int64_t* out) {
   if (!b || !out) return fail(GGEVAL_ERR_ARG, "NULL argument");
   if (b->memory != GGEVAL_MEM_HOST) return fail(GGEVAL_ERR_ARG, "batch_stats needs a host batch");
@@ -990,7 +1013,7 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
   if (b->n > 0 && (!b->op || !b->cval)) return fail(GGEVAL_ERR_ARG, "op or cval is NULL");
   const int stride = stride_of(b->max_height);
   std::vector<uint32_t> w(stride + 1);
-  std::vector<float> c(stride + 1);
+  std::vector<float> c(stride + 1), fv(stride);
   std::vector<uint8_t> d1(stride), nd(stride);
   for (int t = 0; t < b->n; ++t) {
     const int h = b->height ? b->height[t] : b->max_height;
@@ -1000,18 +1023,25 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
       o[0] = -1;
       continue;
     }
-    const gg::PackResult r =
-        gg::pack_tree(b->op + (size_t)t * stride, b->cval + (size_t)t * stride, h, b->layout,
-                      n_features, gg::MAX_SLOTS, w.data(), c.data(), 1, nullptr, stride,
-                      d1.data(), nd.data());
+    const uint8_t* op = b->op + (size_t)t * stride;
+    const float* cv = b->cval + (size_t)t * stride;
+    const gg::PackResult r = gg::pack_tree(op, cv, h, b->layout, n_features, gg::MAX_SLOTS,
+                                           w.data(), c.data(), 1, nullptr, stride, d1.data(),
+                                           nd.data());
     if (r.status) {
       o[0] = -1;
       continue;
     }
+    // the folded program's structure (its constants are not computed here)
+    const gg::PackResult f = gg::pack_tree(op, cv, h, b->layout, n_features, gg::MAX_SLOTS,
+                                           w.data(), c.data(), 1, nullptr, stride, d1.data(),
+                                           nd.data(), true, ShapeFold(), fv.data());
     for (int i = 0; i < 10; ++i) o[i] = r.counts[i];
     o[10] = r.len;
     o[11] = r.slots;
     o[12] = r.counts[10];
+    for (int i = 0; i < 11; ++i) o[13 + i] = f.exec[i];
+    o[24] = f.len;
   }
   return GGEVAL_OK;
 }
@@ -1137,8 +1167,10 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   pp.len = len;
   pp.status = ds->status;
   pp.mask = nullptr;
-  const int pt = pack_threads(pl.stride);
-  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + pt - 1) / pt), dim3(pt), (size_t)pt * 2 * pl.stride,
+  pp.fold = 1;
+  const int pt = pack_kernel_threads(pl.stride);
+  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + pt - 1) / pt), dim3(pt),
+                (size_t)pt * gg::pack_scratch_bytes(pl.stride),
                 st, &pp));
   GG_CU(cudaMemsetAsync(counter, 0, sizeof(int), st));
   gg::FwdParams fp = fwd_params(ds, b->n, pl);

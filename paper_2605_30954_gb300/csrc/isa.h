@@ -127,7 +127,26 @@ struct PackResult {
   int slots;      // stack slots used
   int status;     // 0 ok, 1 invalid template, 2 needs more slots than allowed
   int counts[11]; // active nodes by class, see ggeval_batch_stats ([10]: pow)
+  int exec[11];   // the same for the nodes evaluated per row after constant
+                  // folding (equal to counts when folding is off)
 };
+
+// Constant folding (an addition; the paper evaluates every node on every
+// row): an active function node with no feature among its active
+// descendants has the same value on every row.  An evaluator with `on`
+// true computes such a subtree once per trial with the interpreter's own
+// FP32 operator functions, so each row gets exactly the value it would have
+// computed itself, and the packer emits the largest such subtrees as
+// constant terminals.  NoFold leaves programs unchanged.
+struct NoFold {
+  static constexpr bool on = false;
+  GG_HD float un(int, float) const { return 0.f; }
+  GG_HD float bin(int, float, float) const { return 0.f; }
+};
+// depth1[] flag bits used by the packer next to depth + 1 (at most 9)
+constexpr uint8_t PK_CONST = 0x40;   // active subtree without a feature
+constexpr uint8_t PK_INSIDE = 0x80;  // below the root of a folded subtree
+constexpr uint8_t PK_DEPTH = 0x1F;
 
 // Children of the node at `pos` (depth `depth`) in a template of height h.
 GG_HD void children(int layout, int h, int pos, int depth, int* l, int* r) {
@@ -151,15 +170,23 @@ GG_HD void children(int layout, int h, int pos, int depth, int* l, int* r) {
 // `depth1` and `need` are caller scratch of at least 2^(h+1)-1 bytes each
 // (shared memory in the packing kernel).  With allow_pow false an active
 // pow node makes the template invalid (for interpreters built without pow).
+// Folding: with `fv` (caller scratch of 2^(h+1)-1 floats) and an evaluator
+// whose `on` is true, constant subtrees are folded (never together with
+// `aux`: the adjoint needs every ERC); `fold_stats` alone marks the
+// constant subtrees and fills res.exec without changing the program.
+template <class Ev = NoFold>
 GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layout,
                            int n_features, int max_slots, uint32_t* words, float* consts,
                            int ws, Aux* aux, int cap, uint8_t* depth1, uint8_t* need,
-                           bool allow_pow = true) {
+                           bool allow_pow = true, const Ev& ev = Ev(), float* fv = nullptr,
+                           bool fold_stats = false) {
   PackResult res;
   res.len = 0;
   res.slots = 0;
   res.status = 0;
-  for (int i = 0; i < 11; ++i) res.counts[i] = 0;
+  for (int i = 0; i < 11; ++i) res.counts[i] = res.exec[i] = 0;
+  const bool fold = Ev::on && fv != nullptr && aux == nullptr;
+  const bool marks = fold || fold_stats;
   const int n = (1 << (h + 1)) - 1;
   // depth1[i]: depth + 1 of an active node, 0 for an intron;
   // need[i]: slots the active subtree at i needs
@@ -195,32 +222,75 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
                                                         : 9]++;
     }
   }
-  // pass 2: slot need of every active subtree, bottom-up
+  // pass 2: constant subtrees (and their values when folding) and the slot
+  // need of every active subtree, bottom-up; a folded subtree is a terminal
   for (int pos = n - 1; pos >= 0; --pos) {
     if (!depth1[pos]) continue;
-    const int d = depth1[pos] - 1;
+    const int d = (depth1[pos] & PK_DEPTH) - 1;
     int kind;
     const int cls = classify(op[pos], n_features, &kind);
-    if (cls == C_TERM_F || cls == C_TERM_C) {
-      need[pos] = 0;
+    need[pos] = 0;
+    if (cls == C_TERM_F) continue;
+    if (cls == C_TERM_C) {
+      if (marks) depth1[pos] |= PK_CONST;
+      if (fold) fv[pos] = cval[pos];
       continue;
     }
     int l, r;
     children(layout, h, pos, d, &l, &r);
     if (cls == C_UNARY) {
-      need[pos] = need[l];
+      if (marks && (depth1[l] & PK_CONST)) {
+        depth1[pos] |= PK_CONST;
+        if (fold) fv[pos] = ev.un(kind, fv[l]);
+      }
+      if (!(fold && (depth1[pos] & PK_CONST))) need[pos] = need[l];
       continue;
     }
+    if (marks && (depth1[l] & PK_CONST) && (depth1[r] & PK_CONST)) {
+      depth1[pos] |= PK_CONST;
+      if (fold) fv[pos] = ev.bin(kind, fv[l], fv[r]);
+    }
+    if (fold && (depth1[pos] & PK_CONST)) continue;
     int kl, kr;
     const int cl = classify(op[l], n_features, &kl);
     const int cr = classify(op[r], n_features, &kr);
-    const bool lt = cl == C_TERM_F || cl == C_TERM_C;
-    const bool rt = cr == C_TERM_F || cr == C_TERM_C;
+    const bool lt = cl == C_TERM_F || cl == C_TERM_C || (fold && (depth1[l] & PK_CONST));
+    const bool rt = cr == C_TERM_F || cr == C_TERM_C || (fold && (depth1[r] & PK_CONST));
     if (rt) need[pos] = need[l];
     else if (lt) need[pos] = need[r];
     else {
       const int a = need[l], b = need[r];
       need[pos] = (uint8_t)(a >= b ? (a > b + 1 ? a : b + 1) : (b > a + 1 ? b : a + 1));
+    }
+  }
+  // node counts of the folded program: a folded subtree's root becomes one
+  // constant terminal and the nodes below it disappear (top-down)
+  for (int i = 0; i < 11; ++i) res.exec[i] = res.counts[i];
+  if (marks) {
+    for (int pos = 0; pos < n; ++pos) {
+      if (!depth1[pos]) continue;
+      int kind;
+      const int cls = classify(op[pos], n_features, &kind);
+      const bool inside = (depth1[pos] & PK_INSIDE) != 0;
+      const bool root = !inside && (depth1[pos] & PK_CONST) && (cls == C_UNARY || cls == C_BINARY);
+      if (!inside && !root) continue;
+      int slot = 1;  // terminal
+      if (cls == C_BINARY) slot = kind == K_AQ ? 3 : kind == K_DIV ? 4 : kind == K_POW ? 10 : 2;
+      if (cls == C_UNARY)
+        slot = kind == U_SIN || kind == U_COS ? 5
+               : kind == U_EXP ? 6
+               : (kind == U_LOG_ABS || kind == U_LOG) ? 7
+               : (kind == U_SQRT_ABS || kind == U_SQRT) ? 8 : 9;
+      res.exec[slot]--;
+      if (inside) res.exec[0]--;
+      else res.exec[1]++;  // the root is now a constant terminal
+      if (cls == C_UNARY || cls == C_BINARY) {
+        const int d = (depth1[pos] & PK_DEPTH) - 1;
+        int l, r;
+        children(layout, h, pos, d, &l, &r);
+        depth1[l] |= PK_INSIDE;
+        if (cls == C_BINARY) depth1[r] |= PK_INSIDE;
+      }
     }
   }
   // pass 3: emission
@@ -249,10 +319,21 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
     }
     return k++;
   };
+  // class and constant of a node as emitted: a folded subtree is a constant
+  auto eclass = [&](int pos, int* kind) -> int {
+    if (fold && (depth1[pos] & PK_CONST)) {
+      *kind = 0;
+      return C_TERM_C;
+    }
+    return classify(op[pos], n_features, kind);
+  };
+  auto evalue = [&](int pos) -> float {
+    return fold && (depth1[pos] & PK_CONST) ? fv[pos] : cval[pos];
+  };
   while (sp > 0) {
     Frame& f = st[sp - 1];
     int kind;
-    const int cls = classify(op[f.pos], n_features, &kind);
+    const int cls = eclass(f.pos, &kind);
     if (cls == C_TERM_F || cls == C_TERM_C) {
       const bool feat = cls == C_TERM_F;
       uint32_t opc;
@@ -263,7 +344,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       } else {
         opc = feat ? I_LDF0 : I_LDC0;
       }
-      ret = emit(opc, feat ? kind : 0, feat ? 0.f : cval[f.pos], -1, -1, f.pos, -1);
+      ret = emit(opc, feat ? kind : 0, feat ? 0.f : evalue(f.pos), -1, -1, f.pos, -1);
       if (ret < 0) { res.status = 2; return res; }
       --sp;
       continue;
@@ -284,8 +365,8 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       continue;
     }
     int kl, kr;
-    const int cl = classify(op[l], n_features, &kl);
-    const int cr = classify(op[r], n_features, &kr);
+    const int cl = eclass(l, &kl);
+    const int cr = eclass(r, &kr);
     const bool lt = cl == C_TERM_F || cl == C_TERM_C;
     const bool rt = cr == C_TERM_F || cr == C_TERM_C;
     if (rt || lt) {
@@ -303,7 +384,7 @@ GG_HD PackResult pack_tree(const uint8_t* op, const float* cval, int h, int layo
       } else {
         const bool feat = ct == C_TERM_F;
         const int group = rt ? (feat ? 0 : 1) : (feat ? 2 : 3);
-        ret = emit(fused_opcode(group, kind), feat ? kt : 0, feat ? 0.f : cval[term],
+        ret = emit(fused_opcode(group, kind), feat ? kt : 0, feat ? 0.f : evalue(term),
                    rt ? ret : -1, rt ? -1 : ret, f.pos, term);
         if (ret < 0) { res.status = 2; return res; }
         --sp;

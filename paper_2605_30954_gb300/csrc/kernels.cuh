@@ -20,7 +20,12 @@ struct PackParams {
   unsigned* status;
   const uint8_t* mask;   // nullable: evaluate only trials with a nonzero byte
   int allow_pow;         // 0: an active pow node makes the trial invalid
+  int fold;              // fold constant subtrees (ignored when aux is set)
 };
+
+// shared scratch of the packing kernel per thread: folded values (floats),
+// depth flags and slot needs (bytes) for every template node
+inline size_t pack_scratch_bytes(int stride) { return (size_t)stride * 6; }
 
 // pack_kernel (defined in misc.cu): one thread per trial.
 

@@ -4,12 +4,48 @@
 
 namespace gg {
 
-// One thread per trial: linearise its template (Section 3.2, Fig. 1).
+// The interpreter's own operator functions for constant folding: unop_rows
+// with one row picks the same code path as R equal rows do, and binop is
+// the interpreter's binary operator, so a folded constant is bit-identical
+// to the value the interpreter would compute on every row.
+struct DevFold {
+  static constexpr bool on = true;
+  __device__ float un(int u, float a) const {
+    float v[1] = {a};
+    switch (u) {
+      case U_SIN: unop_rows<U_SIN, 1>(v); break;
+      case U_COS: unop_rows<U_COS, 1>(v); break;
+      case U_EXP: unop_rows<U_EXP, 1>(v); break;
+      case U_LOG_ABS: unop_rows<U_LOG_ABS, 1>(v); break;
+      case U_SQRT_ABS: unop_rows<U_SQRT_ABS, 1>(v); break;
+      case U_SQUARE: unop_rows<U_SQUARE, 1>(v); break;
+      case U_LOG: unop_rows<U_LOG, 1>(v); break;
+      default: unop_rows<U_SQRT, 1>(v); break;
+    }
+    return v[0];
+  }
+  __device__ float bin(int k, float a, float b) const {
+    switch (k) {
+      case K_ADD: return binop<K_ADD>(a, b);
+      case K_SUB: return binop<K_SUB>(a, b);
+      case K_MUL: return binop<K_MUL>(a, b);
+      case K_AQ: return binop<K_AQ>(a, b);
+      case K_DIV: return binop<K_DIV>(a, b);
+      default: return binop<K_POW>(a, b);
+    }
+  }
+};
+
+// One thread per trial: linearise its template (Section 3.2, Fig. 1),
+// folding constant subtrees unless p.fold is 0 or side information for the
+// adjoint is wanted.  Shared scratch per block: [threads][stride] floats of
+// folded values, then [threads][stride] bytes twice (depth flags, need).
 __global__ void pack_kernel(const PackParams p) {
-  extern __shared__ unsigned char pk_smem[];
+  extern __shared__ __align__(16) unsigned char pk_smem[];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.n) return;
-  uint8_t* depth1 = pk_smem + (size_t)threadIdx.x * 2 * p.stride;
+  float* fv = reinterpret_cast<float*>(pk_smem) + (size_t)threadIdx.x * p.stride;
+  uint8_t* depth1 = pk_smem + (size_t)blockDim.x * p.stride * 4 + (size_t)threadIdx.x * 2 * p.stride;
   uint8_t* need = depth1 + p.stride;
   if (p.mask && !p.mask[t]) {  // not evaluated in this call
     p.len[t] = 0;
@@ -24,7 +60,8 @@ __global__ void pack_kernel(const PackParams p) {
                                    reinterpret_cast<uint32_t*>(prog),
                                    reinterpret_cast<float*>(prog) + 1, 2,
                                    p.aux ? p.aux + (size_t)t * p.lstride : nullptr,
-                                   p.lstride - 1, depth1, need, p.allow_pow != 0);
+                                   p.lstride - 1, depth1, need, p.allow_pow != 0, DevFold(),
+                                   p.fold && !p.aux ? fv : nullptr);
     if (r.status == 0) L = r.len;
   }
   p.len[t] = L;

@@ -100,12 +100,41 @@ def test_packed_programs_compute_the_oracle_value(gg, h, layout):
             assert len(words) <= int(O.active_mask(t).sum())
 
 
+def folded_nodes(t):
+    """(nodes strictly below the roots of maximal feature-free active
+    subtrees, number of such roots that are functions)."""
+    out = [0, 0]
+
+    def const(pos, d):  # -> (no feature below, active size)
+        o = int(t.op[pos])
+        if o >= synth.FEAT0 and o != synth.PAD:
+            return False, 1
+        if o == synth.ERC:
+            return True, 1
+        l, r = t.children(pos, d)
+        parts = [const(l, d + 1)] + ([const(r, d + 1)] if o in synth.BINARY else [])
+        c = all(x[0] for x in parts)
+        if not c:
+            for pc, pn in parts:
+                if pc and pn > 1:
+                    out[0] += pn - 1
+                    out[1] += 1
+        return c, 1 + sum(x[1] for x in parts)
+
+    c, n = const(0, 0)
+    if c and n > 1:
+        out[0] += n - 1
+        out[1] += 1
+    return out[0], out[1]
+
+
 def test_stats_count_active_nodes(gg):
     rng = np.random.default_rng(3)
     op, cv, hs = synth.random_templates(rng, 50, rng.integers(0, 6, 50), 5,
                                         synth.FULL_SET + (synth.POW,), 4, 0.7)
     st = gg.batch_stats(torch.from_numpy(op), torch.from_numpy(cv),
                         torch.from_numpy(hs), n_features=4).numpy()
+    total_removed = 0
     for p in range(50):
         t = O.Template(op[p], cv[p], int(hs[p]), n_features=4)
         mask = O.active_mask(t)
@@ -113,6 +142,14 @@ def test_stats_count_active_nodes(gg):
         assert st[p, 1] == np.sum(mask & (op[p] >= synth.ERC))
         assert st[p, 0] == st[p, 1:10].sum() + st[p, 12]
         assert st[p, 12] == np.sum(mask & (op[p] == synth.POW))
+        # constant folding: every active subtree without a feature becomes one
+        # constant terminal (structure counted here by a plain recursion)
+        removed, roots = folded_nodes(t)
+        total_removed += removed
+        assert st[p, 13] == st[p, 0] - removed and st[p, 14] >= roots
+        assert st[p, 13] == st[p, 14:23].sum() + st[p, 23]
+        assert st[p, 24] <= st[p, 10]
+    assert total_removed > 10  # the batch has constant subtrees to fold
 
 
 @pytest.mark.parametrize("tokens,h", [

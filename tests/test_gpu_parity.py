@@ -270,6 +270,32 @@ def test_pow_needs_its_flag(gg):
     ds.close()
 
 
+@pytest.mark.parametrize("cfg", ["c2", "c3", "t2", "l_squ"])
+def test_constant_folding_is_bit_identical(gg, cfg):
+    """Folding constant subtrees (the default) must not change a single bit
+    of the outputs: the folded constants are computed with the
+    interpreter's own FP32 operator functions."""
+    w = PA.build(cfg, 3001, 96)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op, cv = dev(w["op"]), dev(w["cval"])
+    hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
+    pf = gg.F_POW if w.get("uses_pow") else 0
+    st = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
+                        torch.from_numpy(w["heights"]), n_features=w["F"]).numpy()
+    assert st[st[:, 0] >= 0, 13].sum() < st[st[:, 0] >= 0, 0].sum()  # something folds
+    for flags in (pf, pf | gg.F_EXACT):
+        a = [t.cpu().numpy() for t in ds.eval_batch(op, cv, hs, flags=flags)]
+        b = [t.cpu().numpy() for t in ds.eval_batch(op, cv, hs, flags=flags | gg.F_NO_FOLD)]
+        for x, z in zip(a, b):
+            np.testing.assert_array_equal(x, z)
+    p1 = [t.cpu().numpy() for t in ds.eval_plain(op, cv, hs, flags=pf)]
+    p2 = [t.cpu().numpy() for t in ds.eval_plain(op, cv, hs, flags=pf | gg.F_NO_FOLD)]
+    for x, z in zip(p1, p2):
+        np.testing.assert_array_equal(x, z)
+    ds.sync()
+    ds.close()
+
+
 def test_bad_arguments_rejected(gg):
     X = torch.zeros((10, 2))
     y = torch.arange(10, dtype=torch.float32)
