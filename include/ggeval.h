@@ -253,6 +253,17 @@ ggeval_status ggeval_pack_host(const ggeval_batch* batch, int32_t index, int32_t
                                uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
                                int32_t* len);
 
+/* The device packer, for inspection and tests: packs a device batch exactly
+ * as the evaluation calls do with these flags (GGEVAL_F_POW accepts pow;
+ * constant subtrees are folded unless GGEVAL_F_NO_FOLD) and copies the
+ * programs to host memory: words uint32 [n][cap] (opcode | feature << 8),
+ * consts float [n][cap], len int32 [n] (the instruction count, -1 for an
+ * invalid trial, whose template error also reaches ggeval_sync).  Entries
+ * past a trial's length are left as they were.  Synchronous on `stream`. */
+ggeval_status ggeval_pack_device(ggeval_dataset* ds, const ggeval_batch* batch, uint32_t flags,
+                                 uint32_t* words, float* consts, int32_t* len, int32_t cap,
+                                 void* stream);
+
 /* Evaluate only the trials whose mask byte is nonzero: Evaluate(O[changed])
  * of Algorithm 1.  mask is uint8 [n] in device memory (device batches only);
  * the outputs of masked-out trials are left untouched.  Otherwise as

@@ -67,13 +67,6 @@ inline int pack_threads(int stride) {
   int t = (49152 / (2 * stride)) & ~31;
   return t < 32 ? 32 : (t > 128 ? 128 : t);
 }
-// threads per block of the packing kernel (6 x stride bytes of scratch each,
-// within the 48 KB default; 16 threads for the 511-node templates)
-inline int pack_kernel_threads(int stride) {
-  int t = 49152 / (int)gg::pack_scratch_bytes(stride);
-  t = t >= 32 ? (t & ~31) : (t & ~7);
-  return t > 128 ? 128 : (t < 8 ? 8 : t);
-}
 // stack slots of a template of height h: Sethi-Ullman order with fused
 // terminals needs at most h - 1 (the packer checks the bound)
 inline int slots_of(int h) { return h > 2 ? h - 1 : 1; }
@@ -344,9 +337,8 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.mask = mask;
   pp.allow_pow = pl.pow ? 1 : 0;
   pp.fold = pl.fold ? 1 : 0;
-  const int pt = pack_kernel_threads(pl.stride);
-  return launch(gg::pack_ptr(), dim3((n + pt - 1) / pt), dim3(pt),
-                (size_t)pt * gg::pack_scratch_bytes(pl.stride), st,
+  return launch(gg::pack_ptr(), dim3((n + gg::PACK_WARPS - 1) / gg::PACK_WARPS),
+                dim3(32 * gg::PACK_WARPS), gg::PACK_WARPS * gg::pack_warp_bytes(pl.stride), st,
                 &pp);
 }
 
@@ -418,7 +410,8 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
-  GG_TRY(launch(gg::fin_ptr(), dim3((n + 3) / 4), dim3(128), 0, st, &q));
+  GG_TRY(launch(gg::fin_ptr(), dim3((n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
+                dim3(32 * gg::FIN_WARPS), 0, st, &q));
   return GGEVAL_OK;
 }
 
@@ -1046,6 +1039,39 @@ ggeval_status ggeval_batch_stats(const ggeval_batch* b, int32_t n_features, int6
   return GGEVAL_OK;
 }
 
+ggeval_status ggeval_pack_device(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                                 uint32_t* words, float* consts, int32_t* len, int32_t cap,
+                                 void* stream) {
+  GG_TRY(check_batch(ds, b));
+  if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "pack_device needs a device batch");
+  if (b->n == 0) return GGEVAL_OK;
+  if (!words || !consts || !len || cap < 1) return fail(GGEVAL_ERR_ARG, "NULL output or cap < 1");
+  DeviceGuard guard(ds->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan pl;
+  GG_TRY(make_plan(ds, b->n, b->max_height, default_cfg(ds, b->n, b->max_height, flags), &pl,
+                   has_pow(flags)));
+  pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
+  GG_TRY(ensure_ws(ds, b->n, pl, false));
+  DevBatch db{b->op, b->cval, b->height};
+  GG_TRY(enqueue_pack(ds, db, b->n, b->max_height, b->layout, pl, false, st));
+  std::vector<uint2> prog((size_t)b->n * pl.lstride);
+  std::vector<int> ln(b->n);
+  GG_CU(cudaMemcpyAsync(prog.data(), ds->prog, prog.size() * sizeof(uint2), cudaMemcpyDeviceToHost,
+                        st));
+  GG_CU(cudaMemcpyAsync(ln.data(), ds->len, ln.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  GG_CU(cudaStreamSynchronize(st));
+  for (int t = 0; t < b->n; ++t) {
+    len[t] = ln[t];
+    for (int k = 0; k < ln[t] && k < cap; ++k) {
+      const uint2 w = prog[(size_t)t * pl.lstride + k];
+      words[(size_t)t * cap + k] = w.x;
+      std::memcpy(&consts[(size_t)t * cap + k], &w.y, 4);
+    }
+  }
+  return GGEVAL_OK;
+}
+
 ggeval_status ggeval_pack_host(const ggeval_batch* b, int32_t index, int32_t n_features,
                                uint32_t* words, float* consts, int32_t* tpos, int32_t cap,
                                int32_t* len) {
@@ -1168,9 +1194,8 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   pp.status = ds->status;
   pp.mask = nullptr;
   pp.fold = 1;
-  const int pt = pack_kernel_threads(pl.stride);
-  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + pt - 1) / pt), dim3(pt),
-                (size_t)pt * gg::pack_scratch_bytes(pl.stride),
+  GG_TRY(launch(gg::pack_ptr(), dim3((b->n + gg::PACK_WARPS - 1) / gg::PACK_WARPS),
+                dim3(32 * gg::PACK_WARPS), gg::PACK_WARPS * gg::pack_warp_bytes(pl.stride),
                 st, &pp));
   GG_CU(cudaMemsetAsync(counter, 0, sizeof(int), st));
   gg::FwdParams fp = fwd_params(ds, b->n, pl);
@@ -1183,6 +1208,7 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   q.part = part;
   q.len = len;
   q.ab = nullptr;
-  GG_TRY(launch(gg::fin_ptr(), dim3((b->n + 3) / 4), dim3(128), 0, st, &q));
+  GG_TRY(launch(gg::fin_ptr(), dim3((b->n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
+                dim3(32 * gg::FIN_WARPS), 0, st, &q));
   return GGEVAL_OK;
 }

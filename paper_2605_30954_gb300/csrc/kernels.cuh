@@ -23,11 +23,15 @@ struct PackParams {
   int fold;              // fold constant subtrees (ignored when aux is set)
 };
 
-// shared scratch of the packing kernel per thread: folded values (floats),
-// depth flags and slot needs (bytes) for every template node
-inline size_t pack_scratch_bytes(int stride) { return (size_t)stride * 6; }
+// pack_kernel (pack.cu): one warp per trial, PACK_WARPS warps per block.
+// Shared scratch per warp and template node: folded value, constant (floats),
+// subtree size, first instruction, template position (int16), class, kind,
+// flags, stack need (bytes).
+constexpr int PACK_WARPS = 4;
+__host__ __device__ inline size_t pack_warp_bytes(int stride) {
+  return ((size_t)stride * 18 + 15) & ~(size_t)15;
+}
 
-// pack_kernel (defined in misc.cu): one thread per trial.
 
 // ------------------------------------------------------- batched forward
 // Work item = (group of `group` trials, row tile of `tile_rows` rows).  A
@@ -325,6 +329,7 @@ struct FinParams {
 };
 
 constexpr double VAR_TOL = 1e-12;
+constexpr int FIN_WARPS = 16;  // trials per finaliser block
 
 // fin_kernel is defined in misc.cu.
 

@@ -1,87 +1,18 @@
-// Non-template kernels: packer, fitness finaliser, gradient output, Adam,
-// dataset transpose.
+// Non-template kernels: fitness finaliser, gradient output, Adam, dataset
+// transpose.
 #include "misc.cuh"
 
 namespace gg {
 
-// The interpreter's own operator functions for constant folding: unop_rows
-// with one row picks the same code path as R equal rows do, and binop is
-// the interpreter's binary operator, so a folded constant is bit-identical
-// to the value the interpreter would compute on every row.
-struct DevFold {
-  static constexpr bool on = true;
-  __device__ float un(int u, float a) const {
-    float v[1] = {a};
-    switch (u) {
-      case U_SIN: unop_rows<U_SIN, 1>(v); break;
-      case U_COS: unop_rows<U_COS, 1>(v); break;
-      case U_EXP: unop_rows<U_EXP, 1>(v); break;
-      case U_LOG_ABS: unop_rows<U_LOG_ABS, 1>(v); break;
-      case U_SQRT_ABS: unop_rows<U_SQRT_ABS, 1>(v); break;
-      case U_SQUARE: unop_rows<U_SQUARE, 1>(v); break;
-      case U_LOG: unop_rows<U_LOG, 1>(v); break;
-      default: unop_rows<U_SQRT, 1>(v); break;
-    }
-    return v[0];
-  }
-  __device__ float bin(int k, float a, float b) const {
-    switch (k) {
-      case K_ADD: return binop<K_ADD>(a, b);
-      case K_SUB: return binop<K_SUB>(a, b);
-      case K_MUL: return binop<K_MUL>(a, b);
-      case K_AQ: return binop<K_AQ>(a, b);
-      case K_DIV: return binop<K_DIV>(a, b);
-      default: return binop<K_POW>(a, b);
-    }
-  }
-};
-
-// One thread per trial: linearise its template (Section 3.2, Fig. 1),
-// folding constant subtrees unless p.fold is 0 or side information for the
-// adjoint is wanted.  Shared scratch per block: [threads][stride] floats of
-// folded values, then [threads][stride] bytes twice (depth flags, need).
-__global__ void pack_kernel(const PackParams p) {
-  extern __shared__ __align__(16) unsigned char pk_smem[];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.n) return;
-  float* fv = reinterpret_cast<float*>(pk_smem) + (size_t)threadIdx.x * p.stride;
-  uint8_t* depth1 = pk_smem + (size_t)blockDim.x * p.stride * 4 + (size_t)threadIdx.x * 2 * p.stride;
-  uint8_t* need = depth1 + p.stride;
-  if (p.mask && !p.mask[t]) {  // not evaluated in this call
-    p.len[t] = 0;
-    return;
-  }
-  const int h = p.height ? (int)p.height[t] : p.h_max;
-  uint2* prog = p.prog + (size_t)t * p.lstride;
-  int L = -1;
-  if (h >= 0 && h <= p.h_max) {
-    const PackResult r = pack_tree(p.op + (size_t)t * p.stride, p.cval + (size_t)t * p.stride, h,
-                                   p.layout, p.n_features, p.max_slots,
-                                   reinterpret_cast<uint32_t*>(prog),
-                                   reinterpret_cast<float*>(prog) + 1, 2,
-                                   p.aux ? p.aux + (size_t)t * p.lstride : nullptr,
-                                   p.lstride - 1, depth1, need, p.allow_pow != 0, DevFold(),
-                                   p.fold && !p.aux ? fv : nullptr);
-    if (r.status == 0) L = r.len;
-  }
-  p.len[t] = L;
-  if (L < 0) atomicOr(p.status, ST_TEMPLATE);
-}
-
-
 __global__ void fin_kernel(const FinParams p) {
+  __shared__ double red[FIN_WARPS][5];  // cst, S_d, S_dd, S_dy, max|f|
+  __shared__ int lens[FIN_WARPS];
   const int lane = threadIdx.x & 31;
-  const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (t >= p.P || p.len[t] == 0) return;  // 0: masked out, outputs untouched
-  const double nan = __longlong_as_double(0x7ff8000000000000LL);
-  const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  double smse, a, b, mse, ac = 0.0, bo = 0.0;
-  const bool valid = p.len[t] > 0;
-  if (!valid) {
-    smse = a = b = mse = nan;
-  } else {
-    // lanes take tiles lane, lane + 32, ...; the shuffle tree below fixes
-    // the summation order, so the result is deterministic
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int t = blockIdx.x * nw + warp;
+  const int len = t < p.P ? p.len[t] : 0;  // 0: masked out, outputs untouched
+  if (len > 0) {
     const float* q = p.part + (size_t)t * p.n_tiles * NPART;
     const double cst = q[0];
     double sd = 0.0, sdd = 0.0, sdy = 0.0, fm = 0.0;
@@ -107,6 +38,29 @@ __global__ void fin_kernel(const FinParams p) {
       sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
       fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
     }
+    if (lane == 0) {
+      red[warp][0] = cst;
+      red[warp][1] = sd;
+      red[warp][2] = sdd;
+      red[warp][3] = sdy;
+      red[warp][4] = fm;
+    }
+  }
+  if (lane == 0) lens[warp] = len;
+  __syncthreads();
+  if (warp != 0 || lane >= nw) return;
+  const int tt = blockIdx.x * nw + lane;
+  const int L = lens[lane];
+  if (tt >= p.P || L == 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double smse, a, b, mse, ac = 0.0, bo = 0.0;
+  const bool valid = L > 0;
+  if (!valid) {
+    smse = a = b = mse = nan;
+  } else {
+    const double cst = red[lane][0], sd = red[lane][1], sdd = red[lane][2], sdy = red[lane][3];
+    const double fm = red[lane][4];
     const double N = (double)p.N;
     const bool finite = isfinite(sd) && isfinite(sdd) && isfinite(sdy) && isfinite(cst) &&
                         fm <= (double)OUT_BIG;
@@ -127,16 +81,15 @@ __global__ void fin_kernel(const FinParams p) {
       bo = b;
     }
   }
-  if (lane != 0) return;
-  if (p.smse) p.smse[t] = (float)smse;
-  if (p.a) p.a[t] = (float)a;
-  if (p.b) p.b[t] = (float)b;
-  if (p.mse) p.mse[t] = (float)mse;
+  if (p.smse) p.smse[tt] = (float)smse;
+  if (p.a) p.a[tt] = (float)a;
+  if (p.b) p.b[tt] = (float)b;
+  if (p.mse) p.mse[tt] = (float)mse;
   if (p.ab) {
-    p.ab[4 * t] = ac;
-    p.ab[4 * t + 1] = bo;
-    p.ab[4 * t + 2] = (valid && isfinite(smse)) ? 1.0 : 0.0;
-    p.ab[4 * t + 3] = 0.0;
+    p.ab[4 * tt] = ac;
+    p.ab[4 * tt + 1] = bo;
+    p.ab[4 * tt + 2] = (valid && isfinite(smse)) ? 1.0 : 0.0;
+    p.ab[4 * tt + 3] = 0.0;
   }
 }
 
@@ -176,7 +129,6 @@ __global__ void transpose_kernel(const TransposeParams p) {
   }
 }
 
-const void* pack_ptr() { return reinterpret_cast<const void*>(&pack_kernel); }
 const void* fin_ptr() { return reinterpret_cast<const void*>(&fin_kernel); }
 const void* gradout_ptr() { return reinterpret_cast<const void*>(&gradout_kernel); }
 const void* adam_ptr() { return reinterpret_cast<const void*>(&adam_kernel); }

@@ -27,6 +27,7 @@ MAX_HEIGHT = 8
 SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggeval_eval_rows",
            "ggeval_eval_plain", "ggeval_grad_batch", "ggeval_adam_step", "ggeval_autotune",
            "ggeval_sync", "ggeval_last_error", "ggeval_batch_stats", "ggeval_pack_host",
+           "ggeval_pack_device",
            "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc",
            "ggeval_eval_batch_masked", "ggeval_gom_donate", "ggeval_gom_changed",
            "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info")
@@ -66,6 +67,7 @@ def load_library(path: str = LIB_PATH):
         "ggeval_last_error": [],
         "ggeval_batch_stats": [bp, i32, vp],
         "ggeval_pack_host": [bp, i32, i32, vp, vp, vp, i32, vp],
+        "ggeval_pack_device": [vp, bp, u32, vp, vp, vp, i32, vp],
         "ggeval_version": [],
         "ggeval_profile_read": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
         "ggeval_eval_batch_noalloc": [vp, bp, vp, vp, vp, vp, vp],
@@ -224,6 +226,18 @@ class Dataset:
         _check(lib().ggeval_eval_batch_masked(self._h, ctypes.byref(b), _ptr(mask), flags,
                                               *map(_ptr, outs), _stream_handle(stream)))
         return outs
+
+    def pack_device(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None):
+        """The device packer's programs: (words uint32 [n, cap], consts
+        float32 [n, cap], len int32 [n]), cap = the template stride."""
+        b = make_batch(op, cval, heights, layout=layout)
+        cap = op.shape[1]
+        words = torch.zeros((b.n, cap), dtype=torch.int32)
+        consts = torch.zeros((b.n, cap), dtype=torch.float32)
+        ln = torch.zeros(b.n, dtype=torch.int32)
+        _check(lib().ggeval_pack_device(self._h, ctypes.byref(b), flags, _ptr(words),
+                                        _ptr(consts), _ptr(ln), cap, _stream_handle(stream)))
+        return words.numpy().view("uint32"), consts.numpy(), ln.numpy()
 
     def autotune(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None):
         b = make_batch(op, cval, heights, layout=layout)
