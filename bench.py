@@ -19,7 +19,8 @@ flushed (a 512 MB write) between timed steps.  Reported:
   roofline   the batched forward kernel against the FP32 issue peak
              (152 SMs x 128 lanes x the SM clock sampled during the run),
              counting the operations of the folded programs
-  cpu_baseline  the FP64 oracle on the host cores, on a sample of trials
+  cpu_baseline  the FP64 oracle on one host core, on a sample of trials
+  cpu_baseline_all_cores  the same oracle over every host core (process pool)
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -56,7 +57,7 @@ ACC_FP32 = 4
 # DRAM bytes (read + write) of one batched-forward launch from the ncu
 # capture summarised in profiles/fwd_kernel_fos-step-4096xh4-100000x8.md;
 # None for a workload without a capture of the current kernel
-NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4275200 + 9472}
+NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4244992 + 6656}
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}
 # the same classes after constant folding (the nodes evaluated on every row)
@@ -183,6 +184,50 @@ def node_counts(gg, torch, w):
     fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
     sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
     return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 13].sum())
+
+
+_POOL_W = None
+
+
+def _pool_init(w):
+    global _POOL_W
+    _POOL_W = w
+
+
+def _oracle_trials(idx):
+    """Worker of the all-cores oracle timing: fitness of the given trials."""
+    import oracle as O
+    w = _POOL_W
+    nodes = 0
+    for p in idx:
+        t = O.Template(w["op"][p], w["cval"][p], int(w["heights"][p]), w["layout"], w["F"])
+        try:
+            O.fitness(O.eval_tree(t, w["X"]), w["y"])
+            nodes += int(O.active_mask(t).sum())
+        except O.InvalidTemplate:
+            pass
+    return nodes
+
+
+def cpu_baseline_all_cores(w, per_trial_s, seconds):
+    """The same oracle on every host core: a spawn-started process pool (safe
+    after GPU work in this process), trials split evenly, sized so the timed
+    part takes about `seconds`."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = int(min(w["P"], max(cores, seconds * cores / max(per_trial_s, 1e-9))))
+    idx = np.arange(n)
+    chunks = [c.tolist() for c in np.array_split(idx, cores) if len(c)]
+    ww = {k: w[k] for k in ("op", "cval", "heights", "layout", "F", "X", "y")}
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(ww,)) as pool:
+        pool.map(_oracle_trials, [[0]] * cores)  # start-up (imports) outside the timing
+        t0 = time.perf_counter()
+        nodes = sum(pool.map(_oracle_trials, chunks))
+        el = time.perf_counter() - t0
+    return {"value": nodes * w["N"] / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "trial_evals_per_s": n / el,
+            "sample": f"first {n} of {w['P']} trials at all {w['N']} rows split over {cores} "
+                      f"processes ({el:.1f} s, FP64 numpy)"}
 
 
 def cpu_baseline(w, seconds, torch):
@@ -532,7 +577,9 @@ def main():
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not a.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, a.cpu_seconds, torch)
+        line["cpu_baseline"] = cb = cpu_baseline(w, a.cpu_seconds, torch)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(
+            w, 1.0 / cb["trial_evals_per_s"], a.cpu_seconds)
     ds.close()
     if pg:
         pg.destroy_process_group()
