@@ -25,55 +25,103 @@
 
 namespace gg {
 
-__device__ __forceinline__ void dbin(int kind, float a, float b, float& da, float& db) {
+// d op(a, b) / da and / db for R rows: the switch on the (warp-uniform)
+// kind is taken once per instruction.
+template <int R>
+__device__ __forceinline__ void dbin_rows(int kind, const float (&a)[R], const float (&b)[R],
+                                          float (&da)[R], float (&db)[R]) {
   switch (kind) {
-    case K_ADD: da = 1.f; db = 1.f; break;
-    case K_SUB: da = 1.f; db = -1.f; break;
-    case K_MUL: da = b; db = a; break;
-    case K_AQ: {
-      const float q = rsqrtf(fmaf(b, b, 1.f));
-      da = q;
-      db = -a * b * q * q * q;
+    case K_ADD:
+#pragma unroll
+      for (int r = 0; r < R; ++r) da[r] = 1.f, db[r] = 1.f;
       break;
-    }
-    case K_POW: {  // d/da = b a^(b-1); d/db = a^b ln|a| (0 where a^b = 0)
-      const float out = powf(a, b);
-      da = b * powf(a, b - 1.f);
-      db = out == 0.f ? 0.f : out * logf(fabsf(a));
+    case K_SUB:
+#pragma unroll
+      for (int r = 0; r < R; ++r) da[r] = 1.f, db[r] = -1.f;
       break;
-    }
-    default: {  // K_DIV: d/da = 1/b, d/db = -(a/b)/b
-      da = 1.f / b;
-      db = -(a / b) / b;
+    case K_MUL:
+#pragma unroll
+      for (int r = 0; r < R; ++r) da[r] = b[r], db[r] = a[r];
       break;
-    }
+    case K_AQ:
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float q = rsqrtf(fmaf(b[r], b[r], 1.f));
+        da[r] = q;
+        db[r] = -a[r] * b[r] * q * q * q;
+      }
+      break;
+    case K_POW:  // d/da = b a^(b-1); d/db = a^b ln|a| (0 where a^b = 0)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float out = powf(a[r], b[r]);
+        da[r] = b[r] * powf(a[r], b[r] - 1.f);
+        db[r] = out == 0.f ? 0.f : out * logf(fabsf(a[r]));
+      }
+      break;
+    default:  // K_DIV: d/da = 1/b, d/db = -(a/b)/b
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        da[r] = 1.f / b[r];
+        db[r] = -(a[r] / b[r]) / b[r];
+      }
+      break;
   }
 }
 
-__device__ __forceinline__ float dun(int u, float x) {
+// x <- g * d u(x) / dx for R rows.
+template <int R>
+__device__ __forceinline__ void dun_rows(int u, const float (&g)[R], float (&x)[R]) {
   switch (u) {
-    case U_SIN: return cosf(x);
-    case U_COS: return -sinf(x);
-    case U_EXP: return expf(x);
+    case U_SIN:
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * cosf(x[r]);
+      break;
+    case U_COS:
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * -sinf(x[r]);
+      break;
+    case U_EXP:
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * expf(x[r]);
+      break;
     case U_LOG_ABS:
-    case U_LOG: return 1.f / x;
-    case U_SQRT_ABS: return x == 0.f ? 0.f : copysignf(0.5f / sqrtf(fabsf(x)), x);
-    case U_SQUARE: return 2.f * x;
-    default: return 0.5f / sqrtf(x);  // U_SQRT
+    case U_LOG:
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * (1.f / x[r]);
+      break;
+    case U_SQRT_ABS:
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        x[r] = g[r] * (x[r] == 0.f ? 0.f : copysignf(0.5f / sqrtf(fabsf(x[r])), x[r]));
+      break;
+    case U_SQUARE:
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * (2.f * x[r]);
+      break;
+    default:  // U_SQRT
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = g[r] * (0.5f / sqrtf(x[r]));
+      break;
   }
 }
 
-template <bool POW>
+// R rows per lane: each lane runs rows row0 .. row0 + R - 1 of a 32 R-row
+// group (feature-major X, so a lane's rows are one aligned R-wide load).
+// Values and adjoints live at V[instruction][lane][row]; rows past the
+// chunk's end are evaluated on in-bounds data and left out of every sum.
+template <int R, bool POW>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots);
+  constexpr int SLOT = 32 * R;
+  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots, R);
   uint2* wprog = reinterpret_cast<uint2*>(base);
   Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
   float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per instruction
-  float* V = reinterpret_cast<float*>(wg + p.lstride);      // [lstride][32]
-  float* stk = V + (size_t)p.lstride * 32 + lane;            // [slots][32], this lane
+  float* V = reinterpret_cast<float*>(wg + p.lstride) + lane * R;  // [lstride][32][R]
+  float* stk = V + (size_t)p.lstride * SLOT;                         // [slots][32][R]
 
   for (;;) {
     int item = 0;
@@ -101,16 +149,25 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
 
     const int r_beg = chunk * p.chunk_rows;
     const int r_end = min(p.N, r_beg + p.chunk_rows);
-    for (int rb = r_beg; rb < r_end; rb += 32) {
-      const int row = rb + lane;
-      const bool valid = row < r_end;
-      const int rr = valid ? row : r_end - 1;
-      float A[1] = {0.f};
-      run_program<1, true, false, POW>(wprog, L, p.X + rr, p.ldx, A, stk, V + lane);
-      const float f = A[0];
-      const float yc = p.X[(size_t)p.F * p.ldx + rr];
-      float w = p.mse_mode ? two_n * (f - ybar - yc) : two_n * bb * (a_c + bb * f - yc);
-      V[32 * (L - 1) + lane] = valid ? w : 0.f;  // the output's value becomes its adjoint
+    for (int rb = r_beg; rb < r_end; rb += SLOT) {
+      // this lane's first row, kept in bounds (and R-aligned) past the end
+      const int row0 = min(rb + lane * R, (r_end - 1) & ~(R - 1));
+      bool valid[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) valid[r] = rb + lane * R + r < r_end;
+      float A[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = 0.f;
+      run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
+      float yc[R];
+      load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
+      float w[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        w[r] = p.mse_mode ? two_n * (A[r] - ybar - yc[r]) : two_n * bb * (a_c + bb * A[r] - yc[r]);
+        w[r] = valid[r] ? w[r] : 0.f;
+      }
+      store_rows<R>(V + (size_t)SLOT * (L - 1), w);  // the output's value becomes its adjoint
       __syncwarp();
       for (int k = L - 1; k >= 0; --k) {
         const uint2 ins = wprog[k];
@@ -118,52 +175,73 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
         const uint32_t opc = ins.x & 0xffu;
         const int feat = (int)(ins.x >> 8);
         const float c = __uint_as_float(ins.y);
-        const float g = V[32 * k + lane];  // adjoint of instruction k
-        float ge = 0.f;                    // contribution to this instruction's ERC
+        float g[R];  // adjoint of instruction k
+        load_rows<R>(V + (size_t)SLOT * k, g);
+        float ge[R];  // contribution to this instruction's ERC
         bool has_erc = false;
         if (opc == I_LDF0 || opc == I_PSF) {
           // feature load: nothing to propagate
         } else if (opc == I_LDC0 || opc == I_PSC) {
-          ge = g;
+#pragma unroll
+          for (int r = 0; r < R; ++r) ge[r] = g[r];
           has_erc = true;
         } else if (opc >= I_UN && opc < I_UN + NUNARY) {
-          float* vx = &V[32 * ax.src_l + lane];
-          *vx = g * dun((int)(opc - I_UN), *vx);
+          float* vx = V + (size_t)SLOT * ax.src_l;
+          float x[R];
+          load_rows<R>(vx, x);
+          dun_rows<R>((int)(opc - I_UN), g, x);
+          store_rows<R>(vx, x);
         } else if ((opc >= I_BF && opc < I_BS) || (POW && opc >= I_PW && opc < I_PWS)) {
           const bool pw = POW && opc >= I_PW;
           const int grp = pw ? (int)(opc - I_PW) : (int)(opc - I_BF) / NKIND;  // 0 BF, 1 BC, 2 LF, 3 LC
           const int kind = pw ? K_POW : (int)(opc - I_BF) % NKIND;
-          float da, db;
+          float t[R], da[R], db[R];
+          if (grp == 0 || grp == 2) {
+            load_rows<R>(p.X + (size_t)feat * p.ldx + row0, t);
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[r] = c;
+          }
+          float* vs = V + (size_t)SLOT * (grp <= 1 ? ax.src_l : ax.src_r);
+          float v[R];
+          load_rows<R>(vs, v);
           if (grp <= 1) {
-            float* va = &V[32 * ax.src_l + lane];
-            const float b = grp == 0 ? p.X[(size_t)feat * p.ldx + rr] : c;
-            dbin(kind, *va, b, da, db);
-            *va = g * da;
-            if (grp == 1) {
-              ge = g * db;
-              has_erc = true;
+            dbin_rows<R>(kind, v, t, da, db);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              v[r] = g[r] * da[r];
+              ge[r] = g[r] * db[r];
             }
           } else {
-            float* vb = &V[32 * ax.src_r + lane];
-            const float a = grp == 2 ? p.X[(size_t)feat * p.ldx + rr] : c;
-            dbin(kind, a, *vb, da, db);
-            *vb = g * db;
-            if (grp == 3) {
-              ge = g * da;
-              has_erc = true;
+            dbin_rows<R>(kind, t, v, da, db);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              v[r] = g[r] * db[r];
+              ge[r] = g[r] * da[r];
             }
           }
+          store_rows<R>(vs, v);
+          has_erc = grp == 1 || grp == 3;
         } else if ((opc >= I_BS && opc < I_NOP) || (POW && opc >= I_PWS && opc < I_COUNT)) {
           const int kind = POW && opc >= I_PWS ? K_POW : (int)(opc - (opc < I_RS ? I_BS : I_RS));
-          float* va = &V[32 * ax.src_l + lane];
-          float* vb = &V[32 * ax.src_r + lane];
-          float da, db;
-          dbin(kind, *va, *vb, da, db);
-          *va = g * da;
-          *vb = g * db;
+          float* va = V + (size_t)SLOT * ax.src_l;
+          float* vb = V + (size_t)SLOT * ax.src_r;
+          float a[R], b[R], da[R], db[R];
+          load_rows<R>(va, a);
+          load_rows<R>(vb, b);
+          dbin_rows<R>(kind, a, b, da, db);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            a[r] = g[r] * da[r];
+            b[r] = g[r] * db[r];
+          }
+          store_rows<R>(va, a);
+          store_rows<R>(vb, b);
         }
         if (has_erc) {  // warp-uniform: the same instruction on every lane
-          float sm = valid ? ge : 0.f;
+          float sm = 0.f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) sm += valid[r] ? ge[r] : 0.f;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
           if (lane == 0) {
@@ -191,9 +269,15 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   }
 }
 
-const void* adj_ptr(bool pow) {
-  return pow ? reinterpret_cast<const void*>(&adjoint_kernel<true>)
-             : reinterpret_cast<const void*>(&adjoint_kernel<false>);
+const void* adj_ptr(int rows, bool pow) {
+  switch (rows) {
+    case 4: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<4, false>);
+    case 2: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<2, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<2, false>);
+    default: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<1, true>)
+                        : reinterpret_cast<const void*>(&adjoint_kernel<1, false>);
+  }
 }
 
 }  // namespace gg

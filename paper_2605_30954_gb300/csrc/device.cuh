@@ -99,9 +99,15 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
 // Load R consecutive rows of one feature row of the shared-memory tile.
 template <int R>
 __device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v)[R]) {
-  static_assert(R == 1 || R % 4 == 0, "R must be 1 or a multiple of 4");
+  static_assert(R == 1 || R == 2 || R % 4 == 0, "R must be 1, 2 or a multiple of 4");
   if constexpr (R == 1) {
     v[0] = *p;
+    return;
+  }
+  if constexpr (R == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
     return;
   }
 #pragma unroll
@@ -117,9 +123,13 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ p, float (&v
 // Store R consecutive rows of a lane (the counterpart of load_rows).
 template <int R>
 __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&v)[R]) {
-  static_assert(R == 1 || R % 4 == 0, "R must be 1 or a multiple of 4");
+  static_assert(R == 1 || R == 2 || R % 4 == 0, "R must be 1, 2 or a multiple of 4");
   if constexpr (R == 1) {
     *p = v[0];
+    return;
+  }
+  if constexpr (R == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
     return;
   }
 #pragma unroll
@@ -139,9 +149,9 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
 // lane.  The first instruction of every program loads A without a push.
 // With PRESCALED the feature field of each word already holds the
 // feature's offset in floats (feature x ts), as the batched kernel rewrites
-// it when it stages a program.  With TAPE (R == 1 only) the value of A
-// after instruction k is stored at tape[32 k] (the caller offsets `tape` by
-// its lane): the forward half of the adjoint.  POW adds the pow
+// it when it stages a program.  With TAPE the R values of A after
+// instruction k are stored at tape[32 R k] (the caller offsets `tape` by its
+// lane's R rows): the forward half of the adjoint.  POW adds the pow
 // instructions; without it the program must not contain them.
 template <int R, bool TAPE = false, bool PRESCALED = false, bool POW = false>
 __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
@@ -261,7 +271,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
 #undef GG_ROWS
 #undef GG_UN
 #undef GG_BIN
-    if constexpr (TAPE) tape[32 * k] = A[0];
+    if constexpr (TAPE) store_rows<R>(tape + 32 * R * k, A);
     ins = nxt;
   }
 }

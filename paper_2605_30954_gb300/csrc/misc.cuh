@@ -49,20 +49,18 @@ struct TransposeParams {
 };
 
 // per warp and program instruction: word, side information, (hi, lo)
-// gradient accumulator, and one value or adjoint for each of 32 rows; then
-// the warp's stack of `slots` x 32 floats
-constexpr int ADJ_WARP_BYTES_PER_INSTR = 8 + 8 + 8 + 32 * 4;
-
-__host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots) {
-  return (size_t)lstride * ADJ_WARP_BYTES_PER_INSTR + (size_t)slots * 32 * 4;
+// gradient accumulator, and one value or adjoint for each of 32 lanes x R
+// rows; then the warp's stack of `slots` x 32 x R floats
+__host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots, int rows) {
+  return (size_t)lstride * (8 + 8 + 8 + 32 * 4 * (size_t)rows) + (size_t)slots * 32 * 4 * rows;
 }
-inline size_t adj_smem_bytes(int warps, int lstride, int slots) {
-  return (size_t)warps * adj_warp_bytes(lstride, slots) + 16;
+inline size_t adj_smem_bytes(int warps, int lstride, int slots, int rows) {
+  return (size_t)warps * adj_warp_bytes(lstride, slots, rows) + 16;
 }
 
 const void* pack_ptr();
 const void* fin_ptr();
-const void* adj_ptr(bool pow);
+const void* adj_ptr(int rows, bool pow);
 const void* gradout_ptr();
 const void* adam_ptr();
 const void* transpose_ptr();
