@@ -1,5 +1,6 @@
-// Device-side building blocks shared by the kernels: the register-file
-// interpreter, error-free FP32 summation, and the mbarrier / bulk-copy PTX.
+// Device-side building blocks shared by the kernels: the operators, the
+// stack-machine interpreter (top of stack in registers, the rest in shared
+// memory), error-free FP32 summation, and the mbarrier / bulk-copy PTX.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
