@@ -10,7 +10,9 @@ flushed (a 512 MB write) between timed steps.  Reported:
   value      node-row evals/s (active nodes x rows x trials / s), graph form;
              the library folds each feature-free subtree into one constant
              (bit-identical outputs), so fewer nodes run per row than the
-             active count: config.nodes_evaluated_per_row_per_step
+             active count: config.nodes_evaluated_per_row_per_step; a trial
+             stops once one of its tiles is non-finite (+inf fitness):
+             config.trials_with_infinite_fitness
   e2e        the same through the C ABI with pinned HOST buffers: the H2D
              copy of the trial arrays and the D2H copy of the fitness inside
              every step
@@ -511,6 +513,9 @@ def main():
     value = agg["node_row_evals_per_s"]
     trial_rate = agg["trial_evals_per_s"]
     ds.sync(st)
+    # trials whose fitness is +inf: the batched form stops evaluating such a
+    # trial after its first non-finite tile (node-rows still count them all)
+    nonfinite = int((~torch.isfinite(outs[0])).sum().item())
 
     # ---- forward kernel alone: live CUDA events around it (roofline) ----
     def prof_step():
@@ -568,6 +573,7 @@ def main():
                    "features": w["F"], "template_height": w["h_max"],
                    "active_nodes_per_step": nodes,
                    "nodes_evaluated_per_row_per_step": nodes_eval,
+                   "trials_with_infinite_fitness": nonfinite,
                    "flush_l2": "512 MB write between steps",
                    "form": "persistent batched kernel, CUDA graph replay, autotuned tiles",
                    "parallelism": f"replicas x{world} (independent FOS steps)"},

@@ -394,8 +394,10 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
                            const uint8_t* mask = nullptr) {
   const int n = b->n;
   GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st, mask));
-  GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int), st));
+  // counters[0]: the work counter; counters[8 + t]: trial t found non-finite
+  GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int) * ((size_t)n + 8), st));
   gg::FwdParams fp = fwd_params(ds, n, pl);
+  fp.dead = ds->counters + 8;
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if (profile && ds->prof_used < PROF_MAX) {
     if (ds->prof_used == ds->prof_ev.size()) {
@@ -410,6 +412,7 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
+  q.dead = fp.dead;
   GG_TRY(launch(gg::fin_ptr(), dim3((n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
                 dim3(32 * gg::FIN_WARPS), 0, st, &q));
   return GGEVAL_OK;

@@ -59,6 +59,8 @@ struct FwdParams {
   int* counter;        // work-item counter, zero at launch
   unsigned* status;
   float* rows_out;     // [P][N] per-row values (ROWS variant only)
+  int* dead;           // [P] zero at launch, or null: 1 once a tile of the trial
+                       // is non-finite or exceeds 2^50 (its fitness is +inf)
 };
 
 // partial record of one (trial, tile): the shift c, (hi, lo) of S_d, S_dd and
@@ -231,13 +233,17 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
       if (t >= p.group || trial >= p.P) break;
       const int L = p.len[trial];
       if (L <= 0) continue;
-      // stage the program with each feature field scaled to its tile offset
+      // stage the program with each feature field scaled to its tile offset;
+      // a trial another tile has already found non-finite is skipped (its
+      // fitness is +inf whatever the other tiles hold)
+      const int dead = p.dead && lane == 0 ? p.dead[trial] : 0;
       const uint2* src = p.prog + (size_t)trial * p.lstride;
       for (int k = lane; k <= L; k += 32) {
         uint2 w = src[k];
         w.x = (w.x & 0xffu) | (((w.x >> 8) * (uint32_t)p.tile_rows) << 8);
         wprog[k] = w;
       }
+      if (__shfl_sync(0xffffffffu, dead, 0)) continue;
       __syncwarp();
 
       float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
@@ -288,6 +294,9 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
         float4* q = reinterpret_cast<float4*>(p.part + ((size_t)trial * p.n_tiles + tile) * NPART);
         q[0] = make_float4(cs, s1h, s1l, s2h);
         q[1] = make_float4(s2l, s3h, s3l, fm);
+        // the finaliser's test, per tile: this trial's fitness is +inf
+        if (p.dead && !(fm <= OUT_BIG && isfinite(s1h + s2h + s3h) && isfinite(cs)))
+          p.dead[trial] = 1;
       }
       __syncwarp();
     }
@@ -326,6 +335,8 @@ struct FinParams {
   float* b;
   float* mse;
   double* ab;          // [P][4]: a* - ybar, b*, finite flag, 0 (adjoint), nullable
+  const int* dead;     // [P] or null: 1 for a trial the forward kernel found
+                       // non-finite (some of its tile records were skipped)
 };
 
 constexpr double VAR_TOL = 1e-12;

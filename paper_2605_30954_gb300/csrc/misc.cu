@@ -12,7 +12,14 @@ __global__ void fin_kernel(const FinParams p) {
   const int nw = blockDim.x >> 5;
   const int t = blockIdx.x * nw + warp;
   const int len = t < p.P ? p.len[t] : 0;  // 0: masked out, outputs untouched
-  if (len > 0) {
+  if (len > 0 && p.dead && p.dead[t]) {
+    // found non-finite by the forward kernel, which skipped its later tiles:
+    // +inf fitness without the (incomplete) tile records
+    if (lane == 0) {
+      red[warp][0] = red[warp][1] = red[warp][2] = red[warp][3] = 0.0;
+      red[warp][4] = __longlong_as_double(0x7ff0000000000000LL);
+    }
+  } else if (len > 0) {
     const float* q = p.part + (size_t)t * p.n_tiles * NPART;
     const double cst = q[0];
     double sd = 0.0, sdd = 0.0, sdy = 0.0, fm = 0.0;

@@ -296,6 +296,30 @@ def test_constant_folding_is_bit_identical(gg, cfg):
     ds.close()
 
 
+@pytest.mark.parametrize("cfg", ["t2", "l_squ"])
+def test_early_exit_matches_plain_form(gg, cfg):
+    """The batched form stops evaluating a trial once a tile of it is
+    non-finite (its fitness is +inf); the plain form evaluates every row.
+    Both give the same +inf trials and the same finite fitness."""
+    w = PA.build(cfg, 40000, 128)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op, cv = dev(w["op"]), dev(w["cval"])
+    hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
+    pf = gg.F_POW if w.get("uses_pow") else 0
+    bat = [t.cpu().numpy() for t in ds.eval_batch(op, cv, hs, flags=pf)]
+    pla = [t.cpu().numpy() for t in ds.eval_plain(op, cv, hs, flags=pf)]
+    ds.sync()
+    ds.close()
+    inf_b, inf_p = np.isinf(bat[0]), np.isinf(pla[0])
+    np.testing.assert_array_equal(inf_b, inf_p)
+    assert 10 <= inf_b.sum() <= 118  # the workload has both kinds
+    np.testing.assert_array_equal(bat[1][inf_b], 0.0)
+    np.testing.assert_array_equal(bat[2][inf_b], 0.0)
+    assert np.all(np.isinf(bat[3][inf_b]))
+    for x, z in zip(bat, pla):
+        np.testing.assert_allclose(x[~inf_b], z[~inf_b], rtol=2e-5, atol=1e-30)
+
+
 def test_bad_arguments_rejected(gg):
     X = torch.zeros((10, 2))
     y = torch.arange(10, dtype=torch.float32)
