@@ -14,7 +14,8 @@ __all__ = [
     "ADD", "SUB", "MUL", "AQ", "SIN", "COS", "EXP", "LOG_ABS", "SQRT_ABS", "DIV",
     "SQUARE", "LOG", "SQRT", "POW", "ERC", "FEAT0", "PAD", "BINARY", "UNARY", "BIG",
     "VAR_TOL", "InvalidTemplate", "Template", "active_mask", "rpn", "paper_encoding",
-    "eval_tree", "eval_tree_f32", "eval_tree_perturbed", "condition_bound", "fitness", "grad",
+    "eval_tree", "eval_tree_f32", "eval_tree_perturbed", "condition_bound", "pow_ambiguous_rows",
+    "fitness", "grad",
     "fd_grad", "eval_batch",
 ]
 
@@ -279,6 +280,41 @@ def condition_bound(t: Template, X: np.ndarray, rel: float) -> np.ndarray:
         back(0, 0, np.ones(n))
         bound = np.where(np.isfinite(f), rel * bound, np.inf)
         return np.where(np.isnan(bound), np.inf, bound)
+
+
+def pow_ambiguous_rows(t: Template, X: np.ndarray, ulps: float = 64.0) -> np.ndarray:
+    """Rows whose value FP32 rounding may flip between a number and NaN.
+
+    A negative base raised to a non-integer exponent is NaN, to an integer
+    exponent a number, so pow is discontinuous in its exponent at a negative
+    base.  READING: a row where an active pow node has a negative base and an
+    exponent within `ulps` FP32 units in the last place (of max(1, |b|)) of
+    an integer has a value that FP32 evaluation does not determine (rounding
+    the exponent decides); tests exclude such rows, and the finiteness of
+    their trials, from parity and count them.  Exponents of 2^18 and beyond
+    are always within the window (FP32 spacing there is at least 1/64)."""
+    X = np.asarray(X)
+    vals = {}
+    _eval(t, X, np.float64, store=vals)
+    amb = np.zeros(X.shape[0], dtype=bool)
+
+    def visit(pos, depth):
+        nonlocal amb
+        o = int(t.op[pos])
+        if o >= ERC:
+            return
+        l, r = t.children(pos, depth)
+        visit(l, depth + 1)
+        if o in BINARY:
+            visit(r, depth + 1)
+        if o == POW:
+            a, b = vals[l], vals[r]
+            with np.errstate(all="ignore"):
+                near = np.abs(b - np.rint(b)) <= ulps * 2.0 ** -24 * np.maximum(1.0, np.abs(b))
+            amb = amb | ((a < 0) & near)
+
+    visit(0, 0)
+    return amb
 
 
 def _overflowed(f: np.ndarray) -> bool:

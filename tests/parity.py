@@ -10,9 +10,11 @@ Tolerances (from the accuracy targets of this evaluator):
 A row is ill-conditioned in FP32, and excluded, when its FP32-emulated
 oracle value or the first-order bound on the effect of relative errors of
 4 FP32 units in the last place at every function node
-(oracle.condition_bound) exceeds a quarter of its tolerance.  A trial is
-excluded when the same bound, carried to its smse (or mse), exceeds a
-quarter of that tolerance, or when its FP64 and FP32-emulated fitness
+(oracle.condition_bound) exceeds half of its tolerance, or when FP32
+rounding may turn it NaN (oracle.pow_ambiguous_rows: a negative base to an
+exponent next to an integer; its trial is excluded too).  A trial is
+excluded when the same bound, carried to its smse (or mse), exceeds half
+of that tolerance, or when its FP64 and FP32-emulated fitness
 disagree on being infinite (ambiguous).  Both counts are reported.
 """
 import math
@@ -80,10 +82,11 @@ def check_rows(g, f64, f32, tally, tag="", cond=None):
         tol = ROW_TOL * (np.abs(f64) + rms)
         err32 = np.abs(f32.astype(np.float64) - f64)
         c64, c32, cg = value_class(f64), value_class(f32), value_class(g)
-        special = (c64 != 0) & (c64 == c32)
+        amb = np.isnan(cond) if cond is not None else np.zeros(f64.shape, dtype=bool)
+        special = (c64 != 0) & (c64 == c32) & ~amb
         ill = ~special & (~fin | (c32 != 0) | (err32 > COND_MARGIN * tol))
         if cond is not None:
-            ill |= fin & ~(cond <= COND_MARGIN * tol)
+            ill |= amb | (fin & ~(cond <= COND_MARGIN * tol))
         err = np.where(special, 0.0, np.abs(g.astype(np.float64) - f64))
         bad = ~ill & np.where(special, cg != c64, ~(err <= tol))
     tally.checked += int((~ill).sum())
@@ -116,6 +119,9 @@ def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", bounds
     from fit_bounds, used with fit32 to flag ill-conditioned trials."""
     inf64 = not fit64["finite"]
     inf32 = not fit32["finite"]
+    if bounds is not None and np.isnan(bounds[0]):  # a row FP32 rounding may turn NaN
+        tally.excluded += 1
+        return
     if inf64 != inf32 or (bounds is not None and not inf64 and not np.isfinite(bounds[0])):
         tally.excluded += 1
         return
@@ -133,7 +139,8 @@ def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", bounds
         return
     tally.checked += 1
     err = abs(g_smse - r)
-    tally.worst = max(tally.worst, err / tol)
+    # a zero tolerance (one row, or a constant target) asks for the exact value
+    tally.worst = max(tally.worst, err / tol if tol > 0 else (0.0 if err == 0 else math.inf))
     if not err <= tol:
         tally.failed += 1
         tally.msgs.append(f"{tag}: smse gpu {g_smse!r} oracle {r!r} tol {tol:.3g}")
@@ -162,6 +169,11 @@ def oracle_trial(w, p, X=None, y=None):
     fit64 = O.fitness(f64, y)
     cond = O.condition_bound(t, X, COND_REL)
     bounds = fit_bounds(f64, y, fit64, cond) if fit64["finite"] else None
+    if np.any(t.op[O.active_mask(t)] == O.POW):
+        amb = O.pow_ambiguous_rows(t, X)
+        if amb.any():  # NaN marks rows (and the trial) whose finiteness FP32 decides
+            cond = np.where(amb, np.nan, cond)
+            bounds = (math.nan, math.nan)
     return t, f64, f32, fit64, O.fitness(f32.astype(np.float64), y), cond, bounds
 
 

@@ -1,0 +1,91 @@
+"""Randomised GPU parity: seeded random configurations that mix what the
+batched path has to handle together (row counts across tile boundaries and
+ragged tails, 1 to 12 features, heights 0 to 6 mixed within a batch, both
+layouts, every operator including pow, masks, folding on and off, exact and
+pairwise sums), each trial's fitness and per-row values compared with the
+FP64 oracle under the stated tolerances."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+import parity as PA
+
+pytestmark = pytest.mark.gpu
+
+ALL_FUNCS = synth.BINARY + synth.UNARY
+
+
+@pytest.fixture(scope="module")
+def gg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_30954_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def random_case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    N = int(rng.choice([1, 7, 130, 1023, 1025, 2049, 5003]))
+    F = int(rng.integers(1, 13))
+    h_max = int(rng.integers(0, 7))
+    P = int(rng.integers(1, 97))
+    funcs = tuple(rng.choice(ALL_FUNCS, size=int(rng.integers(2, len(ALL_FUNCS) + 1)),
+                             replace=False).tolist())
+    lo = float(rng.choice([-3.0, -1.0, 0.25]))
+    X = rng.uniform(lo, lo + float(rng.uniform(0.5, 4.0)), (N, F)).astype(np.float32)
+    y = (np.sin(X[:, 0]) + 0.3 * rng.standard_normal(N)).astype(np.float32)
+    hs = rng.integers(0, h_max + 1, P)
+    op, cv, hs = synth.random_templates(rng, P, hs, h_max, funcs, F,
+                                        rng.uniform(0.3, 1.0, P))
+    layout = str(rng.choice(["heap", "prefix"]))
+    if layout == "prefix":
+        op, cv = synth.to_prefix(op, cv, hs.astype(np.int64))
+    mask = (rng.random(P) < 0.7).astype(np.uint8) if rng.random() < 0.5 else None
+    flags_extra = int(rng.choice([0, 1, 2, 3]))  # bit 0: exact sums, bit 1: no folding
+    return dict(X=X, y=y, op=op, cval=cv, heights=hs.astype(np.int8), layout=layout, F=F,
+                P=P, N=N, mask=mask, flags_extra=flags_extra, funcs=funcs)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_configurations(gg, seed):
+    w = random_case(seed)
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op = torch.from_numpy(w["op"]).cuda()
+    cv = torch.from_numpy(w["cval"]).cuda()
+    hs = torch.from_numpy(w["heights"]).cuda()
+    lay = 0 if w["layout"] == "heap" else 1
+    flags = gg.F_POW if synth.POW in w["funcs"] else 0
+    if w["flags_extra"] & 1:
+        flags |= gg.F_EXACT
+    if w["flags_extra"] & 2:
+        flags |= gg.F_NO_FOLD
+    P = w["P"]
+    sentinel = -7.0
+    outs = [torch.full((P,), sentinel, device="cuda") for _ in range(4)]
+    if w["mask"] is None:
+        ds.eval_batch(op, cv, hs, layout=lay, flags=flags, out=outs)
+        evaluated = np.ones(P, dtype=bool)
+    else:
+        ds.eval_batch_masked(op, cv, torch.from_numpy(w["mask"]).cuda(), hs, layout=lay,
+                             flags=flags, out=outs)
+        evaluated = w["mask"].astype(bool)
+    rows = ds.eval_rows(op, cv, hs, layout=lay).cpu().numpy()
+    ds.sync()
+    ds.close()
+    smse, a, b, mse = (t.cpu().numpy() for t in outs)
+    # masked-out trials keep the caller's values
+    assert np.all(smse[~evaluated] == sentinel) and np.all(mse[~evaluated] == sentinel)
+    tr, tf = PA.Tally(), PA.Tally()
+    y64 = w["y"].astype(np.float64)
+    var_y, mean_y2 = float(np.var(y64)), float(np.mean(y64 ** 2))
+    for p in np.flatnonzero(evaluated):
+        t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
+        PA.check_rows(rows[p], f64, f32, tr, tag=f"trial {p}", cond=cond)
+        PA.check_fit(float(smse[p]), float(mse[p]), fit64, fit32, var_y, mean_y2, tf,
+                     tag=f"trial {p}", bounds=bounds)
+    assert tr.failed == 0, repr(tr)
+    assert tf.failed == 0, repr(tf)
+    assert tf.checked >= max(1, int(0.5 * evaluated.sum())), repr(tf)

@@ -126,6 +126,20 @@ def test_pow_exponent_derivative_at_negative_base():
     np.testing.assert_allclose(db, want, rtol=1e-14)
 
 
+def test_pow_ambiguous_rows():
+    """Rows where pow has a negative base and an exponent next to an integer
+    (FP32 rounding decides between a number and NaN) are flagged; a positive
+    base, or an exponent far from an integer, is not."""
+    t = T(["pow", "x0", "x1"], 1)
+    X = np.array([[-2.0, 3.0], [-2.0, 0.5], [2.0, 3.0], [-2.0, 3.0000001], [-2.0, 1e6 + 0.5],
+                  [-2.0, 3.1]])
+    np.testing.assert_array_equal(O.pow_ambiguous_rows(t, X),
+                                  [True, False, False, True, True, False])
+    # nested: the flag follows the active pow node wherever it sits
+    t2 = T(["+", "x1", "pow", None, None, "x0", "x1"], 2)
+    np.testing.assert_array_equal(O.pow_ambiguous_rows(t2, X[:3]), [True, False, False])
+
+
 def test_height2_hand_value():
     # (x0 AQ x1) - (2 * x0) at x0 = 3, x1 = 4: 3/sqrt(17) - 6
     t = T(["-", "aq", "*", "x0", "x1", "2", "x0"], 2)
