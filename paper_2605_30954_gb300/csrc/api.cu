@@ -114,7 +114,7 @@ struct GraphKey {
   uint32_t flags;
   const void* mask;
   const void* out[4];
-  const void* ws[7];  // workspace buffers the captured launches point at
+  const void* ws[8];  // workspace buffers the captured launches point at
   Cfg cfg;
   int kind;
 };
@@ -151,6 +151,8 @@ struct ggeval_dataset {
   size_t cap_gacc = 0;
   int* counters = nullptr;
   size_t cap_counters = 0;
+  int* idx = nullptr;  // masked evaluation: the compacted trial indices
+  size_t cap_idx = 0;
   unsigned* status = nullptr;
   // device staging of host-memory batches
   unsigned char* stage = nullptr;
@@ -302,6 +304,7 @@ ggeval_status ensure_ws(ggeval_dataset* ds, int n, const Plan& pl, bool grad) {
   GG_TRY(grow(ds->part, ds->cap_part, (size_t)n * pl.n_tiles * gg::NPART));
   GG_TRY(grow(ds->ab, ds->cap_ab, (size_t)n * 4 + 4));
   GG_TRY(grow(ds->counters, ds->cap_counters, (size_t)n + 8));
+  GG_TRY(grow(ds->idx, ds->cap_idx, (size_t)n + 1));
   if (grad) {
     GG_TRY(grow(ds->aux, ds->cap_aux, (size_t)n * pl.lstride));
     GG_TRY(grow(ds->gacc, ds->cap_gacc, (size_t)n * pl.stride));
@@ -318,7 +321,7 @@ ggeval_status launch(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStr
 
 ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_max, int layout,
                            const Plan& pl, bool with_aux, cudaStream_t st,
-                           const uint8_t* mask = nullptr) {
+                           const int* count = nullptr, const int* idx = nullptr) {
   gg::PackParams pp{};
   pp.op = db.op;
   pp.cval = db.cval;
@@ -334,7 +337,8 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.aux = with_aux ? ds->aux : nullptr;
   pp.len = ds->len;
   pp.status = ds->status;
-  pp.mask = mask;
+  pp.count = count;
+  pp.idx = idx;
   pp.allow_pow = pl.pow ? 1 : 0;
   pp.fold = pl.fold ? 1 : 0;
   return launch(gg::pack_ptr(), dim3((n + gg::PACK_WARPS - 1) / gg::PACK_WARPS),
@@ -387,17 +391,35 @@ gg::FinParams fin_params(ggeval_dataset* ds, int n, const Plan& pl, float* smse,
 
 constexpr size_t PROF_MAX = 4096;
 
-// pack -> zero counter -> batched forward -> finalise
+// zero counters -> [compact the masked trials] -> pack -> batched forward ->
+// finalise.  With a mask the changed trials are compacted into slots
+// 0 .. count-1 on the device (counters[2] = count, ds->idx = their indices), so
+// the forward kernel's work items cover only them.
 ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_batch* b,
                            const Plan& pl, float* smse, float* a, float* bb, float* mse,
                            bool with_aux, cudaStream_t st, bool profile = false,
                            const uint8_t* mask = nullptr) {
   const int n = b->n;
-  GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st, mask));
-  // counters[0]: the work counter; counters[8 + t]: trial t found non-finite
+  // counters[0]: the work counter; counters[2]: the compacted count;
+  // counters[8 + slot]: the slot's trial found non-finite
   GG_CU(cudaMemsetAsync(ds->counters, 0, sizeof(int) * ((size_t)n + 8), st));
+  const int* count = nullptr;
+  const int* idx = nullptr;
+  if (mask) {
+    const int threads = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
+    const uint8_t* m = mask;
+    int nn = n;
+    int* out_idx = ds->idx;
+    int* out_count = ds->counters + 2;
+    void* args[] = {&m, &nn, &out_idx, &out_count};
+    GG_CU(cudaLaunchKernel(gg::compact_ptr(), dim3(1), dim3(threads), args, 0, st));
+    count = ds->counters + 2;
+    idx = ds->idx;
+  }
+  GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st, count, idx));
   gg::FwdParams fp = fwd_params(ds, n, pl);
   fp.dead = ds->counters + 8;
+  fp.count = count;
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if (profile && ds->prof_used < PROF_MAX) {
     if (ds->prof_used == ds->prof_ev.size()) {
@@ -413,6 +435,8 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
   q.dead = fp.dead;
+  q.count = count;
+  q.idx = idx;
   GG_TRY(launch(gg::fin_ptr(), dim3((n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
                 dim3(32 * gg::FIN_WARPS), 0, st, &q));
   return GGEVAL_OK;
@@ -544,6 +568,7 @@ void ggeval_destroy(ggeval_dataset* ds) {
   cudaFree(ds->ab);
   cudaFree(ds->gacc);
   cudaFree(ds->counters);
+  cudaFree(ds->idx);
   cudaFree(ds->stage);
   for (auto& e : ds->prof_ev) {
     cudaEventDestroy(e.first);
@@ -599,7 +624,8 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
     key.flags = flags;
     key.mask = mask;
     for (int i = 0; i < 4; ++i) key.out[i] = outs[i];
-    const void* ws[7] = {ds->prog, ds->len, ds->part, ds->ab, ds->counters, ds->stage, ds->status};
+    const void* ws[8] = {ds->prog, ds->len,   ds->part,   ds->ab,
+                         ds->counters, ds->stage, ds->status, ds->idx};
     std::memcpy(key.ws, ws, sizeof ws);
     key.cfg = pl.cfg;
     key.kind = 1;
@@ -1217,7 +1243,6 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   pp.aux = nullptr;
   pp.len = len;
   pp.status = ds->status;
-  pp.mask = nullptr;
   pp.fold = 1;
   GG_TRY(launch(gg::pack_ptr(), dim3((b->n + gg::PACK_WARPS - 1) / gg::PACK_WARPS),
                 dim3(32 * gg::PACK_WARPS), gg::PACK_WARPS * gg::pack_warp_bytes(pl.stride),

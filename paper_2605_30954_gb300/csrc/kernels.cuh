@@ -16,9 +16,10 @@ struct PackParams {
   int n, h_max, stride, layout, n_features, max_slots, lstride;
   uint2* prog;           // [n][lstride] (word, const bits)
   Aux* aux;              // nullable, [n][lstride]
-  int* len;              // [n] instruction count, -1 for an invalid trial, 0 masked out
+  int* len;              // [n] per slot: instruction count, -1 for an invalid trial
   unsigned* status;
-  const uint8_t* mask;   // nullable: evaluate only trials with a nonzero byte
+  const int* count;      // null, or the number of slots to pack (set on the device)
+  const int* idx;        // with count: the trial packed into each slot
   int allow_pow;         // 0: an active pow node makes the trial invalid
   int fold;              // fold constant subtrees (ignored when aux is set)
 };
@@ -61,6 +62,8 @@ struct FwdParams {
   float* rows_out;     // [P][N] per-row values (ROWS variant only)
   int* dead;           // [P] zero at launch, or null: 1 once a tile of the trial
                        // is non-finite or exceeds 2^50 (its fitness is +inf)
+  const int* count;    // null, or the number of trials (slots) to evaluate, set
+                       // on the device (masked evaluation; at most P)
 };
 
 // partial record of one (trial, tile): the shift c, (hi, lo) of S_d, S_dd and
@@ -141,12 +144,12 @@ __device__ __forceinline__ void fold_group(float& m1, float& m2, float& m3, floa
 // memory with one TMA bulk copy per feature row, completing on bar[s]; a
 // ragged last tile has its tail zeroed first.  Past the last item the
 // barrier is completed without a copy so that waiting warps see the end.
-__device__ __forceinline__ void produce_tile(const FwdParams& p, int s, float* xs, uint64_t* bar,
-                                             int* ctl, int lane) {
+__device__ __forceinline__ void produce_tile(const FwdParams& p, int n_items, int s, float* xs,
+                                             uint64_t* bar, int* ctl, int lane) {
   int item = 0;
   if (lane == 0) item = atomicAdd(p.counter, 1);
   item = __shfl_sync(0xffffffffu, item, 0);
-  if (item < p.n_items) {
+  if (item < n_items) {
     const int tile = item % p.n_tiles;
     const int row0 = tile * p.tile_rows;
     const int nrows = min(p.tile_rows, p.N - row0);
@@ -188,6 +191,10 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const size_t tile_floats = (size_t)(p.F + 1) * p.tile_rows;
+  // trials (slots) to evaluate and the work items they make: a masked
+  // evaluation sets the count on the device (compacted changed trials)
+  const int P = p.count ? min(*p.count, p.P) : p.P;
+  const int n_items = p.count ? p.n_tiles * ((P + p.group - 1) / p.group) : p.n_items;
   float* xsb = reinterpret_cast<float*>(smem);  // two tile buffers
   float* stacks = xsb + 2 * tile_floats;
   float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * R;  // this lane, slot 0
@@ -203,8 +210,8 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
   }
   __syncthreads();
   if (warp == 0) {
-    produce_tile(p, 0, xsb, &bar[0], ctl, lane);
-    produce_tile(p, 1, xsb + tile_floats, &bar[1], ctl + 4, lane);
+    produce_tile(p, n_items, 0, xsb, &bar[0], ctl, lane);
+    produce_tile(p, n_items, 1, xsb + tile_floats, &bar[1], ctl + 4, lane);
   }
 
   float A[R];
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
     parity ^= 1u << s;
     int* c = ctl + 4 * s;
     const int item = *reinterpret_cast<volatile int*>(&c[0]);
-    if (item >= p.n_items) break;
+    if (item >= n_items) break;
     const float* xs = xsb + s * tile_floats;
     const int g = item / p.n_tiles;
     const int tile = item - g * p.n_tiles;
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
       if (lane == 0) t = atomicAdd(&c[1], 1);
       t = __shfl_sync(0xffffffffu, t, 0);
       const int trial = g * p.group + t;
-      if (t >= p.group || trial >= p.P) break;
+      if (t >= p.group || trial >= P) break;
       const int L = p.len[trial];
       if (L <= 0) continue;
       // stage the program with each feature field scaled to its tile offset;
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
         c[2] = 0;
       }
       __syncwarp();
-      produce_tile(p, s, xsb + s * tile_floats, &bar[s], c, lane);
+      produce_tile(p, n_items, s, xsb + s * tile_floats, &bar[s], c, lane);
     }
   }
 }
@@ -337,6 +344,8 @@ struct FinParams {
   double* ab;          // [P][4]: a* - ybar, b*, finite flag, 0 (adjoint), nullable
   const int* dead;     // [P] or null: 1 for a trial the forward kernel found
                        // non-finite (some of its tile records were skipped)
+  const int* count;    // null, or the number of slots evaluated (masked evaluation)
+  const int* idx;      // with count: the trial index of every slot (its outputs)
 };
 
 constexpr double VAR_TOL = 1e-12;

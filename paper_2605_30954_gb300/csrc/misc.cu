@@ -10,8 +10,9 @@ __global__ void fin_kernel(const FinParams p) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  const int t = blockIdx.x * nw + warp;
-  const int len = t < p.P ? p.len[t] : 0;  // 0: masked out, outputs untouched
+  const int t = blockIdx.x * nw + warp;  // slot (= trial unless compacted)
+  const int P = p.count ? min(*p.count, p.P) : p.P;
+  const int len = t < P ? p.len[t] : 0;
   if (len > 0 && p.dead && p.dead[t]) {
     // found non-finite by the forward kernel, which skipped its later tiles:
     // +inf fitness without the (incomplete) tile records
@@ -56,9 +57,10 @@ __global__ void fin_kernel(const FinParams p) {
   if (lane == 0) lens[warp] = len;
   __syncthreads();
   if (warp != 0 || lane >= nw) return;
-  const int tt = blockIdx.x * nw + lane;
+  const int ts = blockIdx.x * nw + lane;
   const int L = lens[lane];
-  if (tt >= p.P || L == 0) return;
+  if (ts >= P || L == 0) return;
+  const int tt = p.count ? p.idx[ts] : ts;  // the trial whose outputs these are
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
   double smse, a, b, mse, ac = 0.0, bo = 0.0;
@@ -136,7 +138,45 @@ __global__ void transpose_kernel(const TransposeParams p) {
   }
 }
 
+// Masked evaluation: the indices of the trials whose mask byte is nonzero,
+// in ascending order, and their count (one block; each thread scans a
+// contiguous run of the mask, then a block-wide exclusive scan of the
+// threads' counts gives each thread its first output slot).
+__global__ void compact_kernel(const uint8_t* mask, int n, int* idx, int* count) {
+  __shared__ int warp_tot[32];
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = (int)threadIdx.x * per;
+  const int b1 = min(n, b0 + per);
+  int c = 0;
+  for (int i = b0; i < b1; ++i) c += mask[i] != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = c;  // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    int w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) warp_tot[lane] = w;  // inclusive totals of warps 0..lane
+    if (lane == nw - 1) *count = w;
+  }
+  __syncthreads();
+  int off = x - c + (warp > 0 ? warp_tot[warp - 1] : 0);
+  for (int i = b0; i < b1; ++i)
+    if (mask[i]) idx[off++] = i;
+}
+
 const void* fin_ptr() { return reinterpret_cast<const void*>(&fin_kernel); }
+const void* compact_ptr() { return reinterpret_cast<const void*>(&compact_kernel); }
 const void* gradout_ptr() { return reinterpret_cast<const void*>(&gradout_kernel); }
 const void* adam_ptr() { return reinterpret_cast<const void*>(&adam_kernel); }
 const void* transpose_ptr() { return reinterpret_cast<const void*>(&transpose_kernel); }

@@ -60,6 +60,7 @@ inline size_t adj_smem_bytes(int warps, int lstride, int slots, int rows) {
 
 const void* pack_ptr();
 const void* fin_ptr();
+const void* compact_ptr();
 const void* adj_ptr(int rows, bool pow);
 const void* gradout_ptr();
 const void* adam_ptr();

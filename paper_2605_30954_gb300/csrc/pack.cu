@@ -76,8 +76,9 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
   extern __shared__ __align__(16) unsigned char pk_smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int t = blockIdx.x * PACK_WARPS + warp;
-  if (t >= p.n) return;  // the whole warp
+  const int t = blockIdx.x * PACK_WARPS + warp;  // the program slot
+  if (t >= p.n || (p.count && t >= *p.count)) return;  // the whole warp
+  const int trial = p.count ? p.idx[t] : t;
   const int S = p.stride;
   unsigned char* base = pk_smem + (size_t)warp * pack_warp_bytes(S);
   float* fv = reinterpret_cast<float*>(base);
@@ -90,11 +91,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
   uint8_t* fl = kind + S;
   uint8_t* need = fl + S;
 
-  if (p.mask && !p.mask[t]) {  // not evaluated in this call
-    if (lane == 0) p.len[t] = 0;
-    return;
-  }
-  const int h = p.height ? (int)p.height[t] : p.h_max;
+  const int h = p.height ? (int)p.height[trial] : p.h_max;
   if (h < 0 || h > p.h_max) {
     if (lane == 0) {
       p.len[t] = -1;
@@ -104,8 +101,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
   }
   const int n = (1 << (h + 1)) - 1;
   const bool fold = p.fold && !p.aux;
-  const uint8_t* gop = p.op + (size_t)t * S;
-  const float* gcv = p.cval + (size_t)t * S;
+  const uint8_t* gop = p.op + (size_t)trial * S;
+  const float* gcv = p.cval + (size_t)trial * S;
   for (int i = lane; i < n; i += 32) {
     const int o = p.layout ? prefix_position(i, h) : i;
     int k;
