@@ -60,13 +60,6 @@ struct DeviceGuard {
 };
 
 inline int stride_of(int h) { return (1 << (h + 1)) - 1; }
-// threads per block of the kernels that mark active nodes (GOM "changed",
-// trial sizes): each thread keeps 2 x stride bytes of shared scratch, within
-// the 48 KB default
-inline int pack_threads(int stride) {
-  int t = (49152 / (2 * stride)) & ~31;
-  return t < 32 ? 32 : (t > 128 ? 128 : t);
-}
 // stack slots of a template of height h: Sethi-Ullman order with fused
 // terminals needs at most h - 1 (the packer checks the bound)
 inline int slots_of(int h) { return h > 2 ? h - 1 : 1; }
@@ -976,12 +969,11 @@ ggeval_status ggeval_gom_changed(const ggeval_batch* b, const uint8_t* backup_op
     return fail(GGEVAL_ERR_ARG, "bad batch");
   if (b->n == 0) return GGEVAL_OK;
   const int stride = stride_of(b->max_height);
-  const int threads = pack_threads(stride);
   gg::GomChangedParams p{b->n, stride, b->max_height, b->layout, n_features, b->op, b->cval,
                          b->height, backup_op, backup_cval, changed};
-  return launch(gg::gom_changed_ptr(), dim3((unsigned)((b->n + threads - 1) / threads)),
-                dim3(threads), (size_t)threads * 2 * stride, static_cast<cudaStream_t>(stream),
-                &p);
+  constexpr int W = 4;  // one warp per offspring
+  return launch(gg::gom_changed_ptr(), dim3((unsigned)((b->n + W - 1) / W)), dim3(32 * W),
+                (size_t)W * 2 * stride, static_cast<cudaStream_t>(stream), &p);
 }
 
 ggeval_status ggeval_gom_accept(int32_t n, int32_t max_height, uint8_t* op, float* cval,
@@ -1007,11 +999,11 @@ ggeval_status ggeval_trial_sizes(const ggeval_batch* b, int32_t n_features, int3
     return fail(GGEVAL_ERR_ARG, "bad batch");
   if (b->n == 0) return GGEVAL_OK;
   const int stride = stride_of(b->max_height);
-  const int threads = 2 * pack_threads(stride) > 128 ? 128 : 2 * pack_threads(stride);
   gg::TrialSizeParams p{b->n, stride, b->max_height, b->layout, n_features, b->op, b->height,
                         size};
-  return launch(gg::trial_size_ptr(), dim3((unsigned)((b->n + threads - 1) / threads)),
-                dim3(threads), (size_t)threads * stride, static_cast<cudaStream_t>(stream), &p);
+  constexpr int W = 4;  // one warp per trial
+  return launch(gg::trial_size_ptr(), dim3((unsigned)((b->n + W - 1) / W)), dim3(32 * W),
+                (size_t)W * stride, static_cast<cudaStream_t>(stream), &p);
 }
 
 ggeval_status ggeval_dataset_info(const ggeval_dataset* ds, int64_t* n_rows, int32_t* n_features,

@@ -24,55 +24,62 @@ __global__ void gom_donate_kernel(const GomDonateParams p) {
   }
 }
 
-// Mark the active nodes of one template in `act` (Section 3.1: the root is
-// active, the children of an active function are active - only the left
-// one of a unary function - and a terminal's subtree is an intron).
-// Nodes of an invalid active opcode are marked too; the evaluation reports
-// such a trial.
-__device__ void mark_active(const uint8_t* op, int h, int layout, int n_features, uint8_t* act) {
+// Mark the active nodes of one template (height h) in `act`, in heap
+// order, with the lanes of a warp over the nodes of one level at a time
+// (Section 3.1: the root is active; the children of an active function are
+// active - only the left one of a unary function - and a terminal's
+// subtree is an intron).  Nodes of an invalid active opcode are marked too;
+// the evaluation reports such a trial.
+__device__ void warp_mark_active(const uint8_t* op, int h, int layout, int n_features,
+                                 uint8_t* act, int lane) {
   const int n = (1 << (h + 1)) - 1;
-  for (int i = 0; i < n; ++i) act[i] = 0;
-  act[0] = 1;
-  for (int pos = 0; pos < n; ++pos) {
-    if (!act[pos]) continue;
-    const int d = act[pos] - 1;
-    int kind;
-    const int cls = classify(op[pos], n_features, &kind);
-    if ((cls != C_UNARY && cls != C_BINARY) || d >= h) continue;
-    int l, r;
-    children(layout, h, pos, d, &l, &r);
-    act[l] = (uint8_t)(d + 2);
-    if (cls == C_BINARY) act[r] = (uint8_t)(d + 2);
+  for (int i = lane; i < n; i += 32) act[i] = i == 0;
+  __syncwarp();
+  for (int d = 0; d < h; ++d) {
+    for (int i = (1 << d) - 1 + lane; i < (1 << (d + 1)) - 1; i += 32) {
+      if (!act[i]) continue;
+      int kind;
+      const int cls = classify(op[layout ? prefix_position(i, h) : i], n_features, &kind);
+      if (cls != C_UNARY && cls != C_BINARY) continue;
+      act[2 * i + 1] = 1;
+      if (cls == C_BINARY) act[2 * i + 2] = 1;
+    }
+    __syncwarp();
   }
 }
 
 // changed_j = 1 when O_j and B_j differ at a node that is active in either
 // (its opcode, or the constant of an ERC): the paper's text evaluates an
 // offspring only if an actively used part of the template was affected
-// (Section 3.1).  One thread per offspring; two active masks in shared memory.
+// (Section 3.1).  One warp per offspring; two active masks in shared memory.
 __global__ void gom_changed_kernel(const GomChangedParams p) {
   extern __shared__ unsigned char gm_smem[];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.n) return;
-  uint8_t* ao = gm_smem + (size_t)threadIdx.x * 2 * p.stride;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= p.n) return;  // the whole warp
+  uint8_t* ao = gm_smem + (size_t)warp * 2 * p.stride;
   uint8_t* ab = ao + p.stride;
   const int h = p.height ? (int)p.height[j] : p.h_max;
-  uint8_t ch = 1;
-  if (h >= 0 && h <= p.h_max) {
-    const uint8_t* o = p.op + (size_t)j * p.stride;
-    const uint8_t* b = p.bop + (size_t)j * p.stride;
-    const float* oc = p.cval + (size_t)j * p.stride;
-    const float* bc = p.bcval + (size_t)j * p.stride;
-    mark_active(o, h, p.layout, p.n_features, ao);
-    mark_active(b, h, p.layout, p.n_features, ab);
-    const int n = (1 << (h + 1)) - 1;
-    ch = 0;
-    for (int i = 0; i < n && !ch; ++i) {
-      if (!ao[i] && !ab[i]) continue;
-      if (o[i] != b[i] || (o[i] == T_ERC && !(oc[i] == bc[i]))) ch = 1;
-    }
+  if (h < 0 || h > p.h_max) {
+    if (lane == 0) p.changed[j] = 1;
+    return;
   }
-  p.changed[j] = ch;
+  const uint8_t* o = p.op + (size_t)j * p.stride;
+  const uint8_t* b = p.bop + (size_t)j * p.stride;
+  const float* oc = p.cval + (size_t)j * p.stride;
+  const float* bc = p.bcval + (size_t)j * p.stride;
+  warp_mark_active(o, h, p.layout, p.n_features, ao, lane);
+  warp_mark_active(b, h, p.layout, p.n_features, ab, lane);
+  const int n = (1 << (h + 1)) - 1;
+  bool diff = false;
+  for (int i = lane; i < n; i += 32) {
+    if (!ao[i] && !ab[i]) continue;
+    const int pos = p.layout ? prefix_position(i, h) : i;
+    diff |= o[pos] != b[pos] || (o[pos] == T_ERC && !(oc[pos] == bc[pos]));
+  }
+  diff = __any_sync(0xffffffffu, diff);
+  if (lane == 0) p.changed[j] = diff ? 1 : 0;
 }
 
 // Accept O_j when its fitness is not worse than B_j's (ties accepted; a
@@ -107,21 +114,27 @@ __global__ void gom_accept_kernel(const GomAcceptParams p) {
 
 // size_j = number of active nodes of trial j (the size objective of a
 // multi-objective error + size search; Section 5 names multi-objective
-// GP-GOMEA as future work).  -1 for an out-of-range height.
+// GP-GOMEA as future work).  -1 for an out-of-range height.  One warp per
+// trial.
 __global__ void trial_size_kernel(const TrialSizeParams p) {
   extern __shared__ unsigned char ts_smem[];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.n) return;
-  uint8_t* act = ts_smem + (size_t)threadIdx.x * p.stride;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= p.n) return;  // the whole warp
+  uint8_t* act = ts_smem + (size_t)warp * p.stride;
   const int h = p.height ? (int)p.height[j] : p.h_max;
-  int cnt = -1;
-  if (h >= 0 && h <= p.h_max) {
-    mark_active(p.op + (size_t)j * p.stride, h, p.layout, p.n_features, act);
-    const int n = (1 << (h + 1)) - 1;
-    cnt = 0;
-    for (int i = 0; i < n; ++i) cnt += act[i] != 0;
+  if (h < 0 || h > p.h_max) {
+    if (lane == 0) p.size[j] = -1;
+    return;
   }
-  p.size[j] = cnt;
+  warp_mark_active(p.op + (size_t)j * p.stride, h, p.layout, p.n_features, act, lane);
+  const int n = (1 << (h + 1)) - 1;
+  int cnt = 0;
+  for (int i = lane; i < n; i += 32) cnt += act[i] != 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) p.size[j] = cnt;
 }
 
 const void* trial_size_ptr() { return reinterpret_cast<const void*>(&trial_size_kernel); }

@@ -148,6 +148,19 @@ constexpr uint8_t PK_CONST = 0x40;   // active subtree without a feature
 constexpr uint8_t PK_INSIDE = 0x80;  // below the root of a folded subtree
 constexpr uint8_t PK_DEPTH = 0x1F;
 
+// Template position of the node with heap index i (children 2i+1, 2i+2) in
+// the prefix layout of a template of height h: the path from the root is
+// the bits of i + 1 below its leading one (0 = left, 1 = right), and in the
+// prefix layout the left child of a node at depth e is the next position,
+// the right child 2^(h - e) further.
+GG_HD int prefix_position(int i, int h) {
+  int d = 0;
+  while (((i + 1) >> (d + 1)) != 0) ++d;
+  int pos = 0;
+  for (int e = 0; e < d; ++e) pos += (((i + 1) >> (d - 1 - e)) & 1) ? (1 << (h - e)) : 1;
+  return pos;
+}
+
 // Children of the node at `pos` (depth `depth`) in a template of height h.
 GG_HD void children(int layout, int h, int pos, int depth, int* l, int* r) {
   if (layout == 0) {

@@ -62,16 +62,6 @@ constexpr uint8_t N_INSIDE = 8;   // below a folded subtree's root: not emitted
 constexpr uint8_t N_RFIRST = 16;  // two subtrees, the right one evaluated first
 constexpr uint8_t N_FUSED = 32;   // terminal fused into its parent's instruction
 
-__device__ __forceinline__ int prefix_position(int i, int h) {
-  // the path from the root is the bits of i + 1 below its leading one
-  // (0 = left, 1 = right); in the prefix layout the left child of a node at
-  // depth e is the next position and the right child 2^(h - e) further
-  const int d = 31 - __clz(i + 1);
-  int pos = 0;
-  for (int e = 0; e < d; ++e) pos += (((i + 1) >> (d - 1 - e)) & 1) ? (1 << (h - e)) : 1;
-  return pos;
-}
-
 __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams p) {
   extern __shared__ __align__(16) unsigned char pk_smem[];
   const int lane = threadIdx.x & 31;

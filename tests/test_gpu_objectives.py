@@ -28,6 +28,33 @@ def test_trial_sizes_match_active_sets(gg):
     np.testing.assert_array_equal(size, want)
 
 
+@pytest.mark.parametrize("layout", ["heap", "prefix"])
+def test_trial_sizes_and_changed_in_both_layouts(gg, layout):
+    """Active-node counts and the active-part "changed" test in either
+    template layout, against the oracle's active sets."""
+    rng = np.random.default_rng(21)
+    op, cv, hs = synth.random_templates(rng, 200, rng.integers(0, 8, 200), 7,
+                                        synth.FULL_SET, 4, 0.6)
+    op2, cv2 = op.copy(), cv.copy()
+    flip = rng.random(op.shape) < 0.03  # mutate a few nodes (active or intron)
+    op2[flip] = synth.FEAT0 + rng.integers(0, 4, flip.sum())
+    if layout == "prefix":
+        op, cv = synth.to_prefix(op, cv, hs.astype(np.int64))
+        op2, cv2 = synth.to_prefix(op2, cv2, hs.astype(np.int64))
+    lay = 0 if layout == "heap" else 1
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h8 = hs.astype(np.int8)
+    size = gg.trial_sizes(d(op), d(cv), 4, d(h8), layout=lay).cpu().numpy()
+    ch = gg.gom_changed(d(op2), d(cv2), d(op), d(cv), 4, d(h8), layout=lay).cpu().numpy()
+    torch.cuda.synchronize()
+    for p in range(200):
+        t = O.Template(op[p], cv[p], int(hs[p]), layout, 4)
+        assert size[p] == int(O.active_mask(t).sum()), p
+    want = O.gom.changed(op2, cv2, op, cv, hs, layout, 4)
+    np.testing.assert_array_equal(ch, want)
+    assert 0 < want.sum() < 200
+
+
 def test_nmse_and_dataset_info(gg):
     w = PA.build("c2", 5000, 30)
     ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
