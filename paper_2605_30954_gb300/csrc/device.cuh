@@ -31,6 +31,36 @@ __device__ __forceinline__ float binop(float a, float b) {
   return 0.f;
 }
 
+// The R rows of a lane through one binary operator.  +, -, x and AQ run on
+// row pairs as packed FP32 instructions (FADD2 / FMUL2 / FFMA2 of sm_100 and
+// later, each half rounded exactly as the scalar instruction, so every row
+// is bit-identical to binop); division and pow stay scalar.  `o` may alias
+// `a` or `b`.
+template <int K, int R>
+__device__ __forceinline__ void binop_rows(const float (&a)[R], const float (&b)[R],
+                                           float (&o)[R]) {
+  if constexpr (R % 2 == 0 && (K == K_ADD || K == K_SUB || K == K_MUL || K == K_AQ)) {
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const float2 x = make_float2(a[2 * i], a[2 * i + 1]);
+      const float2 y = make_float2(b[2 * i], b[2 * i + 1]);
+      float2 v;
+      if constexpr (K == K_ADD) v = __fadd2_rn(x, y);
+      if constexpr (K == K_SUB) v = __fadd2_rn(x, make_float2(-y.x, -y.y));
+      if constexpr (K == K_MUL) v = __fmul2_rn(x, y);
+      if constexpr (K == K_AQ) {
+        const float2 q = __ffma2_rn(y, y, make_float2(1.0f, 1.0f));
+        v = __fmul2_rn(x, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+      }
+      o[2 * i] = v.x;
+      o[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = binop<K>(a[r], b[r]);
+  }
+}
+
 template <int U>
 __device__ __forceinline__ float unop(float a) {
   if constexpr (U == U_SIN) return sinf(a);
@@ -72,6 +102,14 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
     if (__builtin_expect(big, 0)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sinf(A[r]) : cosf(A[r]);
+    } else if constexpr (R % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 v =
+            sin_or_cos_reduced2(make_float2(A[2 * i], A[2 * i + 1]), U == U_SIN ? 0 : 1);
+        A[2 * i] = v.x;
+        A[2 * i + 1] = v.y;
+      }
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sin_reduced(A[r]) : cos_reduced(A[r]);
@@ -86,10 +124,21 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
     if (__builtin_expect(special, 0)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = sqrtf(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
+    } else if constexpr (R % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 v = sqrt_newton2(U == U_SQRT_ABS
+                                          ? make_float2(fabsf(A[2 * i]), fabsf(A[2 * i + 1]))
+                                          : make_float2(A[2 * i], A[2 * i + 1]));
+        A[2 * i] = v.x;
+        A[2 * i + 1] = v.y;
+      }
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = sqrt_newton(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
     }
+  } else if constexpr (U == U_SQUARE) {
+    binop_rows<K_MUL, R>(A, A, A);
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) A[r] = unop<U>(A[r]);
@@ -177,27 +226,29 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
 #define GG_BIN(kd)                                                    \
   case I_BF + kd:                                                     \
     load_rows<R>(xf, t);                                              \
-    GG_ROWS A[r] = binop<kd>(A[r], t[r]);                             \
+    binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_BC + kd:                                                     \
-    GG_ROWS A[r] = binop<kd>(A[r], c);                                \
+    GG_ROWS t[r] = c;                                                 \
+    binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_LF + kd:                                                     \
     load_rows<R>(xf, t);                                              \
-    GG_ROWS A[r] = binop<kd>(t[r], A[r]);                             \
+    binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_LC + kd:                                                     \
-    GG_ROWS A[r] = binop<kd>(c, A[r]);                                \
+    GG_ROWS t[r] = c;                                                 \
+    binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_BS + kd:                                                     \
     sp -= SLOT;                                                       \
     load_rows<R>(sp, t);                                              \
-    GG_ROWS A[r] = binop<kd>(t[r], A[r]);                             \
+    binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_RS + kd:                                                     \
     sp -= SLOT;                                                       \
     load_rows<R>(sp, t);                                              \
-    GG_ROWS A[r] = binop<kd>(A[r], t[r]);                             \
+    binop_rows<kd, R>(A, t, A);                                       \
     break;
 
     switch (opc) {

@@ -93,50 +93,53 @@ __device__ __forceinline__ void accumulate_exact(const float (&A)[R], const floa
   }
 }
 
-// Pairwise sums of the pass's R rows are added to plain FP32 group sums
-// (m1..m3); the caller folds the group sums into the error-free (hi, lo)
-// accumulators every GROUP passes (fold_group).
+// Plain FP32 group sums: the pass's R rows, two at a time as packed
+// FP32 instructions, are added to the lane's group sums m1..m3 (one per
+// half of a row pair); the caller folds the group sums into the error-free
+// (hi, lo) accumulators every GROUP passes (fold_group).  A group sum adds
+// at most GROUP x R / 2 terms per half before it is folded.
 template <int R, bool MASK>
-__device__ __forceinline__ void accumulate_pairwise(const float (&A)[R], const float (&yv)[R],
-                                                    float cs, int valid, float& m1, float& m2,
-                                                    float& m3, float& fm) {
-  float d[R];
+__device__ __forceinline__ void accumulate_grouped(const float (&A)[R], const float (&yv)[R],
+                                                   float cs, int valid, float2& m1, float2& m2,
+                                                   float2& m3, float& fm) {
+  if constexpr (R % 2 == 0) {
+    const float2 nc = make_float2(-cs, -cs);
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const bool ok = !MASK || r < valid;
-    d[r] = ok ? A[r] - cs : 0.f;
-    fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
-  }
-  float a[R / 2], b[R / 2], c[R / 2];
+    for (int i = 0; i < R / 2; ++i) {
+      float2 d = __fadd2_rn(make_float2(A[2 * i], A[2 * i + 1]), nc);
+      const bool ok0 = !MASK || 2 * i < valid, ok1 = !MASK || 2 * i + 1 < valid;
+      if constexpr (MASK) {
+        d.x = ok0 ? d.x : 0.f;
+        d.y = ok1 ? d.y : 0.f;
+      }
+      fm = fmaxf(fm, ok0 ? fabsf(A[2 * i]) : 0.f);
+      fm = fmaxf(fm, ok1 ? fabsf(A[2 * i + 1]) : 0.f);
+      m1 = __fadd2_rn(m1, d);
+      m2 = __ffma2_rn(d, d, m2);
+      m3 = __ffma2_rn(d, make_float2(yv[2 * i], yv[2 * i + 1]), m3);
+    }
+  } else {
 #pragma unroll
-  for (int i = 0; i < R / 2; ++i) {
-    a[i] = d[2 * i] + d[2 * i + 1];
-    b[i] = fmaf(d[2 * i], d[2 * i], d[2 * i + 1] * d[2 * i + 1]);
-    c[i] = fmaf(d[2 * i], yv[2 * i], d[2 * i + 1] * yv[2 * i + 1]);
-  }
-#pragma unroll
-  for (int w = R / 4; w >= 1; w >>= 1) {
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      a[i] = a[2 * i] + a[2 * i + 1];
-      b[i] = b[2 * i] + b[2 * i + 1];
-      c[i] = c[2 * i] + c[2 * i + 1];
+    for (int r = 0; r < R; ++r) {
+      const bool ok = !MASK || r < valid;
+      const float d = ok ? A[r] - cs : 0.f;
+      fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
+      m1.x += d;
+      m2.x = fmaf(d, d, m2.x);
+      m3.x = fmaf(d, yv[r], m3.x);
     }
   }
-  m1 += a[0];
-  m2 += b[0];
-  m3 += c[0];
 }
 
 constexpr int GROUP = 4;  // passes per plain FP32 group sum
 
-__device__ __forceinline__ void fold_group(float& m1, float& m2, float& m3, float& s1h,
+__device__ __forceinline__ void fold_group(float2& m1, float2& m2, float2& m3, float& s1h,
                                            float& s1l, float& s2h, float& s2l, float& s3h,
                                            float& s3l) {
-  acc_add(s1h, s1l, m1);
-  acc_add(s2h, s2l, m2);
-  acc_add(s3h, s3l, m3);
-  m1 = m2 = m3 = 0.f;
+  acc_add(s1h, s1l, m1.x + m1.y);
+  acc_add(s2h, s2l, m2.x + m2.y);
+  acc_add(s3h, s3l, m3.x + m3.y);
+  m1 = m2 = m3 = make_float2(0.f, 0.f);
 }
 
 // Claim the next work item for tile buffer `s` and start loading it: run by
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
       __syncwarp();
 
       float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
-      float m1 = 0.f, m2 = 0.f, m3 = 0.f;
+      float2 m1 = make_float2(0.f, 0.f), m2 = m1, m3 = m1;
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
@@ -285,9 +288,9 @@ __global__ void __launch_bounds__(512, MINB) fwd_kernel(const FwdParams p) {
             accumulate_exact<R, true>(A, yv, cs, valid, s1h, s1l, s2h, s2l, s3h, s3l, fm);
         } else {
           if (full)
-            accumulate_pairwise<R, false>(A, yv, cs, valid, m1, m2, m3, fm);
+            accumulate_grouped<R, false>(A, yv, cs, valid, m1, m2, m3, fm);
           else
-            accumulate_pairwise<R, true>(A, yv, cs, valid, m1, m2, m3, fm);
+            accumulate_grouped<R, true>(A, yv, cs, valid, m1, m2, m3, fm);
           if ((ps & (GROUP - 1)) == GROUP - 1 || ps == npass - 1)
             fold_group(m1, m2, m3, s1h, s1l, s2h, s2l, s3h, s3l);
         }
@@ -353,8 +356,8 @@ constexpr int FIN_WARPS = 16;  // trials per finaliser block
 
 // fin_kernel is defined in misc.cu.
 
-// Kernel pointers: variant 0 = 8 rows/lane pairwise sums, 1 = 4 rows/lane
-// pairwise, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
+// Kernel pointers: variant 0 = 8 rows/lane grouped sums, 1 = 4 rows/lane
+// grouped sums, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
 // variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers.
 // fwd.cu holds the table of the kernels without pow, fwd_pow.cu the kernels
 // that also run pow instructions (kept apart because the pow code costs the

@@ -2,7 +2,7 @@
 batched path has to handle together (row counts across tile boundaries and
 ragged tails, 1 to 12 features, heights 0 to 6 mixed within a batch, both
 layouts, every operator including pow, masks, folding on and off, exact and
-pairwise sums), each trial's fitness and per-row values compared with the
+grouped sums), each trial's fitness and per-row values compared with the
 FP64 oracle under the stated tolerances."""
 import numpy as np
 import pytest

@@ -101,8 +101,8 @@ def test_prefix_layout_matches_heap(gg, cfg):
     np.testing.assert_array_equal(outs_p[0], outs_h[0])
 
 
-def test_pairwise_sums_large_n(gg):
-    # N >= 32768 selects the 8-rows-per-lane kernel with pairwise sums
+def test_grouped_sums_large_n(gg):
+    # N >= 32768 selects the 8-rows-per-lane kernel with grouped sums
     w = PA.build("c2", 40_000, 48)
     tr, tf, _ = run_case(gg, w, check_rows=True)
     assert_tally(tr, min_checked=40_000 * 10)
