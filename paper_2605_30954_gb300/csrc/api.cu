@@ -233,7 +233,7 @@ ggeval_status make_plan(ggeval_dataset* ds, int n, int h_max, const Cfg& cfg, Pl
   if (!pl->fn) return fail(GGEVAL_ERR_ARG, "no kernel for variant %d", cfg.variant);
   const int rpp = 32 * gg::variant_rows(cfg.variant);
   if (cfg.tile_rows < rpp || cfg.tile_rows % rpp || cfg.group < 1 || cfg.warps < 1 ||
-      cfg.warps > 16)
+      cfg.warps > gg::variant_max_warps(cfg.variant))
     return fail(GGEVAL_ERR_ARG, "bad tile configuration");
   pl->smem = gg::fwd_smem_bytes(ds->F, cfg.tile_rows, cfg.warps, pl->lstride, pl->slots,
                                 gg::variant_rows(cfg.variant));
@@ -860,9 +860,10 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   else variants = {5, 1, 4, 0};
   std::vector<Cfg> cands;
   for (int v : variants)
-    for (int warps : {8, 16})
+    for (int warps : {8, 16, 20})
       for (int tmul : {2, 4, 8, 16})
         for (int gdiv : {1, 2}) {
+          if (warps > gg::variant_max_warps(v)) continue;
           Cfg c;
           c.variant = v;
           c.warps = warps;

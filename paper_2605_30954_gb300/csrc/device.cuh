@@ -74,15 +74,17 @@ __device__ __forceinline__ float unop(float a) {
   return 0.f;
 }
 
-// A unary operator on the R rows of a lane.  sin, cos and sqrt use the
+// A unary operator on the R rows of a lane.  sin, cos, sqrt and log use the
 // branch-free forms of gmath.cuh: one test over the R rows sends an
 // argument outside their domain (|x| > 2^17 for sin and cos; zero,
-// subnormal, infinite or NaN for sqrt) to the CUDA library function on a
-// cold path, so the common path has no per-row branch and each case holds
-// one short copy of the math per row (the library functions' range
-// handling, replicated R times in every case, crowds the instruction cache:
-// measured 3 to 9 % slower per step).  -DGG_LIBM_TRIG and -DGG_LIBM_SQRT
-// select the library functions everywhere.
+// subnormal, infinite, NaN or, without the absolute value, negative for
+// sqrt and log) to the CUDA library function on a cold path, so the common
+// path has no per-row branch and each case holds one short copy of the math
+// per row (the library functions' range handling, replicated R times in
+// every case, crowds the instruction cache: measured 3 to 9 % slower per
+// step).  With R even the rows go through the packed pair forms.
+// -DGG_LIBM_TRIG, -DGG_LIBM_SQRT and -DGG_LIBM_LOG select the library
+// functions everywhere.
 template <int U, int R>
 __device__ __forceinline__ void unop_rows(float (&A)[R]) {
 #ifdef GG_LIBM_TRIG
@@ -94,6 +96,11 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
   constexpr bool own = false;
 #else
   constexpr bool own = true;
+#endif
+#ifdef GG_LIBM_LOG
+  constexpr bool own_log = false;
+#else
+  constexpr bool own_log = true;
 #endif
   if constexpr (own_trig && (U == U_SIN || U == U_COS)) {
     bool big = false;
@@ -114,13 +121,30 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sin_reduced(A[r]) : cos_reduced(A[r]);
     }
+  } else if constexpr (own_log && (U == U_LOG_ABS || U == U_LOG)) {
+    bool special = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) special |= !positive_normal(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
+    if (__builtin_expect(special, 0)) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = logf(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
+    } else if constexpr (R % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        const float2 v = log_normal2(U == U_LOG_ABS
+                                         ? make_float2(fabsf(A[2 * i]), fabsf(A[2 * i + 1]))
+                                         : make_float2(A[2 * i], A[2 * i + 1]));
+        A[2 * i] = v.x;
+        A[2 * i + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = log_normal(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
+    }
   } else if constexpr (own && (U == U_SQRT_ABS || U == U_SQRT)) {
     bool special = false;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float v = U == U_SQRT_ABS ? fabsf(A[r]) : A[r];
-      special |= !(v >= SQRT_MIN && v <= SQRT_MAX);
-    }
+    for (int r = 0; r < R; ++r) special |= !positive_normal(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
     if (__builtin_expect(special, 0)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = sqrtf(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);

@@ -1,7 +1,9 @@
-"""Accuracy of the interpreter's sin, cos and sqrt against FP64 (per-row values
-through the C ABI), in FP32 units in the last place of the exact result.
-Arguments cover the reduction's range (|x| <= 2^17), the neighbourhoods of
-multiples of pi/2, the library fallback beyond it, and the special values."""
+"""Accuracy of the interpreter's sin, cos, sqrt and log against FP64 (per-row
+values through the C ABI), in FP32 units in the last place of the exact
+result.  Arguments cover the reduction's range (|x| <= 2^17), the
+neighbourhoods of multiples of pi/2, the library fallback beyond it, the
+neighbourhoods of 1 and of sqrt(1/2) 2^k where log's reduction switches
+exponent, and the special values."""
 import math
 
 import numpy as np
@@ -83,3 +85,40 @@ def test_sqrt_within_one_ulp(gg, tok):
     assert np.all(np.isinf(got[~fin]))
     if tok == "sqrt":
         assert np.isnan(rows_of(gg, "sqrt", np.array([-1.0, -1e-30], np.float32))).all()
+
+
+@pytest.mark.parametrize("tok", ["logabs", "log"])
+def test_log_within_one_and_a_half_ulp(gg, tok):
+    rng = np.random.default_rng(2)
+    k = np.arange(-126, 128)
+    edge = (np.sqrt(0.5) * 2.0 ** k).astype(np.float32)
+    one = np.float32(1.0) + np.arange(-3000, 3001, dtype=np.float32) * np.float32(2.0 ** -20)
+    x = np.concatenate([10.0 ** rng.uniform(-37.9, 38.5, 30000), rng.uniform(0, 4, 10000),
+                        edge, np.nextafter(edge, np.float32(0)), np.nextafter(edge, np.float32(np.inf)),
+                        one]).astype(np.float32)
+    x = x[(x >= np.float32(1.17549435e-38)) & np.isfinite(x)]
+    if tok == "logabs":
+        x = np.concatenate([x, -x])
+    got = rows_of(gg, tok, x).astype(np.float64)
+    want = np.log(np.abs(x.astype(np.float64)))
+    err = np.abs(got - want) / ulp32(want)
+    i = np.argmax(err)
+    assert err.max() <= 1.5, (x[i], got[i], want[i])
+
+
+@pytest.mark.parametrize("tok", ["logabs", "log"])
+def test_log_special_arguments(gg, tok):
+    x = np.array([0.0, -0.0, 1e-45, 1e-40, np.inf, np.nan, 1.0, 3.4028235e38, 1.17549435e-38],
+                 dtype=np.float32)
+    got = rows_of(gg, tok, x).astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        want = np.log(np.abs(x.astype(np.float64)))
+    assert np.all(got[:2] == -np.inf) and got[4] == np.inf and np.isnan(got[5])
+    assert got[6] == 0.0
+    fin = np.isfinite(want)
+    assert np.all(np.abs(got[fin] - want[fin]) <= 1.5 * ulp32(want[fin]))
+    neg = rows_of(gg, tok, np.array([-1.0, -2.5, -1e-30], np.float32))
+    if tok == "log":
+        assert np.isnan(neg).all()
+    else:
+        np.testing.assert_allclose(neg, np.log([1.0, 2.5, 1e-30]), rtol=2e-7)
