@@ -46,7 +46,7 @@ __device__ __forceinline__ void binop_rows(const float (&a)[R], const float (&b)
       const float2 y = make_float2(b[2 * i], b[2 * i + 1]);
       float2 v;
       if constexpr (K == K_ADD) v = __fadd2_rn(x, y);
-      if constexpr (K == K_SUB) v = __fadd2_rn(x, make_float2(-y.x, -y.y));
+      if constexpr (K == K_SUB) v = __ffma2_rn(y, make_float2(-1.0f, -1.0f), x);  // exact -y
       if constexpr (K == K_MUL) v = __fmul2_rn(x, y);
       if constexpr (K == K_AQ) {
         const float2 q = __ffma2_rn(y, y, make_float2(1.0f, 1.0f));
@@ -234,8 +234,20 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
                                             float* __restrict__ tape = nullptr) {
   constexpr int SLOT = 32 * R;  // floats per stack slot
   float* sp = stk;              // next free slot of this lane
-  uint2 ins = prog[0];
-  for (int k = 0; k < L; ++k) {
+  {
+    // the first instruction is always I_LDF0 or I_LDC0 (the packers emit a
+    // load without a push exactly there), so it is peeled off the switch
+    const uint2 first = prog[0];
+    if ((first.x & 0xffu) == I_LDF0) {
+      load_rows<R>(PRESCALED ? xs + (first.x >> 8) : xs + (first.x >> 8) * ts, A);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = __uint_as_float(first.y);
+    }
+    if constexpr (TAPE) store_rows<R>(tape, A);
+  }
+  uint2 ins = prog[1];
+  for (int k = 1; k < L; ++k) {
     const uint2 nxt = prog[k + 1];
     const uint32_t opc = ins.x & 0xffu;
     const float c = __uint_as_float(ins.y);
@@ -276,12 +288,6 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;
 
     switch (opc) {
-      case I_LDF0:
-        load_rows<R>(xf, A);
-        break;
-      case I_LDC0:
-        GG_ROWS A[r] = c;
-        break;
       case I_PSF:
         store_rows<R>(sp, A);
         sp += SLOT;

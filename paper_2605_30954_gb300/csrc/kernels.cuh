@@ -185,10 +185,10 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int n_items, in
 // [2] how many warps are done with it.  The warp that finishes a buffer
 // last resets [1], [2] and refills the buffer with the next item; no warp
 // ever waits for the others except for the tile it is about to use.
-// MINB is the launch-bounds occupancy target: 1 allows CTAs of up to 20
-// warps and the compiler up to 96 registers per thread (the register file
-// holds 20 warps at 96), 2 caps it at 64 (two 512-thread CTAs per SM).
-constexpr int fwd_max_threads(int minb) { return minb == 1 ? 640 : 512; }
+// MINB is the launch-bounds occupancy target: 1 allows CTAs of up to 24
+// warps and the compiler up to 80 registers per thread (the register file
+// holds 24 warps at 80), 2 caps it at 64 (two 512-thread CTAs per SM).
+constexpr int fwd_max_threads(int minb) { return minb == 1 ? 768 : 512; }
 template <int R, bool EXACT, bool ROWS, int MINB, bool POW>
 __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
