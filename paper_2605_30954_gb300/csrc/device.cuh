@@ -74,93 +74,99 @@ __device__ __forceinline__ float unop(float a) {
   return 0.f;
 }
 
-// A unary operator on the R rows of a lane.  sin, cos, sqrt and log use the
-// branch-free forms of gmath.cuh: one test over the R rows sends an
-// argument outside their domain (|x| > 2^17 for sin and cos; zero,
-// subnormal, infinite, NaN or, without the absolute value, negative for
-// sqrt and log) to the CUDA library function on a cold path, so the common
-// path has no per-row branch and each case holds one short copy of the math
-// per row (the library functions' range handling, replicated R times in
-// every case, crowds the instruction cache: measured 3 to 9 % slower per
-// step).  With R even the rows go through the packed pair forms.
-// -DGG_LIBM_TRIG, -DGG_LIBM_SQRT and -DGG_LIBM_LOG select the library
-// functions everywhere.
+// The cold path of a unary operator: the CUDA library function on the R
+// rows of a lane, kept out of line.  Inlined into every case (R copies of
+// the library's range handling each), it spread the interpreter's hot code
+// over more instruction-cache lines: 3 to 5 % slower per step.  The rows go
+// by value in a struct, so the caller's registers are not forced to memory.
+template <int R>
+struct ColdRows {
+  float v[R];
+};
+template <int U, int R>
+__device__ __noinline__ ColdRows<R> unop_cold(ColdRows<R> a) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) a.v[r] = unop<U>(a.v[r]);
+  return a;
+}
+template <int U, int R>
+__device__ __forceinline__ void unop_cold_rows(float (&A)[R]) {
+  ColdRows<R> t;
+#pragma unroll
+  for (int r = 0; r < R; ++r) t.v[r] = A[r];
+  t = unop_cold<U, R>(t);
+#pragma unroll
+  for (int r = 0; r < R; ++r) A[r] = t.v[r];
+}
+
+// sin and cos on the R rows of a lane: the branch-free form of gmath.cuh,
+// on row pairs as packed instructions when R is even.  One test over the R
+// rows sends an argument beyond the reduction's range (|x| > 2^17, inf,
+// NaN) to the library function on the cold path.  `shift` is 0 for sin and
+// 1 for cos (a run-time value in the interpreter: both share one body).
+template <int R>
+__device__ __forceinline__ void sincos_rows(float (&A)[R], int shift) {
+  bool big = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) big |= !(fabsf(A[r]) <= TRIG_RANGE);
+  if (__builtin_expect(big, 0)) {
+    if (shift) unop_cold_rows<U_COS, R>(A);
+    else unop_cold_rows<U_SIN, R>(A);
+  } else if constexpr (R % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const float2 v = sin_or_cos_reduced2(make_float2(A[2 * i], A[2 * i + 1]), shift);
+      A[2 * i] = v.x;
+      A[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[r] = sin_or_cos_reduced(A[r], shift);
+  }
+}
+
+// log (LOG) or sqrt on the R rows of a lane, after `mask` is applied to the
+// bits (0x7fffffff for log|x| and sqrt|x|, all ones for the unprotected
+// forms): the branch-free forms of gmath.cuh for positive normal finite
+// arguments, the library function on the cold path otherwise.
+template <int R, bool LOG>
+__device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
+  bool special = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    A[r] = __uint_as_float(__float_as_uint(A[r]) & mask);
+    special |= !positive_normal(A[r]);
+  }
+  if (__builtin_expect(special, 0)) {
+    if constexpr (LOG) unop_cold_rows<U_LOG, R>(A);
+    else unop_cold_rows<U_SQRT, R>(A);
+  } else if constexpr (R % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const float2 x = make_float2(A[2 * i], A[2 * i + 1]);
+      const float2 v = LOG ? log_normal2(x) : sqrt_newton2(x);
+      A[2 * i] = v.x;
+      A[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[r] = LOG ? log_normal(A[r]) : sqrt_newton(A[r]);
+  }
+}
+
+constexpr uint32_t ABS_MASK = 0x7fffffffu;
+
+// A unary operator on the R rows of a lane (compile-time operator; the
+// interpreter's switch calls the shared bodies above directly).  exp is the
+// library function.
 template <int U, int R>
 __device__ __forceinline__ void unop_rows(float (&A)[R]) {
-#ifdef GG_LIBM_TRIG
-  constexpr bool own_trig = false;
-#else
-  constexpr bool own_trig = true;
-#endif
-#ifdef GG_LIBM_SQRT
-  constexpr bool own = false;
-#else
-  constexpr bool own = true;
-#endif
-#ifdef GG_LIBM_LOG
-  constexpr bool own_log = false;
-#else
-  constexpr bool own_log = true;
-#endif
-  if constexpr (own_trig && (U == U_SIN || U == U_COS)) {
-    bool big = false;
-#pragma unroll
-    for (int r = 0; r < R; ++r) big |= fabsf(A[r]) > TRIG_RANGE;
-    if (__builtin_expect(big, 0)) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sinf(A[r]) : cosf(A[r]);
-    } else if constexpr (R % 2 == 0) {
-#pragma unroll
-      for (int i = 0; i < R / 2; ++i) {
-        const float2 v =
-            sin_or_cos_reduced2(make_float2(A[2 * i], A[2 * i + 1]), U == U_SIN ? 0 : 1);
-        A[2 * i] = v.x;
-        A[2 * i + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = U == U_SIN ? sin_reduced(A[r]) : cos_reduced(A[r]);
-    }
-  } else if constexpr (own_log && (U == U_LOG_ABS || U == U_LOG)) {
-    bool special = false;
-#pragma unroll
-    for (int r = 0; r < R; ++r) special |= !positive_normal(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
-    if (__builtin_expect(special, 0)) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = logf(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
-    } else if constexpr (R % 2 == 0) {
-#pragma unroll
-      for (int i = 0; i < R / 2; ++i) {
-        const float2 v = log_normal2(U == U_LOG_ABS
-                                         ? make_float2(fabsf(A[2 * i]), fabsf(A[2 * i + 1]))
-                                         : make_float2(A[2 * i], A[2 * i + 1]));
-        A[2 * i] = v.x;
-        A[2 * i + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = log_normal(U == U_LOG_ABS ? fabsf(A[r]) : A[r]);
-    }
-  } else if constexpr (own && (U == U_SQRT_ABS || U == U_SQRT)) {
-    bool special = false;
-#pragma unroll
-    for (int r = 0; r < R; ++r) special |= !positive_normal(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
-    if (__builtin_expect(special, 0)) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = sqrtf(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
-    } else if constexpr (R % 2 == 0) {
-#pragma unroll
-      for (int i = 0; i < R / 2; ++i) {
-        const float2 v = sqrt_newton2(U == U_SQRT_ABS
-                                          ? make_float2(fabsf(A[2 * i]), fabsf(A[2 * i + 1]))
-                                          : make_float2(A[2 * i], A[2 * i + 1]));
-        A[2 * i] = v.x;
-        A[2 * i + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < R; ++r) A[r] = sqrt_newton(U == U_SQRT_ABS ? fabsf(A[r]) : A[r]);
-    }
+  if constexpr (U == U_SIN || U == U_COS) {
+    sincos_rows<R>(A, U == U_COS);
+  } else if constexpr (U == U_LOG_ABS || U == U_LOG) {
+    logsqrt_rows<R, true>(A, U == U_LOG_ABS ? ABS_MASK : ~0u);
+  } else if constexpr (U == U_SQRT_ABS || U == U_SQRT) {
+    logsqrt_rows<R, false>(A, U == U_SQRT_ABS ? ABS_MASK : ~0u);
   } else if constexpr (U == U_SQUARE) {
     binop_rows<K_MUL, R>(A, A, A);
   } else {
@@ -298,14 +304,23 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
         sp += SLOT;
         GG_ROWS A[r] = c;
         break;
-      GG_UN(U_SIN)
-      GG_UN(U_COS)
+      // each pair of related operators shares one body (a run-time quadrant
+      // shift or sign mask): half the code in the switch, which is bound by
+      // instruction fetch as much as by issue (measured 1 to 9 % per step)
+      case I_UN + U_SIN:
+      case I_UN + U_COS:
+        sincos_rows<R>(A, (int)(opc - (I_UN + U_SIN)));
+        break;
+      case I_UN + U_LOG_ABS:
+      case I_UN + U_LOG:
+        logsqrt_rows<R, true>(A, opc == I_UN + U_LOG ? ~0u : ABS_MASK);
+        break;
+      case I_UN + U_SQRT_ABS:
+      case I_UN + U_SQRT:
+        logsqrt_rows<R, false>(A, opc == I_UN + U_SQRT ? ~0u : ABS_MASK);
+        break;
       GG_UN(U_EXP)
-      GG_UN(U_LOG_ABS)
-      GG_UN(U_SQRT_ABS)
       GG_UN(U_SQUARE)
-      GG_UN(U_LOG)
-      GG_UN(U_SQRT)
       GG_BIN(K_ADD)
       GG_BIN(K_SUB)
       GG_BIN(K_MUL)
