@@ -243,19 +243,22 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       t = __shfl_sync(0xffffffffu, t, 0);
       const int trial = g * p.group + t;
       if (t >= p.group || trial >= P) break;
-      const int L = p.len[trial];
-      if (L <= 0) continue;
       // stage the program with each feature field scaled to its tile offset;
       // a trial another tile has already found non-finite is skipped (its
-      // fitness is +inf whatever the other tiles hold)
-      const int dead = p.dead && lane == 0 ? p.dead[trial] : 0;
+      // fitness is +inf whatever the other tiles hold).  The first 32 words
+      // of the program slot are loaded together with the length and the
+      // flag, so that a program of up to 31 instructions costs one memory
+      // round trip; the rest of a longer one follows once L is known.
       const uint2* src = p.prog + (size_t)trial * p.lstride;
+      const uint2 w0 = lane < p.lstride ? src[lane] : make_uint2(0u, 0u);
+      const int L = p.len[trial];
+      const int dead = p.dead && lane == 0 ? p.dead[trial] : 0;
+      if (L <= 0 || __shfl_sync(0xffffffffu, dead, 0)) continue;
       for (int k = lane; k <= L; k += 32) {
-        uint2 w = src[k];
+        uint2 w = k < 32 ? w0 : src[k];
         w.x = (w.x & 0xffu) | (((w.x >> 8) * (uint32_t)p.tile_rows) << 8);
         wprog[k] = w;
       }
-      if (__shfl_sync(0xffffffffu, dead, 0)) continue;
       __syncwarp();
 
       float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f, fm = 0.f;
