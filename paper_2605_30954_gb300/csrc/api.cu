@@ -860,7 +860,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   else variants = {5, 1, 4, 0};
   std::vector<Cfg> cands;
   for (int v : variants)
-    for (int warps : {8, 16, 20, 24})
+    for (int warps : {8, 16, 20, 24, 28})
       for (int tmul : {2, 4, 8, 16})
         for (int gdiv : {1, 2}) {
           if (warps > gg::variant_max_warps(v)) continue;

@@ -100,16 +100,17 @@ __device__ __forceinline__ void unop_cold_rows(float (&A)[R]) {
 }
 
 // sin and cos on the R rows of a lane: the branch-free form of gmath.cuh,
-// on row pairs as packed instructions when R is even.  One test over the R
-// rows sends an argument beyond the reduction's range (|x| > 2^17, inf,
-// NaN) to the library function on the cold path.  `shift` is 0 for sin and
+// on row pairs as packed instructions when R is even.  One test of the
+// rows' largest magnitude sends a group with an argument beyond the
+// reduction's range (|x| > 2^17 or inf) to the library function on the
+// cold path (a NaN row stays on the fast path, whose result is NaN too).  `shift` is 0 for sin and
 // 1 for cos (a run-time value in the interpreter: both share one body).
 template <int R>
 __device__ __forceinline__ void sincos_rows(float (&A)[R], int shift) {
-  bool big = false;
+  float mx = fabsf(A[0]);
 #pragma unroll
-  for (int r = 0; r < R; ++r) big |= !(fabsf(A[r]) <= TRIG_RANGE);
-  if (__builtin_expect(big, 0)) {
+  for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
+  if (__builtin_expect(!(mx <= TRIG_RANGE), 0)) {
     if (shift) unop_cold_rows<U_COS, R>(A);
     else unop_cold_rows<U_SIN, R>(A);
   } else if constexpr (R % 2 == 0) {
@@ -134,8 +135,9 @@ __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
   bool special = false;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    A[r] = __uint_as_float(__float_as_uint(A[r]) & mask);
-    special |= !positive_normal(A[r]);
+    const uint32_t b = __float_as_uint(A[r]) & mask;
+    A[r] = __uint_as_float(b);
+    special |= outside_positive_normal(b);
   }
   if (__builtin_expect(special, 0)) {
     if constexpr (LOG) unop_cold_rows<U_LOG, R>(A);
