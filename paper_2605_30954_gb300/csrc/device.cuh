@@ -229,9 +229,10 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
 // shared memory: `stk` is this lane's entry in slot 0 (slot j at
 // stk + 32 R j), so a push or a pop is one R-float shared-memory access per
 // lane.  The first instruction of every program loads A without a push.
-// With PRESCALED the feature field of each word already holds the
-// feature's offset in floats (feature x ts), as the batched kernel rewrites
-// it when it stages a program.  With TAPE the R values of A after
+// With PRESCALED the words are in the staged form the batched kernel
+// writes: .x holds the opcode alone and, for an instruction that reads a
+// feature, .y holds the feature's offset in floats (feature x ts) in place
+// of the unused constant, so the decode needs neither a mask nor a shift.  With TAPE the R values of A after
 // instruction k are stored at tape[32 R k] (the caller offsets `tape` by its
 // lane's R rows): the forward half of the adjoint.  POW adds the pow
 // instructions; without it the program must not contain them.
@@ -246,8 +247,8 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     // the first instruction is always I_LDF0 or I_LDC0 (the packers emit a
     // load without a push exactly there), so it is peeled off the switch
     const uint2 first = prog[0];
-    if ((first.x & 0xffu) == I_LDF0) {
-      load_rows<R>(PRESCALED ? xs + (first.x >> 8) : xs + (first.x >> 8) * ts, A);
+    if ((PRESCALED ? first.x : first.x & 0xffu) == I_LDF0) {
+      load_rows<R>(PRESCALED ? xs + first.y : xs + (first.x >> 8) * ts, A);
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = __uint_as_float(first.y);
@@ -257,9 +258,9 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
   uint2 ins = prog[1];
   for (int k = 1; k < L; ++k) {
     const uint2 nxt = prog[k + 1];
-    const uint32_t opc = ins.x & 0xffu;
+    const uint32_t opc = PRESCALED ? ins.x : ins.x & 0xffu;
     const float c = __uint_as_float(ins.y);
-    const float* xf = PRESCALED ? xs + (ins.x >> 8) : xs + (ins.x >> 8) * ts;
+    const float* xf = PRESCALED ? xs + ins.y : xs + (ins.x >> 8) * ts;
     float t[R];
 
 #define GG_ROWS _Pragma("unroll") for (int r = 0; r < R; ++r)

@@ -71,6 +71,12 @@ enum : uint32_t {
   I_COUNT = 49
 };
 
+// The instructions that read a feature (all opcodes are below 64).
+constexpr uint64_t FEATURE_OPS =
+    (1ull << I_LDF0) | (1ull << I_PSF) | (0x1full << I_BF) | (0x1full << I_LF) |
+    (1ull << (I_PW + 0)) | (1ull << (I_PW + 2));
+GG_HD bool reads_feature(uint32_t opc) { return opc < 64 && ((FEATURE_OPS >> opc) & 1u); }
+
 // Opcode of a binary node with a fused terminal: group 0 BF, 1 BC, 2 LF, 3 LC.
 GG_HD uint32_t fused_opcode(int group, int kind) {
   return kind == K_POW ? I_PW + (uint32_t)group : I_BF + (uint32_t)(group * NKIND + kind);

@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       t = __shfl_sync(0xffffffffu, t, 0);
       const int trial = g * p.group + t;
       if (t >= p.group || trial >= P) break;
-      // stage the program with each feature field scaled to its tile offset;
+      // stage the program: the opcode alone in .x and, for an instruction
+      // that reads a feature, the feature's offset in the tile in .y;
       // a trial another tile has already found non-finite is skipped (its
       // fitness is +inf whatever the other tiles hold).  The first 32 words
       // of the program slot are loaded together with the length and the
@@ -259,7 +260,9 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       if (L <= 0 || __shfl_sync(0xffffffffu, dead, 0)) continue;
       for (int k = lane; k <= L; k += 32) {
         uint2 w = k < 32 ? w0 : src[k];
-        w.x = (w.x & 0xffu) | (((w.x >> 8) * (uint32_t)p.tile_rows) << 8);
+        const uint32_t op = w.x & 0xffu;
+        if (reads_feature(op)) w.y = (w.x >> 8) * (uint32_t)p.tile_rows;
+        w.x = op;
         wprog[k] = w;
       }
       __syncwarp();
