@@ -862,7 +862,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   for (int v : variants)
     for (int warps : {8, 16, 20, 24, 28})
       for (int tmul : {2, 4, 8, 16})
-        for (int gdiv : {1, 2}) {
+        for (int gq : {1, 2, 4}) {  // items per SM: 16, 32, 64
           if (warps > gg::variant_max_warps(v)) continue;
           Cfg c;
           c.variant = v;
@@ -871,7 +871,7 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
           if (c.tile_rows > 2 * ds->N + 256) continue;
           const int n_tiles = (int)((ds->N + c.tile_rows - 1) / c.tile_rows);
           const double target = 32.0 * ds->sms;
-          long long ng = (long long)std::ceil(target * gdiv / n_tiles);
+          long long ng = (long long)std::ceil(target * gq / 2 / n_tiles);
           if (ng < 1) ng = 1;
           if (ng > b->n) ng = b->n;
           c.group = (int)((b->n + ng - 1) / ng);
