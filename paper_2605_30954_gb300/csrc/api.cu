@@ -126,7 +126,7 @@ struct ggeval_dataset {
   int F = 0, ldx = 0;
   size_t smem_optin = 0;
   float* X = nullptr;        // [F + 1][ldx], row F = y - mean(y)
-  double* pref = nullptr;    // [N + 1] prefix sums of the stored centred target
+  float2* pref = nullptr;    // [N + 1] prefix sums of the stored centred target (hi, lo)
   double ybar = 0, syc = 0, sycyc = 0;
   cudaStream_t cap_stream = nullptr;
   // workspace (grown on demand)
@@ -492,6 +492,12 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
   }
   ds->syc = pref[N];
   ds->sycyc = s2;
+  // the prefix sums as FP32 (hi, lo) pairs: the finaliser merges in FP32
+  std::vector<float2> pref2((size_t)N + 1);
+  for (size_t i = 0; i <= (size_t)N; ++i) {
+    const float hi = (float)pref[i];
+    pref2[i] = make_float2(hi, (float)(pref[i] - (double)hi));
+  }
   auto cleanup = [&](ggeval_status s) {
     ggeval_destroy(ds);
     return s;
@@ -531,7 +537,7 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
     if ((e = cudaMemcpyAsync(ds->X + (size_t)F * ds->ldx, yh.data(), (size_t)N * 4,
                              cudaMemcpyHostToDevice, st)))
       break;
-    if ((e = cudaMemcpyAsync(ds->pref, pref.data(), ((size_t)N + 1) * 8, cudaMemcpyHostToDevice,
+    if ((e = cudaMemcpyAsync(ds->pref, pref2.data(), ((size_t)N + 1) * 8, cudaMemcpyHostToDevice,
                              st)))
       break;
     e = cudaStreamSynchronize(st);

@@ -349,7 +349,7 @@ struct FinParams {
   const int* len;
   int P, n_tiles, tile_rows;
   long long N;
-  const double* pref;  // [N + 1] prefix sums of the stored centred target
+  const float2* pref;  // [N + 1] prefix sums of the stored centred target (FP32 hi, lo)
   double ybar, syc, sycyc;
   float* smse;
   float* a;

@@ -4,8 +4,33 @@
 
 namespace gg {
 
+// Double-float (FP32 hi + lo) products for the finaliser's tile merge; the
+// sums use dd_add.  The merge runs in FP32 arithmetic: GB300's FP64 pipe is
+// narrow, and merging the tile records in FP64 kept it 72 % busy for the
+// whole launch (38 us on 4,096 trials x 49 tiles).
+__device__ __forceinline__ float2 df_mulf(float2 a, float b) {
+  const float p = a.x * b;
+  float e = fmaf(a.x, b, -p);
+  e = fmaf(a.y, b, e);
+  const float h = p + e;
+  return make_float2(h, e - (h - p));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float h = p + e;
+  return make_float2(h, e - (h - p));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  dd_add(a.x, a.y, b.x, b.y);
+  return a;
+}
+
 __global__ void fin_kernel(const FinParams p) {
-  __shared__ double red[FIN_WARPS][5];  // cst, S_d, S_dd, S_dy, max|f|
+  // per warp: cst, (hi, lo) of S_d, S_dd, S_dy, max|f| (FP32; phase 2 widens)
+  __shared__ float red[FIN_WARPS][8];
   __shared__ int lens[FIN_WARPS];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -17,41 +42,50 @@ __global__ void fin_kernel(const FinParams p) {
     // found non-finite by the forward kernel, which skipped its later tiles:
     // +inf fitness without the (incomplete) tile records
     if (lane == 0) {
-      red[warp][0] = red[warp][1] = red[warp][2] = red[warp][3] = 0.0;
-      red[warp][4] = __longlong_as_double(0x7ff0000000000000LL);
+      for (int k = 0; k < 7; ++k) red[warp][k] = 0.f;
+      red[warp][7] = __int_as_float(0x7f800000);
     }
   } else if (len > 0) {
+    // every tile's sums move from its own shift c_t to the first tile's
+    // (cst): with del = c_t - cst (exact as a double-float),
+    //   S_d += n del,  S_dd += 2 del S_d + n del^2,  S_dy += del S_yc(tile)
     const float* q = p.part + (size_t)t * p.n_tiles * NPART;
-    const double cst = q[0];
-    double sd = 0.0, sdd = 0.0, sdy = 0.0, fm = 0.0;
+    const float cst = q[0];
+    float2 sd = make_float2(0.f, 0.f), sdd = sd, sdy = sd;
+    float fm = 0.f;
     for (int i = lane; i < p.n_tiles; i += 32) {
-      const float* u = q + (size_t)i * NPART;
+      const float4* u = reinterpret_cast<const float4*>(q + (size_t)i * NPART);
+      const float4 u0 = u[0], u1 = u[1];  // c_t, S_d, S_d lo, S_dd | S_dd lo, S_dy, S_dy lo, max
       const long long r0 = (long long)i * p.tile_rows;
       const long long r1 = min(p.N, r0 + p.tile_rows);
-      const double n = (double)(r1 - r0);
-      const double del = (double)u[0] - cst;
-      const double syt = p.pref[r1] - p.pref[r0];
-      const double a1 = (double)u[1] + (double)u[2];
-      const double a2 = (double)u[3] + (double)u[4];
-      const double a3 = (double)u[5] + (double)u[6];
-      sd += a1 + n * del;
-      sdd += a2 + 2.0 * del * a1 + n * del * del;
-      sdy += a3 + del * syt;
-      fm = fmax(fm, (double)u[7]);
+      const float n = (float)(r1 - r0);
+      float dh, dl;
+      two_sum(u0.x, -cst, dh, dl);
+      const float2 del = make_float2(dh, dl);
+      const float2 tsd = make_float2(u0.y, u0.z), tsdd = make_float2(u0.w, u1.x),
+                   tsdy = make_float2(u1.y, u1.z);
+      const float2 a = p.pref[r1], b = p.pref[r0];
+      const float2 syt = df_add(a, make_float2(-b.x, -b.y));
+      const float2 nd = df_mulf(del, n);
+      sd = df_add(sd, df_add(tsd, nd));
+      sdd = df_add(sdd, df_add(tsdd, df_add(df_mulf(df_mul(del, tsd), 2.f), df_mul(nd, del))));
+      sdy = df_add(sdy, df_add(tsdy, df_mul(del, syt)));
+      fm = fmaxf(fm, u1.w);
     }
+    warp_dd_sum(sd.x, sd.y);
+    warp_dd_sum(sdd.x, sdd.y);
+    warp_dd_sum(sdy.x, sdy.y);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sd += __shfl_xor_sync(0xffffffffu, sd, o);
-      sdd += __shfl_xor_sync(0xffffffffu, sdd, o);
-      sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
-      fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
-    }
+    for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
     if (lane == 0) {
       red[warp][0] = cst;
-      red[warp][1] = sd;
-      red[warp][2] = sdd;
-      red[warp][3] = sdy;
-      red[warp][4] = fm;
+      red[warp][1] = sd.x;
+      red[warp][2] = sd.y;
+      red[warp][3] = sdd.x;
+      red[warp][4] = sdd.y;
+      red[warp][5] = sdy.x;
+      red[warp][6] = sdy.y;
+      red[warp][7] = fm;
     }
   }
   if (lane == 0) lens[warp] = len;
@@ -68,8 +102,11 @@ __global__ void fin_kernel(const FinParams p) {
   if (!valid) {
     smse = a = b = mse = nan;
   } else {
-    const double cst = red[lane][0], sd = red[lane][1], sdd = red[lane][2], sdy = red[lane][3];
-    const double fm = red[lane][4];
+    const double cst = red[lane][0];
+    const double sd = (double)red[lane][1] + (double)red[lane][2];
+    const double sdd = (double)red[lane][3] + (double)red[lane][4];
+    const double sdy = (double)red[lane][5] + (double)red[lane][6];
+    const double fm = red[lane][7];
     const double N = (double)p.N;
     const bool finite = isfinite(sd) && isfinite(sdd) && isfinite(sdy) && isfinite(cst) &&
                         fm <= (double)OUT_BIG;
