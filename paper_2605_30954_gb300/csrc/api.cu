@@ -312,6 +312,26 @@ ggeval_status launch(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStr
   return GGEVAL_OK;
 }
 
+// A launch that may start before the kernel ahead of it in the stream has
+// finished (programmatic dependent launch): the kernel waits for it with
+// griddepcontrol.wait before it reads that kernel's output.
+ggeval_status launch_overlapped(const void* fn, dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t st, void* params) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {params};
+  GG_CU(cudaLaunchKernelExC(&cfg, fn, args));
+  return GGEVAL_OK;
+}
+
 ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_max, int layout,
                            const Plan& pl, bool with_aux, cudaStream_t st,
                            const int* count = nullptr, const int* idx = nullptr) {
@@ -424,14 +444,17 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
     ev = &ds->prof_ev[ds->prof_used++];
     GG_CU(cudaEventRecord(ev->first, st));
   }
-  GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+  // the forward kernel overlaps the packer's tail and the finaliser the
+  // forward kernel's (not when a profiling event sits between them)
+  if (ev) GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
+  else GG_TRY(launch_overlapped(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
   q.dead = fp.dead;
   q.count = count;
   q.idx = idx;
-  GG_TRY(launch(gg::fin_ptr(), dim3((n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
-                dim3(32 * gg::FIN_WARPS), 0, st, &q));
+  GG_TRY(launch_overlapped(gg::fin_ptr(), dim3((n + gg::FIN_WARPS - 1) / gg::FIN_WARPS),
+                           dim3(32 * gg::FIN_WARPS), 0, st, &q));
   return GGEVAL_OK;
 }
 

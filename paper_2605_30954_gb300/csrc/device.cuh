@@ -445,6 +445,19 @@ __device__ __forceinline__ void warp_dd_sum(float& hi, float& lo) {
   }
 }
 
+// ------------------------------------------ programmatic dependent launch
+// A kernel launched with the programmatic-serialisation attribute may start
+// while the kernel ahead of it in the stream is still running.
+// grid_dependency_wait() blocks until that kernel has completed and its
+// writes are visible (a no-op for a kernel launched without the attribute);
+// allow_dependents() lets the kernel behind this one start launching.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // -------------------------------------------------- mbarrier and bulk copy
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -211,16 +211,22 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
   uint64_t* bar = reinterpret_cast<uint64_t*>(progs + (size_t)nw * p.lstride);
   int* ctl = reinterpret_cast<int*>(bar + 2);
 
+  // the finaliser behind this kernel may launch now: it waits for this
+  // grid to complete before it reads anything
+  allow_dependents();
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     for (int i = 0; i < 8; ++i) ctl[i] = 0;
   }
   __syncthreads();
+  // the first two tiles read only the dataset and the work counter (zeroed
+  // before the packer ran), so they load while the packer may still run
   if (warp == 0) {
     produce_tile(p, n_items, 0, xsb, &bar[0], ctl, lane);
     produce_tile(p, n_items, 1, xsb + tile_floats, &bar[1], ctl + 4, lane);
   }
+  grid_dependency_wait();  // the packer's programs and lengths
 
   float A[R];
 #pragma unroll

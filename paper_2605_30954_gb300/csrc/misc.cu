@@ -36,6 +36,7 @@ __global__ void fin_kernel(const FinParams p) {
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int t = blockIdx.x * nw + warp;  // slot (= trial unless compacted)
+  grid_dependency_wait();  // the forward kernel's records and flags
   const int P = p.count ? min(*p.count, p.P) : p.P;
   const int len = t < P ? p.len[t] : 0;
   if (len > 0 && p.dead && p.dead[t]) {

@@ -64,6 +64,7 @@ constexpr uint8_t N_FUSED = 32;   // terminal fused into its parent's instructio
 
 __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams p) {
   extern __shared__ __align__(16) unsigned char pk_smem[];
+  allow_dependents();  // the forward kernel's prologue needs nothing from here
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int t = blockIdx.x * PACK_WARPS + warp;  // the program slot
