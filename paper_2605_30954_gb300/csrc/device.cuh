@@ -1,6 +1,7 @@
 // Device-side building blocks shared by the kernels: the operators, the
 // stack-machine interpreter (top of stack in registers, the rest in shared
-// memory), error-free FP32 summation, and the mbarrier / bulk-copy PTX.
+// memory), error-free FP32 summation, and the PTX of programmatic launch,
+// mbarriers and bulk copies.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

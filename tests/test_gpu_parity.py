@@ -30,7 +30,9 @@ def dev(a, dtype=None):
     return t.cuda() if dtype is None else t.to(dtype).cuda()
 
 
-def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0):
+def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0, tuned=False):
+    """tuned: the launch configuration the benchmark times (autotuned tile
+    shape, CUDA graph replay on a side stream)."""
     X = torch.from_numpy(w["X"])
     y = torch.from_numpy(w["y"])
     ds = gg.Dataset(X, y)
@@ -38,7 +40,16 @@ def run_case(gg, w, sample=None, flags=0, check_rows=True, layout=0):
     hs = dev(w["heights"]) if len(set(w["heights"].tolist())) > 1 else None
     if w.get("uses_pow"):
         flags |= gg.F_POW
-    smse, a, b, mse = ds.eval_batch(op, cv, hs, layout=layout, flags=flags)
+    if tuned:
+        ds.autotune(op, cv, hs, layout=layout, flags=flags)
+        st = torch.cuda.Stream()
+        outs = [torch.full((w["P"],), -7.0, device="cuda") for _ in range(4)]
+        for _ in range(2):  # the second call replays the captured graph
+            ds.eval_batch(op, cv, hs, layout=layout, flags=flags | gg.F_GRAPH, stream=st, out=outs)
+        st.synchronize()
+        smse, a, b, mse = outs
+    else:
+        smse, a, b, mse = ds.eval_batch(op, cv, hs, layout=layout, flags=flags)
     idx = range(w["P"]) if sample is None else sample
     rows = None
     if check_rows:
@@ -351,12 +362,15 @@ def test_max_height_and_feature_counts(gg, h, nf):
 FULL = [("c1", None), ("c2", 24), ("c3", 24), ("c4", 24), ("c5", 12), ("t2", 24)]
 
 
+@pytest.mark.parametrize("tuned", [False, True])
 @pytest.mark.parametrize("cfg,n_sample", FULL)
-def test_full_size_config_sampled(gg, cfg, n_sample):
+def test_full_size_config_sampled(gg, cfg, n_sample, tuned):
+    if tuned and cfg == "c4":
+        pytest.skip("the gradient workload's benchmark times the gradient path (test_gpu_grad)")
     w = PA.build(cfg)
     sample = None
     if n_sample is not None:
         sample = np.random.default_rng(7).choice(w["P"], n_sample, replace=False).tolist()
-    tr, tf, outs = run_case(gg, w, sample=sample, check_rows=False)
+    tr, tf, outs = run_case(gg, w, sample=sample, check_rows=False, tuned=tuned)
     assert_tally(tf, min_checked=(n_sample or w["P"]) // 2, max_excl=0.25)
     assert np.sum(np.isnan(outs[0])) == 0
