@@ -390,18 +390,20 @@ def run_extra_mode(a, gg, torch):
         changed_total = torch.zeros((), dtype=torch.int64, device="cuda")
 
         def sweep():
+            chs = []  # each step's changed flags (distinct buffers), counted once per sweep
             for i in range(stride):
                 gg.gom_donate(O_op, O_cv, pop_op, pop_cv, donors[i], order[i], off_d, nodes_d,
                               stream=st)
                 ch = gg.gom_changed(O_op, O_cv, B_op, B_cv, w["F"], hs, stream=st)
-                changed_total.add_(ch.sum())
+                chs.append(ch)
                 ds.eval_batch_masked(O_op, O_cv, ch, hs, flags=PF, stream=st,
                                      out=[f_new, None, None, None])
                 gg.gom_accept(O_op, O_cv, B_op, B_cv, f_new, f_b, ch, stream=st)
+            changed_total.add_(torch.stack(chs).sum())
         with torch.cuda.stream(st):
             sweep()  # sizes the workspace and tunes the plan outside the capture
         st.synchronize()
-        # the whole sweep (31 GOM steps, about 280 launches) as one CUDA graph
+        # the whole sweep (31 GOM steps, about 220 launches) as one CUDA graph
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=st):
             sweep()
