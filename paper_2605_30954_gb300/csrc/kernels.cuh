@@ -202,7 +202,17 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
   // trials (slots) to evaluate and the work items they make: a masked
   // evaluation sets the count on the device (compacted changed trials)
   const int P = p.count ? min(*p.count, p.P) : p.P;
-  const int n_items = p.count ? p.n_tiles * ((P + p.group - 1) / p.group) : p.n_items;
+  // a masked evaluation has fewer trials than the plan was sized for: its
+  // groups shrink so that the work items still cover every CTA 16 times,
+  // but keep three trials per warp (with fewer, warps that finish early
+  // wait for the slowest before the tile buffer is refilled)
+  int group = p.group;
+  if (p.count) {
+    const long long target = 16LL * gridDim.x;
+    const int want = (int)(((long long)P * p.n_tiles + target - 1) / target);
+    group = min(p.group, max(3 * nw, want));
+  }
+  const int n_items = p.count ? p.n_tiles * ((P + group - 1) / group) : p.n_items;
   float* xsb = reinterpret_cast<float*>(smem);  // two tile buffers
   float* stacks = xsb + 2 * tile_floats;
   float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * R;  // this lane, slot 0
@@ -250,8 +260,8 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       int t = 0;
       if (lane == 0) t = atomicAdd(&c[1], 1);
       t = __shfl_sync(0xffffffffu, t, 0);
-      const int trial = g * p.group + t;
-      if (t >= p.group || trial >= P) break;
+      const int trial = g * group + t;
+      if (t >= group || trial >= P) break;
       // stage the program: the opcode alone in .x and, for an instruction
       // that reads a feature, the feature's offset in the tile in .y;
       // a trial another tile has already found non-finite is skipped (its
