@@ -207,8 +207,8 @@ ggeval_status ggeval_adam_step(const ggeval_batch* batch, float* cval, const flo
                                float* m, float* v, int32_t t, float lr, float beta1,
                                float beta2, float eps, void* stream);
 
-/* Time candidate tile shapes (rows per tile, trials per work item, rows per
- * lane, register budget) on this batch and keep the fastest for batches of
+/* Time candidate tile shapes (rows per tile, trials per work item, warps per
+ * CTA, rows per lane, register budget) on this batch and keep the fastest for batches of
  * the same shape (n, max_height, layout, flags).  Synchronises the stream;
  * runs the evaluation several times.  Device batches only.  With the
  * environment variable GGEVAL_VERBOSE set (not "0") every candidate's time
