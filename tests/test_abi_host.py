@@ -98,6 +98,11 @@ def test_packed_programs_compute_the_oracle_value(gg, h, layout):
             np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300, equal_nan=True)
             assert slots <= max(h - 1, 0)
             assert len(words) <= int(O.active_mask(t).sum())
+            # a load without a push comes first and nowhere else (the
+            # interpreter decides the first instruction before its switch)
+            opc = np.asarray(words) & 0xFF
+            assert opc[0] in (emu.I_LDF0, emu.I_LDC0)
+            assert not np.isin(opc[1:], (emu.I_LDF0, emu.I_LDC0)).any()
 
 
 def folded_nodes(t):
