@@ -77,6 +77,8 @@ def test_folded_programs(gg, layout):
         np.testing.assert_array_equal(L, st[:, 24])
         shorter += int(np.sum(st[:, 24] < st[:, 10]))
         for p in range(op.shape[0]):  # a load without a push first, and only there
+            if L[p] <= 0:
+                continue
             opc = w[p, :L[p]] & 0xFF
             assert opc[0] in (emu.I_LDF0, emu.I_LDC0)
             assert not np.isin(opc[1:], (emu.I_LDF0, emu.I_LDC0)).any()
