@@ -1,0 +1,316 @@
+"""Parity checks: build a seeded workload with its target from the oracle,
+and compare library outputs with the oracle under the stated tolerances.
+
+Test infrastructure, like the rest of this package: the GPU tests and the
+benchmark's oracle leg use it; the library never does.
+
+Tolerances (from the accuracy targets of this evaluator):
+  per row   |g - r| <= 1e-5 (|r| + rms(r))      rms over the trial's rows
+  smse      |g - r| <= 1e-4 r + 1e-8 Var(y)
+  mse       |g - r| <= 1e-4 r + 1e-8 (mean y^2 + mean f^2)
+  gradient  |g - r| <= 1e-3 (|r| + 1e-3 max_k |r_k|) + 1e-6 G_k, G_k the
+            oracle's scale of the FP32 row terms (oracle.grad with_abs)
+A row is ill-conditioned in FP32, and excluded, when its FP32-emulated
+oracle value or the first-order bound on the effect of relative errors of
+4 FP32 units in the last place at every function node
+(oracle.condition_bound) exceeds half of its tolerance, or when FP32
+rounding may turn it NaN (oracle.pow_ambiguous_rows: a negative base to an
+exponent next to an integer; its trial is excluded too).  A trial is
+excluded when the same bound, carried to its smse (or mse), exceeds half
+of that tolerance, or when its FP64 and FP32-emulated fitness
+disagree on being infinite (ambiguous).  Both counts are reported.
+"""
+import math
+
+import numpy as np
+
+import synth
+
+from . import gp as O
+
+ROW_TOL = 1e-5
+SMSE_RTOL, SMSE_FLOOR = 1e-4, 1e-8
+GRAD_TOL = 1e-3
+COND_MARGIN = 0.5
+
+
+def target_from_oracle(w):
+    """First candidate generator tree with finite values, nonzero variance
+    and |f| <= 1e6 (the oracle evaluates it), plus the workload's noise."""
+    for gop, gcv, gh in w["y_cands"]():
+        f = O.eval_tree(O.Template(gop, gcv, gh, "heap", w["F"]), w["X"])
+        with np.errstate(all="ignore"):
+            if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
+                return synth.make_target(f, w["z"], w["noise"]), (gop, gcv, gh)
+    raise RuntimeError("no usable generator tree")
+
+
+def build(cfg, n_rows=None, n_trials=None, rep=0, layout="heap"):
+    w = synth.workload(cfg, rep, n_rows, n_trials, layout)
+    if "y" not in w:
+        w["y"], w["gen"] = target_from_oracle(w)
+    return w
+
+
+def template(w, p):
+    h = int(w["heights"][p])
+    return O.Template(w["op"][p], w["cval"][p], h, w["layout"], w["F"])
+
+
+class Tally:
+    def __init__(self):
+        self.checked = self.excluded = self.failed = 0
+        self.worst = 0.0
+        self.msgs = []
+
+    def __repr__(self):
+        return (f"checked={self.checked} excluded={self.excluded} failed={self.failed} "
+                f"worst={self.worst:.3g} {self.msgs[:5]}")
+
+    def merge(self, other):
+        self.checked += other.checked
+        self.excluded += other.excluded
+        self.failed += other.failed
+        self.worst = max(self.worst, other.worst)
+        self.msgs.extend(other.msgs)
+        return self
+
+    def excluded_frac(self):
+        n = self.checked + self.excluded
+        return self.excluded / n if n else 0.0
+
+    def as_dict(self):
+        return {"checked": self.checked, "excluded": self.excluded, "failed": self.failed,
+                "worst_err_over_tol": self.worst}
+
+
+def value_class(v):
+    """0 finite, 1 NaN, 2 +inf, 3 -inf."""
+    v = np.asarray(v, dtype=np.float64)
+    return np.where(np.isnan(v), 1, np.where(v == np.inf, 2, np.where(v == -np.inf, 3, 0)))
+
+
+def check_rows(g, f64, f32, tally, tag="", cond=None):
+    """Per-row values of one trial.  ``cond``: per-row error bound
+    (oracle.condition_bound) used with f32 to flag ill-conditioned rows.
+    A row that is non-finite in the oracle's FP64 and FP32 passes alike
+    (both NaN, or the same infinity) must be that on the GPU too; a row on
+    which the two passes disagree is excluded."""
+    with np.errstate(all="ignore"):
+        fin = np.isfinite(f64)
+        rms = math.sqrt(np.mean(f64[fin] ** 2)) if fin.any() else 0.0
+        tol = ROW_TOL * (np.abs(f64) + rms)
+        err32 = np.abs(f32.astype(np.float64) - f64)
+        c64, c32, cg = value_class(f64), value_class(f32), value_class(g)
+        amb = np.isnan(cond) if cond is not None else np.zeros(f64.shape, dtype=bool)
+        special = (c64 != 0) & (c64 == c32) & ~amb
+        ill = ~special & (~fin | (c32 != 0) | (err32 > COND_MARGIN * tol))
+        if cond is not None:
+            ill |= amb | (fin & ~(cond <= COND_MARGIN * tol))
+        err = np.where(special, 0.0, np.abs(g.astype(np.float64) - f64))
+        bad = ~ill & np.where(special, cg != c64, ~(err <= tol))
+    tally.checked += int((~ill).sum())
+    tally.excluded += int(ill.sum())
+    if bad.any():
+        tally.failed += int(bad.sum())
+        i = int(np.argmax(np.where(bad, err / np.maximum(tol, 1e-300), 0)))
+        tally.msgs.append(f"{tag} row {i}: gpu {g[i]!r} oracle {f64[i]!r}")
+    ok = ~ill
+    if ok.any():
+        tally.worst = max(tally.worst, float(np.max(err[ok] / np.maximum(tol[ok], 1e-300))))
+
+
+def fit_bounds(f64, y, fit64, cond):
+    """Bounds on the change of smse and mse when every row value moves by at
+    most cond_i: (1/N) sum (2 |r_i| e_i + e_i^2) with r_i the residual of
+    the scaled (b e_i) or plain fit."""
+    y = np.asarray(y, dtype=np.float64)
+    with np.errstate(all="ignore"):
+        r = y - fit64["a"] - fit64["b"] * f64
+        e = np.abs(fit64["b"]) * cond
+        ds = float(np.mean(2 * np.abs(r) * e + e * e))
+        rm = f64 - y
+        dm = float(np.mean(2 * np.abs(rm) * cond + cond * cond))
+    return ds, dm
+
+
+def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", bounds=None):
+    """smse (and mse) of one trial.  ``bounds``: (smse, mse) change bounds
+    from fit_bounds, used with fit32 to flag ill-conditioned trials."""
+    inf64 = not fit64["finite"]
+    inf32 = not fit32["finite"]
+    if bounds is not None and np.isnan(bounds[0]):  # a row FP32 rounding may turn NaN
+        tally.excluded += 1
+        return
+    if inf64 != inf32 or (bounds is not None and not inf64 and not np.isfinite(bounds[0])):
+        tally.excluded += 1
+        return
+    if inf64:
+        tally.checked += 1
+        if not (math.isinf(g_smse) and g_smse > 0):
+            tally.failed += 1
+            tally.msgs.append(f"{tag}: oracle +inf, gpu {g_smse}")
+        return
+    r = fit64["smse"]
+    tol = SMSE_RTOL * r + SMSE_FLOOR * var_y
+    if (abs(fit32["smse"] - r) > COND_MARGIN * tol or (fit64["b"] == 0.0) != (fit32["b"] == 0.0)
+            or (bounds is not None and not bounds[0] <= COND_MARGIN * tol)):
+        tally.excluded += 1
+        return
+    tally.checked += 1
+    err = abs(g_smse - r)
+    # a zero tolerance (one row, or a constant target) asks for the exact value
+    tally.worst = max(tally.worst, err / tol if tol > 0 else (0.0 if err == 0 else math.inf))
+    if not err <= tol:
+        tally.failed += 1
+        tally.msgs.append(f"{tag}: smse gpu {g_smse!r} oracle {r!r} tol {tol:.3g}")
+    if g_mse is not None:
+        rm = fit64["mse"]
+        tm = SMSE_RTOL * rm + SMSE_FLOOR * mean_y2
+        well = abs(fit32["mse"] - rm) <= COND_MARGIN * tm and (
+            bounds is None or bounds[1] <= COND_MARGIN * tm)
+        if well and not abs(g_mse - rm) <= tm:
+            tally.failed += 1
+            tally.msgs.append(f"{tag}: mse gpu {g_mse!r} oracle {rm!r}")
+
+
+#: relative error assumed at every function node: 4 FP32 units in the last place
+COND_REL = 4 * 2.0 ** -24
+
+
+def oracle_trial(w, p, X=None, y=None):
+    """Oracle data of trial p: template, FP64 rows, FP32-emulated rows,
+    their fitness, the per-row condition bound and the fitness bounds."""
+    X = w["X"] if X is None else X
+    y = w["y"] if y is None else y
+    t = template(w, p)
+    f64 = O.eval_tree(t, X)
+    f32 = O.eval_tree_f32(t, X)
+    fit64 = O.fitness(f64, y)
+    cond = O.condition_bound(t, X, COND_REL)
+    bounds = fit_bounds(f64, y, fit64, cond) if fit64["finite"] else None
+    if np.any(t.op[O.active_mask(t)] == O.POW):
+        amb = O.pow_ambiguous_rows(t, X)
+        if amb.any():  # NaN marks rows (and the trial) whose finiteness FP32 decides
+            cond = np.where(amb, np.nan, cond)
+            bounds = (math.nan, math.nan)
+    return t, f64, f32, fit64, O.fitness(f32.astype(np.float64), y), cond, bounds
+
+
+def intermediates_finite_f32(t, X):
+    """True if every active node of the FP32-emulated evaluation is finite."""
+    store = {}
+    O._eval(t, np.asarray(X, dtype=np.float32), np.float32, store=store)
+    with np.errstate(all="ignore"):
+        return all(np.all(np.isfinite(v)) for v in store.values())
+
+
+#: FP32 floor of the gradient test, relative to the size of the terms the
+#: FP32 residual a + b f - y is made of: a gradient that is 0 (or small) by
+#: an invariance is a cancelling FP32 sum of such terms
+GRAD_FLOOR = 1e-6
+
+
+def floor_only_entries(g, r, rabs):
+    """Gradient entries inside the tolerance only because of its FP32 floor
+    term GRAD_FLOOR * G_k (outside 1e-3 (|r| + 1e-3 max|r|))."""
+    scale = 1e-3 * float(np.max(np.abs(r))) if r.size else 0.0
+    base = GRAD_TOL * (np.abs(r) + scale)
+    err = np.abs(np.asarray(g, dtype=np.float64) - r)
+    return int(np.sum((err > base) & (err <= base + GRAD_FLOOR * rabs)))
+
+
+def check_grad(g, r, tally, tag="", rabs=None):
+    scale = 1e-3 * float(np.max(np.abs(r))) if r.size else 0.0
+    tol = GRAD_TOL * (np.abs(r) + scale)
+    if rabs is not None:
+        tol = tol + GRAD_FLOOR * rabs
+    err = np.abs(g.astype(np.float64) - r)
+    tally.checked += 1
+    with np.errstate(all="ignore"):
+        ratio = np.where(tol > 0, err / np.maximum(tol, 1e-300), np.where(err > 0, np.inf, 0.0))
+    tally.worst = max(tally.worst, float(np.max(ratio)) if ratio.size else 0.0)
+    if not np.all(err <= tol):
+        tally.failed += 1
+        k = int(np.argmax(ratio))
+        tally.msgs.append(f"{tag} pos {k}: gpu {g[k]!r} oracle {r[k]!r}")
+
+
+# --------------------------------------------- checks over a process pool --
+# The oracle is slow on purpose; checking thousands of trials at the full row
+# count runs it on every host core.  The pool is started with "spawn" so
+# that it is safe after CUDA work in the calling process.
+
+#: arrays a worker needs (the workload's generator closure is not sent)
+_SHIP = ("X", "y", "op", "cval", "heights", "layout", "F")
+_W = None
+
+
+def _init_worker(w):
+    global _W
+    _W = w
+
+
+def _fit_task(items):
+    w = _W
+    y = w["y"].astype(np.float64)
+    var_y, mean_y2 = float(np.var(y)), float(np.mean(y * y))
+    t = Tally()
+    for p, g_smse, g_mse in items:
+        _, _, _, fit64, fit32, _, bounds = oracle_trial(w, p)
+        check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, t, tag=f"trial {p}",
+                  bounds=bounds)
+    return t
+
+
+def _grad_task(items):
+    w = _W
+    t = Tally()
+    n_floor = 0
+    for p, mode, g in items:
+        tt = template(w, p)
+        r, fit, rabs = O.grad(tt, w["X"], w["y"], mode, with_abs=True)
+        if not (fit["finite"] and np.all(np.isfinite(r))):
+            t.excluded += 1
+            continue
+        n_floor += floor_only_entries(g, r, rabs)
+        check_grad(g, r, t, tag=f"trial {p}", rabs=rabs)
+    return t, n_floor
+
+
+def _pool_map(w, fn, items, processes, chunk):
+    import multiprocessing as mp
+    import os
+    tasks = [items[i:i + chunk] for i in range(0, len(items), chunk)]
+    if not tasks:
+        return []
+    n = min(processes or os.cpu_count() or 1, len(tasks))
+    ship = {k: w[k] for k in _SHIP}
+    if n <= 1:
+        _init_worker(ship)
+        return [fn(tk) for tk in tasks]
+    with mp.get_context("spawn").Pool(n, initializer=_init_worker, initargs=(ship,)) as pool:
+        return list(pool.imap_unordered(fn, tasks))
+
+
+def check_fitness(w, trials, smse, mse=None, processes=None, chunk=2):
+    """Check GPU smse (and mse) of the listed trials against the oracle at the
+    workload's full row count, on a spawn-started process pool; returns the
+    merged Tally."""
+    items = [(int(p), float(smse[p]), None if mse is None else float(mse[p])) for p in trials]
+    out = Tally()
+    for t in _pool_map(w, _fit_task, items, processes, chunk):
+        out.merge(t)
+    return out
+
+
+def check_gradients(w, trials, dcval, mode="smse", processes=None, chunk=1):
+    """Check GPU gradients (rows of dcval) of the listed trials against the
+    oracle's reverse mode; returns (Tally, entries that pass only through
+    the FP32 floor term of the tolerance)."""
+    items = [(int(p), mode, np.asarray(dcval[p], dtype=np.float64)) for p in trials]
+    out, floor = Tally(), 0
+    for t, nf in _pool_map(w, _grad_task, items, processes, chunk):
+        out.merge(t)
+        floor += nf
+    return out, floor

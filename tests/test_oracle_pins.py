@@ -358,6 +358,49 @@ def test_fp32_emulation_close_on_benign_tree():
     np.testing.assert_allclose(f32, f64, rtol=1e-6, atol=1e-6)
 
 
+def test_fp32_emulation_rounds_every_node():
+    """Each node's value is rounded to FP32 before its parent uses it:
+    (x0 + x1) - x0 is 0 in FP32 when x1 is below half a unit in the last
+    place of x0 (1 + 2^-30 and 3 + 2^-23 round to 1 and 3), while FP64
+    keeps x1; (x0 * x0) - x1 with x0 = 1 + 2^-12, x1 = 1 + 2^-11 is 0 in FP32
+    (1 + 2^-11 + 2^-24 rounds to even, down to 1 + 2^-11) and 2^-24 in FP64."""
+    X = np.array([[1.0, 2.0 ** -30], [3.0, 2.0 ** -23]], dtype=np.float32)
+    t = T(["-", "+", "x0", "x0", "x1"], 2)
+    np.testing.assert_array_equal(O.eval_tree_f32(t, X), [0.0, 0.0])
+    np.testing.assert_array_equal(O.eval_tree(t, X), [2.0 ** -30, 2.0 ** -23])
+    X2 = np.array([[1.0 + 2.0 ** -12, 1.0 + 2.0 ** -11]], dtype=np.float32)
+    t2 = T(["-", "*", "x1", "x0", "x0"], 2)
+    assert O.eval_tree_f32(t2, X2)[0] == 0.0
+    assert O.eval_tree(t2, X2)[0] == 2.0 ** -24
+
+
+def test_gradient_scale_terms_hand_values():
+    """oracle.grad's with_abs scale G = sum_i s_i |d f_i / d c| by hand.
+    X = (1, 2, 3), y = (1, 3, 2).  Tree c * x0 with c = 2: f = (2, 4, 6),
+    b* = 1/4, a* = 1, smse = 1/2; the smse gradient is 0 (c only scales f)
+    and G = (2/3)(1/4) sum (1 + f_i/4 + y_i) x_i = 13/3; for mse the gradient
+    is (2/3) sum (f_i - y_i) x_i = 10 and G = (2/3) sum (f_i + y_i) x_i = 82/3.
+    Tree x0 (x0 + c) with c = 1: f = (2, 6, 12), b* = 3/38, a* = 28/19,
+    residuals (12, -20, 8)/19, gradient (1/19) sum r_i x_i = -4/361 and
+    G = (1/19) sum (28/19 + 3 f_i/38 + y_i) x_i = 490/361."""
+    X = np.array([[1.0], [2.0], [3.0]])
+    y = np.array([1.0, 3.0, 2.0])
+    t = T(["*", "2", "x0"], 1)
+    g, fit, ga = O.grad(t, X, y, with_abs=True)
+    assert math.isclose(fit["a"], 1.0, rel_tol=1e-14) and math.isclose(fit["b"], 0.25, rel_tol=1e-14)
+    assert math.isclose(fit["smse"], 0.5, rel_tol=1e-14)
+    assert abs(g[1]) < 1e-15 and math.isclose(ga[1], 13 / 3, rel_tol=1e-14)
+    g, fit, ga = O.grad(t, X, y, "mse", with_abs=True)
+    assert math.isclose(g[1], 10.0, rel_tol=1e-14) and math.isclose(ga[1], 82 / 3, rel_tol=1e-14)
+    t = T(["*", "x0", "+", None, None, "x0", "1"], 2)
+    g, fit, ga = O.grad(t, X, y, with_abs=True)
+    assert math.isclose(fit["b"], 3 / 38, rel_tol=1e-14)
+    assert math.isclose(fit["a"], 28 / 19, rel_tol=1e-14)
+    assert math.isclose(g[6], -4 / 361, rel_tol=1e-12)
+    assert math.isclose(ga[6], 490 / 361, rel_tol=1e-14)
+    assert np.count_nonzero(ga) == 1 and np.count_nonzero(g) == 1
+
+
 def test_perturbed_evaluation_bounds():
     rng, X = rand_xy(12)
     t = T(["*", "x0", "x1"], 1)
@@ -410,7 +453,8 @@ PINS = [test_fig1_rpn_and_encoding, test_fig1_value_is_printed_expression,
             ("-", [-3.0, -1.0, 3.0, -3.0]), ("aq", [2 / math.sqrt(26), 3 / math.sqrt(17), 6 / math.sqrt(10), -3.0]),
             ("/", [0.4, 0.75, 2.0, -math.inf]), ("pow", [32.0, 81.0, 216.0, 1.0])]],
         lambda: test_unary_hand_values_use_left_child("sin", math.pi / 6, 0.5),
-        test_intron_invariance_random_trees]
+        test_intron_invariance_random_trees, test_fp32_emulation_rounds_every_node,
+        test_gradient_scale_terms_hand_values]
 
 
 def _pins_fail():
@@ -466,4 +510,26 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(gp, "_dapply", dsin_sign)
     assert _pins_fail(), "wrong sign in d sin"
     monkeypatch.setattr(gp, "_dapply", real_dapply)
+
+    real_f32, real_grad = gp.eval_tree_f32, gp.grad
+    rounded_at_end = lambda t, X: gp.eval_tree(t, X).astype(np.float32)
+    monkeypatch.setattr(gp, "eval_tree_f32", rounded_at_end)
+    monkeypatch.setattr(O, "eval_tree_f32", rounded_at_end)
+    assert _pins_fail(), "FP32 emulation rounds only the result"
+    monkeypatch.setattr(gp, "eval_tree_f32", real_f32)
+    monkeypatch.setattr(O, "eval_tree_f32", real_f32)
+
+    def scale_without_y(t, X, y, mode="smse", with_abs=False):
+        out = real_grad(t, X, y, mode, with_abs)
+        if not with_abs:
+            return out
+        g, fit, ga = out
+        # the |y_i| term of the scale dropped
+        _, _, ga0 = real_grad(t, X, np.zeros_like(np.asarray(y, float)), mode, True)
+        return g, fit, ga0
+    monkeypatch.setattr(gp, "grad", scale_without_y)
+    monkeypatch.setattr(O, "grad", scale_without_y)
+    assert _pins_fail(), "gradient scale drops |y|"
+    monkeypatch.setattr(gp, "grad", real_grad)
+    monkeypatch.setattr(O, "grad", real_grad)
     assert not _pins_fail()
