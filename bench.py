@@ -1,11 +1,12 @@
 """Benchmark: batched fitness evaluation of one GOM/FOS step on GB300.
 
 One step = one batched evaluation of every trial of one FOS step (pack,
-batched forward, finalise), replayed as a CUDA graph, on the workload
-"fos-step-4096xh4-100000x8": 4,096 trials of height 4 (31 nodes, full
-function set), X 100,000 x 8 ~ U[-3, 3], y from a seeded height-4 tree plus
-1 % noise.  Inputs are resident in HBM when the timed region starts; L2 is
-flushed (a 512 MB write) between timed steps.  Reported:
+batched forward, finalise), replayed as a CUDA graph, on the largest
+workload, "large-16384xh6-1000000x10": 16,384 trials of height 6 (127
+nodes, full function set), X 1,000,000 x 10 ~ U[-1, 1], y from a seeded
+height-6 tree plus 1 % noise.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 512 MB write) between timed steps.
+Reported:
 
   value      node-row evals/s (active nodes x rows x trials / s), graph form;
              the library folds each feature-free subtree into one constant
@@ -21,8 +22,16 @@ flushed (a 512 MB write) between timed steps.  Reported:
   roofline   the batched forward kernel against the FP32 issue peak
              (152 SMs x 128 lanes x the SM clock sampled during the run),
              counting the operations of the folded programs
+  parity     the timed outputs of a sample of trials against the FP64 oracle
   cpu_baseline  the FP64 oracle on one host core, on a sample of trials
   cpu_baseline_all_cores  the same oracle over every host core (process pool)
+  also       the FOS-step (4,096 x h4 over 100,000 x 8) and uneven-heights
+             (8,192 x h3..7 over 200,000 x 10) workloads: graph form,
+             roofline and parity
+
+The oracle leg (the target y of each workload, the parity sample and the
+CPU baselines) is the only part that runs the oracle package; the timed
+path runs the CUDA library alone.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -46,7 +55,8 @@ import synth  # noqa: E402
 METRIC = ("node-row evals/sec and trial fitness evals/sec at scaled-MSE rel err ≤1e-4, "
           "batched vs plain")
 UNIT = "node-row evals/s"
-CFG = "c2"
+CFG = "c5"
+EXTRA_CFGS = ("c2", "c3")
 SMS, FP32_LANES, SFU_LANES = 152, 128, 16
 # algorithmic FP32 / SFU operations per evaluated node (by class) and per
 # row-trial for the fitness sums (shift, sum d, sum d^2, sum d*y); pow counts
@@ -57,15 +67,31 @@ OPS_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, 
            "sqrt": 1, "square": 0, "pow": 2}
 ACC_FP32 = 4
 TUNE_STEPS = 20  # Adam steps of the constant-tuning report (grad mode)
-# DRAM bytes (read + write) of one batched-forward launch from the ncu
-# capture summarised in profiles/fwd_kernel_fos-step-4096xh4-100000x8.md;
-# None for a workload without a capture of the current kernel
-NCU_TRAFFIC = {"fos-step-4096xh4-100000x8": 4789504 + 512}
+PARITY_TRIALS = 64  # timed trials compared with the oracle per workload
+# DRAM bytes (read + write) of one batched-forward launch from an ncu
+# capture, keyed by (workload, hash of the CUDA sources and the header at
+# the time of the capture); reported only while the sources still match
+NCU_TRAFFIC: dict = {}
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}
 # the same classes after constant folding (the nodes evaluated on every row)
 EXEC_COLS = {"term": 14, "addsubmul": 15, "aq": 16, "div": 17, "sincos": 18, "exp": 19,
              "log": 20, "sqrt": 21, "square": 22, "pow": 23}
+
+
+def source_hash():
+    """Hash of the CUDA sources and the C header the library is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_30954_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
+                   if f.endswith((".cu", ".cuh", ".h")))
+    files.append(os.path.join(ROOT, "include", "ggeval.h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -77,7 +103,8 @@ def parse():
     ap.add_argument("--config", default=CFG, choices=sorted(synth.CONFIGS))
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
     ap.add_argument("--mode", default="eval", choices=["eval", "grad", "sweep"],
                     help="eval: one batched FOS-step evaluation per step (the headline); "
                          "grad: fitness + adjoint + one Adam step per step; "
@@ -157,36 +184,35 @@ def aggregate(step_ms_total, steps, nodes, trials, rows, allreduce, ops):
             "trial_evals_per_s": p_sum / (ms * 1e-3), "nodes": n_sum, "trials": p_sum}
 
 
-def make_workload(cfg, rep, gg, torch, device):
-    """Seeded workload; the target comes from the library's own per-row
-    evaluation of the first usable generator tree."""
+# ------------------------------------------------------------ oracle leg --
+# Everything in this section runs the FP64 oracle on the host: the target of
+# each workload (the same computation the parity tests use), the parity
+# sample of the timed outputs and the CPU baselines.
+
+def oracle_workload(cfg, rep):
+    """Seeded workload with its target y from the oracle's evaluation of the
+    first usable generator tree (as in the parity tests)."""
+    import oracle.parity as OP
     w = synth.workload(cfg, rep)
-    if "y" in w:  # a closed-form target
-        return w
-    X = torch.from_numpy(w["X"])
-    dummy = torch.zeros(w["N"], dtype=torch.float32)
-    probe = gg.Dataset(X, dummy, device=device)
-    for gop, gcv, gh in w["y_cands"]():
-        f = probe.eval_rows(torch.from_numpy(gop[None]).cuda(device),
-                            torch.from_numpy(gcv[None]).cuda(device))[0].double().cpu().numpy()
-        if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
-            break
-    probe.sync()
-    probe.close()
-    w["y"] = synth.make_target(f, w["z"], w["noise"])
+    if "y" not in w:
+        w["y"], _ = OP.target_from_oracle(w)
     return w
 
 
-def node_counts(gg, torch, w):
-    st = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
-                        torch.from_numpy(w["heights"]) if "h_min" in synth.CONFIGS[w["cfg"]] else None,
-                        n_features=w["F"]).numpy()
-    ok = st[:, 0] >= 0
-    nodes = int(st[ok, 0].sum())
-    # algorithmic operations of what runs per row: the program after folding
-    fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
-    sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
-    return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 13].sum())
+def oracle_parity(w, smse, mse, n=PARITY_TRIALS, seed=5):
+    """The timed outputs of n sampled trials against the oracle at the full
+    row count (spawn-started process pool over the host cores)."""
+    import oracle.parity as OP
+    trials = sorted(np.random.default_rng(seed).choice(w["P"], min(n, w["P"]),
+                                                       replace=False).tolist())
+    t0 = time.perf_counter()
+    t = OP.check_fitness(w, trials, smse, mse)
+    d = t.as_dict()
+    d.update(trials_sampled=len(trials), seconds=round(time.perf_counter() - t0, 1),
+             tolerance="|g - r| <= 1e-4 r + 1e-8 Var(y)", ok=t.failed == 0)
+    if t.msgs:
+        d["first_failures"] = t.msgs[:3]
+    return d
 
 
 _POOL_W = None
@@ -216,16 +242,18 @@ def cpu_baseline_all_cores(w, per_trial_s, seconds):
     """The same oracle on every host core: a spawn-started process pool (safe
     after GPU work in this process), trials split evenly, sized so the timed
     part takes about `seconds`."""
+    import concurrent.futures as cf
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     n = int(min(w["P"], max(cores, seconds * cores / max(per_trial_s, 1e-9))))
     idx = np.arange(n)
     chunks = [c.tolist() for c in np.array_split(idx, cores) if len(c)]
     ww = {k: w[k] for k in ("op", "cval", "heights", "layout", "F", "X", "y")}
-    with mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(ww,)) as pool:
-        pool.map(_oracle_trials, [[0]] * cores)  # start-up (imports) outside the timing
+    with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn"),
+                                initializer=_pool_init, initargs=(ww,)) as ex:
+        list(ex.map(_oracle_trials, [[0]] * cores))  # start-up (imports) outside the timing
         t0 = time.perf_counter()
-        nodes = sum(pool.map(_oracle_trials, chunks))
+        nodes = sum(ex.map(_oracle_trials, chunks))
         el = time.perf_counter() - t0
     return {"value": nodes * w["N"] / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "trial_evals_per_s": n / el,
@@ -265,12 +293,8 @@ def run_reference(a):
     import oracle as O
     import torch
     torch.set_num_threads(1)
-    w = synth.workload(a.config, 0)
-    for gop, gcv, gh in w["y_cands"]():
-        f = O.eval_tree(O.Template(gop, gcv, gh, "heap", w["F"]), w["X"])
-        if np.all(np.isfinite(f)) and np.var(f) > 0 and np.max(np.abs(f)) <= 1e6:
-            break
-    y = synth.make_target(f, w["z"], w["noise"])
+    w = oracle_workload(a.config, 0)
+    y = w["y"]
     per_step = 1
     idx = 0
 
@@ -309,6 +333,132 @@ def run_reference(a):
     }))
 
 
+# -------------------------------------------------------------- GPU legs --
+def node_counts(gg, torch, w):
+    st = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
+                        torch.from_numpy(w["heights"]) if "h_min" in synth.CONFIGS[w["cfg"]] else None,
+                        n_features=w["F"]).numpy()
+    ok = st[:, 0] >= 0
+    nodes = int(st[ok, 0].sum())
+    # algorithmic operations of what runs per row: the program after folding
+    fp32 = sum(OPS_FP32[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
+    sfu = sum(OPS_SFU[k] * int(st[ok, c].sum()) for k, c in EXEC_COLS.items())
+    return nodes, fp32, sfu, int(ok.sum()), int(st[ok, 13].sum())
+
+
+class Runner:
+    """One workload on one GPU: dataset, device batch, side stream, timing."""
+
+    def __init__(self, gg, torch, w, dev, barrier):
+        self.gg, self.torch, self.w, self.dev, self.barrier = gg, torch, w, dev, barrier
+        self.PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
+        self.ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
+        self.op = torch.from_numpy(w["op"]).cuda(dev)
+        self.cv = torch.from_numpy(w["cval"]).cuda(dev)
+        self.hs = (torch.from_numpy(w["heights"]).cuda(dev)
+                   if "h_min" in synth.CONFIGS[w["cfg"]] else None)
+        self.st = torch.cuda.Stream(dev)
+        self.outs = [torch.empty(w["P"], device=f"cuda:{dev}") for _ in range(4)]
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32,
+                                 device=f"cuda:{dev}")
+        self.ds.autotune(self.op, self.cv, self.hs, flags=self.PF)
+        self.cfg = self.ds.tile_config(self.op, self.cv, self.hs, flags=self.PF)
+        torch.cuda.synchronize()
+
+    def graph_step(self):
+        self.ds.eval_batch(self.op, self.cv, self.hs, flags=self.gg.F_GRAPH | self.PF,
+                           stream=self.st, out=self.outs)
+
+    def prof_step(self):
+        self.ds.eval_batch(self.op, self.cv, self.hs, flags=self.gg.F_PROFILE | self.PF,
+                           stream=self.st, out=self.outs)
+
+    def timed(self, fn, steps, clocks=None, name="timed"):
+        """Sum of per-step CUDA-event times (ms) on the side stream, L2
+        flushed before every step."""
+        torch = self.torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        self.barrier()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        torch.cuda.nvtx.range_push(name)
+        for i in range(steps):
+            with torch.cuda.stream(self.st):
+                self.flush.fill_(float(i))
+                ev[i][0].record(self.st)
+                fn()
+                ev[i][1].record(self.st)
+        self.st.synchronize()
+        torch.cuda.nvtx.range_pop()
+        self.barrier()
+        ck = clocks.stop() if clocks else None
+        return float(np.sum([e0.elapsed_time(e1) for e0, e1 in ev])), ck
+
+    def warm(self, fn, n):
+        for _ in range(n):
+            with self.torch.cuda.stream(self.st):
+                fn()
+        self.st.synchronize()
+
+    def roofline(self, steps, fp32_ops, sfu_ops, valid, fallback_ck):
+        """The batched forward kernel alone: CUDA events around it on its
+        launching stream (GGEVAL_F_PROFILE), eager launches."""
+        self.warm(self.prof_step, 2)
+        self.ds.profile_read()
+        clocks = Clocks(self.dev)
+        eager_ms, ck = self.timed(self.prof_step, steps, clocks, "timed_eager")
+        fwd_ms, launches = self.ds.profile_read()
+        fwd_avg = fwd_ms / max(launches, 1)
+        w = self.w
+        N = w["N"]
+        sm_mhz = (ck or fallback_ck or {}).get("sm_mhz") or 1477.0
+        peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9  # Gop/s
+        peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
+        alg_fp32 = (fp32_ops + ACC_FP32 * valid) * N  # per launch
+        alg_sfu = sfu_ops * N
+        ach_fp32 = alg_fp32 / (fwd_avg * 1e-3) / 1e9
+        ach_sfu = alg_sfu / (fwd_avg * 1e-3) / 1e9
+        x_bytes = (w["F"] + 1) * N * 4
+        traffic = NCU_TRAFFIC.get((w["name"], source_hash()))
+        return {"bound": "alu", "achieved": ach_fp32, "peak": peak_fp32, "unit": "Gop/s",
+                "frac": ach_fp32 / peak_fp32, "traffic": traffic,
+                "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
+                "algorithmic_fp32_ops_per_launch": alg_fp32,
+                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
+                              "(SM clock sampled during the kernel's timing)",
+                "sfu": {"achieved": ach_sfu, "peak": peak_sfu, "frac": ach_sfu / peak_sfu},
+                "hbm_gbs": x_bytes / (fwd_avg * 1e-3) / 1e9,
+                "eager_ms_per_step": eager_ms / steps, "clocks": ck}
+
+    def close(self):
+        self.ds.close()
+
+
+def extra_workload(gg, torch, cfg, a, dev, barrier):
+    """A smaller workload in the same process: graph-form throughput,
+    roofline and parity (no plain form, end-to-end or CPU legs)."""
+    w = oracle_workload(cfg, 0)
+    nodes, fp32_ops, sfu_ops, valid, nodes_eval = node_counts(gg, torch, w)
+    r = Runner(gg, torch, w, dev, barrier)
+    r.warm(r.graph_step, a.warmup)
+    clocks = Clocks(dev)
+    tot_ms, ck = r.timed(r.graph_step, a.steps, clocks, "timed_graph_" + cfg)
+    ms = tot_ms / a.steps
+    smse, mse = r.outs[0].cpu().numpy(), r.outs[3].cpu().numpy()
+    r.ds.sync(r.st)
+    roof = r.roofline(a.steps, fp32_ops, sfu_ops, valid, ck)
+    cfg_used = r.cfg
+    r.close()
+    return {"workload": w["name"], "value": nodes * w["N"] / (ms * 1e-3), "unit": UNIT,
+            "trial_evals_per_s": w["P"] / (ms * 1e-3), "ms_per_step": ms,
+            "nodes_evaluated_per_row_per_step": nodes_eval,
+            "tile_config": {"variant": cfg_used[0], "tile_rows": cfg_used[1],
+                            "group": cfg_used[2], "warps": cfg_used[3]},
+            "roofline": roof, "clocks": ck, "parity": oracle_parity(w, smse, mse)}
+
+
 def fos_csr(stride):
     """One FOS subset per template node: the node and its children."""
     subsets = [[i] + [c for c in (2 * i + 1, 2 * i + 2) if c < stride] for i in range(stride)]
@@ -320,7 +470,7 @@ def run_extra_mode(a, gg, torch):
     """--mode grad / sweep on one GPU (documentation lines, not the headline)."""
     dev = 0
     torch.cuda.set_device(dev)
-    w = make_workload(a.config, 0, gg, torch, dev)
+    w = oracle_workload(a.config, 0)
     PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
     nodes, _, _, valid, _ = node_counts(gg, torch, w)
     N, P = w["N"], w["P"]
@@ -403,7 +553,7 @@ def run_extra_mode(a, gg, torch):
         with torch.cuda.stream(st):
             sweep()  # sizes the workspace and tunes the plan outside the capture
         st.synchronize()
-        # the whole sweep (31 GOM steps, about 220 launches) as one CUDA graph
+        # the whole sweep (one GOM step per FOS subset) as one CUDA graph
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=st):
             sweep()
@@ -434,12 +584,10 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode != "eval":
-        import torch
-        import paper_2605_30954_gb300 as gg
-        return run_extra_mode(a, gg, torch)
     import torch
     import paper_2605_30954_gb300 as gg
+    if a.mode != "eval":
+        return run_extra_mode(a, gg, torch)
 
     rank, world, local = dist_env()
     dev = local
@@ -464,112 +612,54 @@ def main():
 
     ops = {"max": pg.ReduceOp.MAX if pg else None, "sum": pg.ReduceOp.SUM if pg else None}
 
-    w = make_workload(a.config, rank, gg, torch, dev)
-    PF = gg.F_POW if w["uses_pow"] else 0  # kernels with pow, for a pow function set
+    w = oracle_workload(a.config, rank)
     nodes, fp32_ops, sfu_ops, valid, nodes_eval = node_counts(gg, torch, w)
     N, P = w["N"], w["P"]
-    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]), device=dev)
-    op = torch.from_numpy(w["op"]).cuda(dev)
-    cv = torch.from_numpy(w["cval"]).cuda(dev)
-    hs = torch.from_numpy(w["heights"]).cuda(dev) if "h_min" in synth.CONFIGS[a.config] else None
-    ds.autotune(op, cv, hs, flags=PF)
-    st = torch.cuda.Stream(dev)
-    outs = [torch.empty(P, device=f"cuda:{dev}") for _ in range(4)]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
-    torch.cuda.synchronize()
-
-    def graph_step():
-        ds.eval_batch(op, cv, hs, flags=gg.F_GRAPH | PF, stream=st, out=outs)
-
-    def timed(fn, steps, clocks=None, name="timed"):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        barrier()
-        if clocks:
-            clocks.start()
-            time.sleep(0.3)
-        torch.cuda.nvtx.range_push(name)
-        for i in range(steps):
-            with torch.cuda.stream(st):
-                flush.fill_(float(i))
-                ev[i][0].record(st)
-                fn()
-                ev[i][1].record(st)
-        st.synchronize()
-        torch.cuda.nvtx.range_pop()
-        barrier()
-        ck = clocks.stop() if clocks else None
-        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-        return float(np.sum(ms)), ck
+    r = Runner(gg, torch, w, dev, barrier)
 
     # ---- batched form, graph replay (the headline) ----
-    for _ in range(a.warmup):
-        with torch.cuda.stream(st):
-            graph_step()
-    st.synchronize()
+    r.warm(r.graph_step, a.warmup)
     clocks = Clocks(dev)
-    tot_ms, ck = timed(graph_step, a.steps, clocks, "timed_graph")
+    tot_ms, ck = r.timed(r.graph_step, a.steps, clocks, "timed_graph")
     agg = aggregate(tot_ms, a.steps, nodes, P, N, allreduce, ops)
     ms_step = agg["ms_per_step"]
     all_nodes, all_trials = agg["nodes"], agg["trials"]
-    value = agg["node_row_evals_per_s"]
-    trial_rate = agg["trial_evals_per_s"]
-    ds.sync(st)
+    r.ds.sync(r.st)
+    timed_smse, timed_mse = r.outs[0].cpu().numpy(), r.outs[3].cpu().numpy()
     # trials whose fitness is +inf: the batched form stops evaluating such a
     # trial after its first non-finite tile (node-rows still count them all)
-    nonfinite = int((~torch.isfinite(outs[0])).sum().item())
+    nonfinite = int((~np.isfinite(timed_smse)).sum())
 
     # ---- forward kernel alone: live CUDA events around it (roofline) ----
-    def prof_step():
-        ds.eval_batch(op, cv, hs, flags=gg.F_PROFILE | PF, stream=st, out=outs)
-    for _ in range(2):
-        with torch.cuda.stream(st):
-            prof_step()
-    st.synchronize()
-    ds.profile_read()
-    clocks2 = Clocks(dev)
-    eager_ms, ck2 = timed(prof_step, a.steps, clocks2, "timed_eager")
-    fwd_ms, launches = ds.profile_read()
-    fwd_avg = fwd_ms / max(launches, 1)
-    sm_mhz = (ck2 or ck or {}).get("sm_mhz") or 1477.0
-    peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9  # Gop/s
-    peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
-    alg_fp32 = (fp32_ops + ACC_FP32 * valid) * N  # per launch
-    alg_sfu = sfu_ops * N
-    ach_fp32 = alg_fp32 / (fwd_avg * 1e-3) / 1e9
-    ach_sfu = alg_sfu / (fwd_avg * 1e-3) / 1e9
-    x_bytes = (w["F"] + 1) * N * 4
+    roof = r.roofline(a.steps, fp32_ops, sfu_ops, valid, ck)
 
     # ---- plain form: one launch per trial ----
     def plain_step():
-        ds.eval_plain(op, cv, hs, flags=PF, stream=st, out=outs)
-    with torch.cuda.stream(st):
-        plain_step()
-    st.synchronize()
-    plain_ms, _ = timed(plain_step, a.plain_steps, name="timed_plain")
+        r.ds.eval_plain(r.op, r.cv, r.hs, flags=r.PF, stream=r.st, out=r.outs)
+    r.warm(plain_step, 1)
+    plain_ms, _ = r.timed(plain_step, a.plain_steps, name="timed_plain")
     plain_step_ms = allreduce(plain_ms, ops["max"]) / a.plain_steps
     plain_trials = all_trials / (plain_step_ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     hop = torch.from_numpy(w["op"]).pin_memory()
     hcv = torch.from_numpy(w["cval"]).pin_memory()
-    hhs = torch.from_numpy(w["heights"]).pin_memory() if hs is not None else None
+    hhs = torch.from_numpy(w["heights"]).pin_memory() if r.hs is not None else None
     hout = [torch.empty(P, dtype=torch.float32).pin_memory(), None, None, None]
 
     def e2e_step():
-        ds.eval_batch(hop, hcv, hhs, flags=PF, stream=st, out=hout)
-    for _ in range(a.warmup):
-        with torch.cuda.stream(st):
-            e2e_step()
-    st.synchronize()
-    e2e_ms, _ = timed(e2e_step, a.steps, name="timed_e2e")
+        r.ds.eval_batch(hop, hcv, hhs, flags=r.PF, stream=r.st, out=hout)
+    r.warm(e2e_step, a.warmup)
+    e2e_ms, _ = r.timed(e2e_step, a.steps, name="timed_e2e")
     e2e_ms = allreduce(e2e_ms, ops["max"]) / a.steps
-    h2d = w["op"].nbytes + w["cval"].nbytes + (w["heights"].nbytes if hs is not None else 0)
-    ds.sync(st)
+    h2d = w["op"].nbytes + w["cval"].nbytes + (w["heights"].nbytes if r.hs is not None else 0)
+    r.ds.sync(r.st)
+    cfg_used = r.cfg
+    r.close()
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "metric": METRIC, "value": agg["node_row_evals_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "trials_per_step": P, "rows": N,
                    "features": w["F"], "template_height": w["h_max"],
@@ -578,31 +668,31 @@ def main():
                    "trials_with_infinite_fitness": nonfinite,
                    "flush_l2": "512 MB write between steps",
                    "form": "persistent batched kernel, CUDA graph replay, autotuned tiles",
+                   "tile_config": {"variant": cfg_used[0], "tile_rows": cfg_used[1],
+                                   "group": cfg_used[2], "warps": cfg_used[3]},
                    "parallelism": f"replicas x{world} (independent FOS steps)"},
-        "trial_evals_per_s": trial_rate,
+        "trial_evals_per_s": agg["trial_evals_per_s"],
         "plain": {"trial_evals_per_s": plain_trials, "ms_per_step": plain_step_ms,
                   "node_row_evals_per_s": all_nodes * N / (plain_step_ms * 1e-3),
                   "launches_per_step": 2 * P + 2},
-        "batched_over_plain": trial_rate / plain_trials,
+        "batched_over_plain": agg["trial_evals_per_s"] / plain_trials,
         "e2e": {"value": all_nodes * N / (e2e_ms * 1e-3), "unit": UNIT,
                 "trial_evals_per_s": all_trials / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(4 * P)},
-        "roofline": {"bound": "alu", "achieved": ach_fp32, "peak": peak_fp32, "unit": "Gop/s",
-                     "frac": ach_fp32 / peak_fp32, "traffic": NCU_TRAFFIC.get(w["name"]),
-                     "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
-                     "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
-                                   "(sampled SM clock)",
-                     "sfu": {"achieved": ach_sfu, "peak": peak_sfu, "frac": ach_sfu / peak_sfu},
-                     "hbm_gbs": x_bytes / (fwd_avg * 1e-3) / 1e9,
-                     "eager_ms_per_step": eager_ms / a.steps},
+        "roofline": roof,
         "gpu_launches": 3 * a.steps,
         "clocks": ck,
+        "kernel_sources": source_hash(),
     }
+    if rank == 0:
+        line["parity"] = oracle_parity(w, timed_smse, timed_mse)
     if rank == 0 and world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cb = cpu_baseline(w, a.cpu_seconds, torch)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(
             w, 1.0 / cb["trial_evals_per_s"], a.cpu_seconds)
-    ds.close()
+    if world == 1 and not a.no_extra:
+        line["also"] = [extra_workload(gg, torch, c, a, dev, barrier)
+                        for c in EXTRA_CFGS if c != a.config]
     if pg:
         pg.destroy_process_group()
     if rank == 0:

@@ -174,10 +174,14 @@ ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* batch,
 
 /* Per-row values f_i of every trial (float [n][n_rows], batch memory), the
  * quantity each "sub-evaluation" of Section 3.2 squares.  For checking and
- * for building targets; not the fast path (it accepts POW nodes without a
- * flag). */
+ * for building targets: it runs the launch configuration ggeval_eval_batch
+ * would run with the same flags (tuned or default; see
+ * ggeval_tile_config), in a build of the same kernel that also stores
+ * every row's value, so the per-row values are those the fitness sums
+ * take.  flags: GGEVAL_F_POW, GGEVAL_F_NO_FOLD, GGEVAL_F_EXACT as for
+ * ggeval_eval_batch (the others are ignored). */
 ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* batch,
-                               float* f, void* stream);
+                               uint32_t flags, float* f, void* stream);
 
 /* The same fitness as ggeval_eval_batch computed the plain way: one launch
  * of the row-parallel kernel per trial followed by a second-stage
@@ -215,6 +219,20 @@ ggeval_status ggeval_adam_step(const ggeval_batch* batch, float* cval, const flo
  * and the choice are printed to stderr. */
 ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* batch,
                               uint32_t flags, void* stream);
+
+/* The launch configuration of ggeval_eval_batch for batches of this shape
+ * (n, max_height, layout, flags & (EXACT | POW)): int32 [4] = {variant,
+ * rows per tile, trials per work item, warps per CTA}.  variant: 0 = 8
+ * rows per lane with grouped sums, 1 = 4 rows per lane grouped, 2 = 4 rows
+ * per lane with per-row error-free sums, 4..6 = 0..2 built for at most 64
+ * registers.  With `set` non-NULL the given configuration is checked (it
+ * must fit in shared memory; rows per tile a multiple of 32 x rows per
+ * lane) and kept for such batches, as ggeval_autotune keeps its choice;
+ * with `get` non-NULL the configuration in force is written there.  The
+ * evaluation results do not depend on the configuration beyond rounding
+ * of the fitness sums.  Errors: ERR_ARG (bad configuration, empty batch). */
+ggeval_status ggeval_tile_config(ggeval_dataset* ds, const ggeval_batch* batch,
+                                 uint32_t flags, const int32_t* set, int32_t* get);
 
 /* Wait for the dataset's work on `stream`, then report and clear the
  * device-side status: GGEVAL_OK, ERR_TEMPLATE, ERR_TIMEOUT or ERR_CHECKED. */

@@ -683,17 +683,19 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
   return GGEVAL_OK;
 }
 
-ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* b, float* f,
-                               void* stream) {
+ggeval_status ggeval_eval_rows(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                               float* f, void* stream) {
   GG_TRY(check_batch(ds, b));
   if (b->n == 0) return GGEVAL_OK;
   if (!f) return fail(GGEVAL_ERR_ARG, "f is NULL");
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Cfg c = default_cfg(ds, b->n, b->max_height, GGEVAL_F_EXACT);
-  c.variant = 3;
+  // the configuration ggeval_eval_batch would run, in its per-row build
+  Cfg c = pick_cfg(ds, b, flags);
+  c.variant = gg::rows_variant(c.variant);
   Plan pl;
-  GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl, true));  // an inspection path: any operator
+  GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl, has_pow(flags)));
+  pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   const size_t fbytes = (size_t)b->n * ds->N * 4;
@@ -956,6 +958,36 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   ds->tuned[{b->n, b->max_height, b->layout, (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW))}] =
       best;
   drop_graph(ds);
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_tile_config(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                                 const int32_t* set, int32_t* get) {
+  GG_TRY(check_batch(ds, b));
+  if (b->n == 0) return fail(GGEVAL_ERR_ARG, "empty batch");
+  DeviceGuard guard(ds->device);
+  const auto key = std::make_tuple(b->n, b->max_height, b->layout,
+                                   (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW)));
+  if (set) {
+    Cfg c;
+    c.variant = set[0];
+    c.tile_rows = set[1];
+    c.group = set[2];
+    c.warps = set[3];
+    if (!gg::fitness_variant(c.variant))
+      return fail(GGEVAL_ERR_ARG, "variant %d is not a fitness variant", c.variant);
+    Plan pl;
+    GG_TRY(make_plan(ds, b->n, b->max_height, c, &pl, has_pow(flags)));
+    ds->tuned[key] = c;
+    drop_graph(ds);
+  }
+  if (get) {
+    const Cfg c = pick_cfg(ds, b, flags);
+    get[0] = c.variant;
+    get[1] = c.tile_rows;
+    get[2] = c.group;
+    get[3] = c.warps;
+  }
   return GGEVAL_OK;
 }
 

@@ -385,11 +385,13 @@ constexpr int FIN_WARPS = 16;  // trials per finaliser block
 
 // Kernel pointers: variant 0 = 8 rows/lane grouped sums, 1 = 4 rows/lane
 // grouped sums, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
-// variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers.
+// variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers;
+// 7 = variant 0 writing per-row values.  The per-row variants run the same
+// interpreter code as the variants with the same rows per lane.
 // fwd.cu holds the table of the kernels without pow, fwd_pow.cu the kernels
 // that also run pow instructions (kept apart because the pow code costs the
 // other kernels registers and instruction-cache locality).
-constexpr int NVARIANT = 7;
+constexpr int NVARIANT = 8;
 template <bool P>
 const void* fwd_table(int variant) {
   switch (variant) {
@@ -400,12 +402,17 @@ const void* fwd_table(int variant) {
     case 4: return reinterpret_cast<const void*>(&fwd_kernel<8, false, false, 2, P>);
     case 5: return reinterpret_cast<const void*>(&fwd_kernel<4, false, false, 2, P>);
     case 6: return reinterpret_cast<const void*>(&fwd_kernel<4, true, false, 2, P>);
+    case 7: return reinterpret_cast<const void*>(&fwd_kernel<8, false, true, 1, P>);
     default: return nullptr;
   }
 }
 const void* fwd_ptr_plain(int variant);
 const void* fwd_ptr_pow(int variant);
-inline int variant_rows(int v) { return (v == 0 || v == 4) ? 8 : 4; }
+inline int variant_rows(int v) { return (v == 0 || v == 4 || v == 7) ? 8 : 4; }
+// the variant that also writes per-row values, with v's rows per lane
+inline int rows_variant(int v) { return variant_rows(v) == 8 ? 7 : 3; }
+// variants a caller may choose for the fitness path (no per-row output)
+inline bool fitness_variant(int v) { return v >= 0 && v < 7 && v != 3; }
 inline int variant_max_warps(int v) { return fwd_max_threads(v >= 4 ? 2 : 1) / 32; }
 inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
 

@@ -30,7 +30,8 @@ SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggev
            "ggeval_pack_device",
            "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc",
            "ggeval_eval_batch_masked", "ggeval_gom_donate", "ggeval_gom_changed",
-           "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info")
+           "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info",
+           "ggeval_tile_config")
 
 
 class GGEvalError(RuntimeError):
@@ -58,7 +59,7 @@ def load_library(path: str = LIB_PATH):
         "ggeval_create_dataset": [vp, vp, i64, i32, i32, i32, vp, ctypes.POINTER(vp)],
         "ggeval_destroy": [vp],
         "ggeval_eval_batch": [vp, bp, u32, vp, vp, vp, vp, vp],
-        "ggeval_eval_rows": [vp, bp, vp, vp],
+        "ggeval_eval_rows": [vp, bp, u32, vp, vp],
         "ggeval_eval_plain": [vp, bp, u32, vp, vp, vp, vp, vp],
         "ggeval_grad_batch": [vp, bp, u32, vp, vp, vp],
         "ggeval_adam_step": [bp, vp, vp, vp, vp, i32, f32, f32, f32, f32, vp],
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "ggeval_gom_changed": [bp, vp, vp, i32, vp, vp],
         "ggeval_gom_accept": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ggeval_trial_sizes": [bp, i32, vp, vp],
+        "ggeval_tile_config": [vp, bp, u32, vp, vp],
         "ggeval_dataset_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
@@ -193,14 +195,27 @@ class Dataset:
                                        _stream_handle(stream)))
         return outs
 
-    def eval_rows(self, op, cval, heights=None, layout=LAYOUT_HEAP, stream=None):
+    def eval_rows(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None):
+        """Per-row values [n, N] from the configuration eval_batch would run
+        with these flags."""
         b = make_batch(op, cval, heights, layout=layout)
         kw = dict(dtype=torch.float32, device=op.device)
         if not op.is_cuda:
             kw["pin_memory"] = True
         f = torch.empty((b.n, self.N), **kw)
-        _check(lib().ggeval_eval_rows(self._h, ctypes.byref(b), _ptr(f), _stream_handle(stream)))
+        _check(lib().ggeval_eval_rows(self._h, ctypes.byref(b), flags, _ptr(f),
+                                      _stream_handle(stream)))
         return f
+
+    def tile_config(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, set=None):
+        """(variant, rows per tile, trials per item, warps per CTA) that
+        eval_batch uses for this batch shape; with ``set`` that tuple is
+        checked and kept first."""
+        b = make_batch(op, cval, heights, layout=layout)
+        got = (ctypes.c_int32 * 4)()
+        arr = None if set is None else (ctypes.c_int32 * 4)(*[int(x) for x in set])
+        _check(lib().ggeval_tile_config(self._h, ctypes.byref(b), flags, arr, got))
+        return tuple(got)
 
     def grad_batch(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None,
                    smse=None, dcval=None):

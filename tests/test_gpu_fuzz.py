@@ -45,8 +45,17 @@ def random_case(seed):
         op, cv = synth.to_prefix(op, cv, hs.astype(np.int64))
     mask = (rng.random(P) < 0.7).astype(np.uint8) if rng.random() < 0.5 else None
     flags_extra = int(rng.choice([0, 1, 2, 3]))  # bit 0: exact sums, bit 1: no folding
+    # half the cases force a launch configuration: any fitness variant (8 or
+    # 4 rows per lane, grouped or exact sums, either register budget), tile,
+    # trials per work item and warps per CTA
+    forced = None
+    if rng.random() < 0.5:
+        v = int(rng.choice([0, 1, 2, 4, 5, 6]))
+        rpp = 32 * (8 if v in (0, 4) else 4)
+        forced = (v, rpp * int(rng.choice([1, 2, 4])), int(rng.integers(1, P + 1)),
+                  int(rng.choice([1, 2, 4, 8, 16])))
     return dict(X=X, y=y, op=op, cval=cv, heights=hs.astype(np.int8), layout=layout, F=F,
-                P=P, N=N, mask=mask, flags_extra=flags_extra, funcs=funcs)
+                P=P, N=N, mask=mask, flags_extra=flags_extra, funcs=funcs, forced=forced)
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -63,6 +72,8 @@ def test_random_configurations(gg, seed):
     if w["flags_extra"] & 2:
         flags |= gg.F_NO_FOLD
     P = w["P"]
+    if w["forced"] is not None:
+        ds.tile_config(op, cv, hs, layout=lay, flags=flags, set=w["forced"])
     sentinel = -7.0
     outs = [torch.full((P,), sentinel, device="cuda") for _ in range(4)]
     if w["mask"] is None:
@@ -72,7 +83,7 @@ def test_random_configurations(gg, seed):
         ds.eval_batch_masked(op, cv, torch.from_numpy(w["mask"]).cuda(), hs, layout=lay,
                              flags=flags, out=outs)
         evaluated = w["mask"].astype(bool)
-    rows = ds.eval_rows(op, cv, hs, layout=lay).cpu().numpy()
+    rows = ds.eval_rows(op, cv, hs, layout=lay, flags=flags).cpu().numpy()
     ds.sync()
     ds.close()
     smse, a, b, mse = (t.cpu().numpy() for t in outs)
