@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "_lib", "libggeval.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+GEN = os.path.join(BUILD, "gen")  # generated sources (the PTX interpreter)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+         "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", GEN]
 
 
 def _nvcc():
@@ -40,17 +41,28 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
+def build(verbose: bool = False, extra_flags=(), force: bool = False, out: str = OUT,
+          build_dir: str = BUILD) -> str:
+    """Compile every csrc/*.cu for sm_103a and link the library.  A variant
+    build (extra compiler flags) takes its own `out` and `build_dir`."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    # the interpreter's inline PTX, written only when its text changes
+    sys.path.insert(0, CSRC)
+    try:
+        import interp_gen
+    finally:
+        sys.path.pop(0)
+    gen_inc = os.path.join(GEN, "interp_asm.inc")
+    interp_gen.main(gen_inc)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "ggeval.h"))
+    headers += [os.path.join(ROOT, "include", "ggeval.h"), gen_inc]
     jobs = []
     objs = []
     for src in sources():
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src[:-3] + ".o")
+        o = os.path.join(build_dir, src[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers, __file__]):
             jobs.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o])
@@ -65,13 +77,13 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
-    if force or jobs or not os.path.exists(OUT) or _stale(OUT, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", OUT, *objs, "-cudart", "static"]
+    if force or jobs or not os.path.exists(out) or _stale(out, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", out, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link failed")
-    return OUT
+    return out
 
 
 if __name__ == "__main__":

@@ -26,7 +26,7 @@ __device__ __forceinline__ float binop(float a, float b) {
   if constexpr (K == K_ADD) return a + b;
   if constexpr (K == K_SUB) return a - b;
   if constexpr (K == K_MUL) return a * b;
-  if constexpr (K == K_AQ) return a * rsqrtf(fmaf(b, b, 1.0f));
+  if constexpr (K == K_AQ) return a * rsqrt_approx(fmaf(b, b, 1.0f));
   if constexpr (K == K_DIV) return a / b;
   if constexpr (K == K_POW) return powf(a, b);
   return 0.f;
@@ -51,7 +51,7 @@ __device__ __forceinline__ void binop_rows(const float (&a)[R], const float (&b)
       if constexpr (K == K_MUL) v = __fmul2_rn(x, y);
       if constexpr (K == K_AQ) {
         const float2 q = __ffma2_rn(y, y, make_float2(1.0f, 1.0f));
-        v = __fmul2_rn(x, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+        v = __fmul2_rn(x, make_float2(rsqrt_approx(q.x), rsqrt_approx(q.y)));
       }
       o[2 * i] = v.x;
       o[2 * i + 1] = v.y;
@@ -159,9 +159,31 @@ __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
 
 constexpr uint32_t ABS_MASK = 0x7fffffffu;
 
+// exp on the R rows of a lane: the own form of gmath.cuh (exp_ex2), on row
+// pairs as packed instructions when R is even; a group whose largest |x|
+// exceeds 87 (or is NaN in every row) takes the library function.
+template <int R>
+__device__ __forceinline__ void exp_rows(float (&A)[R]) {
+  float mx = fabsf(A[0]);
+#pragma unroll
+  for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
+  if (__builtin_expect(!(mx <= EXP_RANGE), 0)) {
+    unop_cold_rows<U_EXP, R>(A);
+  } else if constexpr (R % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const float2 v = exp_ex2_2(make_float2(A[2 * i], A[2 * i + 1]));
+      A[2 * i] = v.x;
+      A[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[r] = exp_ex2(A[r]);
+  }
+}
+
 // A unary operator on the R rows of a lane (compile-time operator; the
-// interpreter's switch calls the shared bodies above directly).  exp is the
-// library function.
+// interpreter's switch calls the shared bodies above directly).
 template <int U, int R>
 __device__ __forceinline__ void unop_rows(float (&A)[R]) {
   if constexpr (U == U_SIN || U == U_COS) {
@@ -172,6 +194,8 @@ __device__ __forceinline__ void unop_rows(float (&A)[R]) {
     logsqrt_rows<R, false>(A, U == U_SQRT_ABS ? ABS_MASK : ~0u);
   } else if constexpr (U == U_SQUARE) {
     binop_rows<K_MUL, R>(A, A, A);
+  } else if constexpr (U == U_EXP) {
+    exp_rows<R>(A);
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) A[r] = unop<U>(A[r]);
@@ -220,6 +244,11 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
     reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// The feature row `byte_off` bytes past xs (the staged words' offsets).
+__device__ __forceinline__ const float* feature_at(const float* xs, uint32_t byte_off) {
+  return reinterpret_cast<const float*>(reinterpret_cast<const char*>(xs) + byte_off);
+}
+
 // Run one packed program on R rows per lane.  `prog` is the warp's copy of
 // the program in shared memory (word, const bits) with a NOP at [L];
 // `xs` points at row r0 of feature 0 of the tile, features `ts` floats
@@ -232,8 +261,9 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
 // lane.  The first instruction of every program loads A without a push.
 // With PRESCALED the words are in the staged form the batched kernel
 // writes: .x holds the opcode alone and, for an instruction that reads a
-// feature, .y holds the feature's offset in floats (feature x ts) in place
-// of the unused constant, so the decode needs neither a mask nor a shift.  With TAPE the R values of A after
+// feature, .y holds the feature's offset in bytes (4 x feature x ts) in
+// place of the unused constant, so the decode needs neither a mask nor a
+// shift.  With TAPE the R values of A after
 // instruction k are stored at tape[32 R k] (the caller offsets `tape` by its
 // lane's R rows): the forward half of the adjoint.  POW adds the pow
 // instructions; without it the program must not contain them.
@@ -249,7 +279,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     // load without a push exactly there), so it is peeled off the switch
     const uint2 first = prog[0];
     if ((PRESCALED ? first.x : first.x & 0xffu) == I_LDF0) {
-      load_rows<R>(PRESCALED ? xs + first.y : xs + (first.x >> 8) * ts, A);
+      load_rows<R>(PRESCALED ? feature_at(xs, first.y) : xs + (first.x >> 8) * ts, A);
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = __uint_as_float(first.y);
@@ -261,7 +291,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     const uint2 nxt = prog[k + 1];
     const uint32_t opc = PRESCALED ? ins.x : ins.x & 0xffu;
     const float c = __uint_as_float(ins.y);
-    const float* xf = PRESCALED ? xs + ins.y : xs + (ins.x >> 8) * ts;
+    const float* xf = PRESCALED ? feature_at(xs, ins.y) : xs + (ins.x >> 8) * ts;
     float t[R];
 
 #define GG_ROWS _Pragma("unroll") for (int r = 0; r < R; ++r)
@@ -512,5 +542,101 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// ---------------------------------------- the PTX interpreter (fast path)
+// interp_asm<R> (generated by interp_gen.py, included from the build
+// folder) runs a staged program from the instruction at shared address pc
+// on R rows per lane: the same operations as run_program<R, false, true>,
+// dispatched through an indexed branch instead of a compare tree.  It
+// returns at the program's NOP, and at an instruction it leaves to the C++
+// code below: pow, or a unary operator whose rows fall outside the domain
+// of its own-math form (the CUDA library function then takes the group of
+// rows, as run_program decides).  pc then addresses the next instruction,
+// sp the lane's next free stack slot.
+#include "interp_asm.inc"
+
+// One instruction the PTX interpreter left (opcode `code`, operand word
+// `arg`), run by the C++ bodies of run_program.  Out of line: the rare
+// cases stay off the hot loop's instruction stream.
+template <int R, bool POW>
+__device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R],
+                                       uint32_t& sp, const float* xs) {
+  constexpr uint32_t SLOTB = 32 * R * 4;
+  switch (code) {
+    case I_UN + U_SIN:
+    case I_UN + U_COS:
+      sincos_rows<R>(A, (int)(code - (I_UN + U_SIN)));
+      break;
+    case I_UN + U_EXP:
+      exp_rows<R>(A);
+      break;
+    case I_UN + U_LOG_ABS:
+    case I_UN + U_LOG:
+      logsqrt_rows<R, true>(A, code == I_UN + U_LOG ? ~0u : ABS_MASK);
+      break;
+    case I_UN + U_SQRT_ABS:
+    case I_UN + U_SQRT:
+      logsqrt_rows<R, false>(A, code == I_UN + U_SQRT ? ~0u : ABS_MASK);
+      break;
+    default:
+      if constexpr (POW) {
+        // pow(left, right): the operands into (A, t) = (left, right)
+        float t[R];
+        const float c = __uint_as_float(arg);
+        const float* xf = feature_at(xs, arg);
+        switch (code) {
+          case I_PW + 0:  // A = pow(A, X[f])
+            load_rows<R>(xf, t);
+            break;
+          case I_PW + 1:  // A = pow(A, c)
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[r] = c;
+            break;
+          case I_PW + 2:  // A = pow(X[f], A)
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[r] = A[r];
+            load_rows<R>(xf, A);
+            break;
+          case I_PW + 3:  // A = pow(c, A)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              t[r] = A[r];
+              A[r] = c;
+            }
+            break;
+          case I_PWS:  // A = pow(pop, A)
+            sp -= SLOTB;
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[r] = A[r];
+            load_rows<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), A);
+            break;
+          default:  // I_PWR: A = pow(A, pop)
+            sp -= SLOTB;
+            load_rows<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), t);
+            break;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) A[r] = binop<K_POW>(A[r], t[r]);
+      }
+      break;
+  }
+}
+
+// Run a staged program (words as run_program's PRESCALED form, a NOP after
+// the last instruction and one readable word after that) on R rows per lane:
+// `xs` is this lane's first row of feature 0 in the tile, `stk` this lane's
+// entry in stack slot 0.
+template <int R, bool POW>
+__device__ __forceinline__ void run_program_fast(const uint2* __restrict__ prog,
+                                                 const float* __restrict__ xs, float (&A)[R],
+                                                 float* __restrict__ stk) {
+  uint32_t pc = smem_u32(prog), sp = smem_u32(stk), code = 0, arg = 0;
+  const uint32_t xb = smem_u32(xs);
+  for (;;) {
+    interp_asm<R>(A, pc, sp, xb, code, arg);
+    if (code == I_NOP || code >= I_COUNT) break;
+    exec_cold<R, POW>(code, arg, A, sp, xs);
+  }
+}
 
 }  // namespace gg

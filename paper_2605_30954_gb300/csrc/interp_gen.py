@@ -493,7 +493,9 @@ def emit(R: int) -> str:
             f"__device__ __forceinline__ void interp_asm<{R}>(float (&A)[{R}], uint32_t& pc,\n"
             f"    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg) {{\n"
             f"  asm volatile(\n{body}\n"
-XX
+            f'      : "+r"(pc), "+r"(sp), "+r"(code), "+r"(arg), {outs}\n'
+            f'      : "r"(xs)\n'
+            f'      : "memory");\n'
             f"}}\n")
 
 

@@ -71,11 +71,13 @@ struct FwdParams {
 constexpr int NPART = 8;
 
 // two tile buffers, one stack of `slots` x 32 lanes x R floats per warp, one
-// program buffer per warp, two mbarriers, two 4-int control blocks
+// program buffer of lstride + 1 words per warp (the interpreter reads one
+// word past the NOP that ends a program), two mbarriers, two 4-int control
+// blocks
 __host__ __device__ inline size_t fwd_smem_bytes(int F, int tile_rows, int warps, int lstride,
                                                  int slots, int R) {
   return 2 * (size_t)(F + 1) * tile_rows * 4 + (size_t)warps * slots * 32 * R * 4 +
-         (size_t)warps * lstride * 8 + 16 + 32;
+         (size_t)warps * (lstride + 1) * 8 + 16 + 32;
 }
 
 template <int R, bool MASK>
@@ -217,8 +219,8 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
   float* stacks = xsb + 2 * tile_floats;
   float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * R;  // this lane, slot 0
   uint2* progs = reinterpret_cast<uint2*>(stacks + (size_t)nw * p.slots * 32 * R);
-  uint2* wprog = progs + (size_t)warp * p.lstride;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(progs + (size_t)nw * p.lstride);
+  uint2* wprog = progs + (size_t)warp * (p.lstride + 1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(progs + (size_t)nw * (p.lstride + 1));
   int* ctl = reinterpret_cast<int*>(bar + 2);
 
   // the finaliser behind this kernel may launch now: it waits for this
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       const int trial = g * group + t;
       if (t >= group || trial >= P) break;
       // stage the program: the opcode alone in .x and, for an instruction
-      // that reads a feature, the feature's offset in the tile in .y;
+      // that reads a feature, the feature's byte offset in the tile in .y;
       // a trial another tile has already found non-finite is skipped (its
       // fitness is +inf whatever the other tiles hold).  The first 32 words
       // of the program slot are loaded together with the length and the
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       for (int k = lane; k <= L; k += 32) {
         uint2 w = k < 32 ? w0 : src[k];
         const uint32_t op = w.x & 0xffu;
-        if (reads_feature(op)) w.y = (w.x >> 8) * (uint32_t)p.tile_rows;
+        if (reads_feature(op)) w.y = (w.x >> 8) * (uint32_t)p.tile_rows * 4u;
         w.x = op;
         wprog[k] = w;
       }
@@ -288,7 +290,11 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
+#ifdef GG_INTERP_CXX
         run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk);
+#else
+        run_program_fast<R, POW>(wprog, xs + r0, A, stk);
+#endif
         const int valid = nrows - r0;  // rows of this lane inside the tile
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
@@ -413,7 +419,7 @@ inline int variant_rows(int v) { return (v == 0 || v == 4 || v == 7) ? 8 : 4; }
 inline int rows_variant(int v) { return variant_rows(v) == 8 ? 7 : 3; }
 // variants a caller may choose for the fitness path (no per-row output)
 inline bool fitness_variant(int v) { return v >= 0 && v < 7 && v != 3; }
-inline int variant_max_warps(int v) { return fwd_max_threads(v >= 4 ? 2 : 1) / 32; }
+inline int variant_max_warps(int v) { return fwd_max_threads(v >= 4 && v <= 6 ? 2 : 1) / 32; }
 inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
 
 }  // namespace gg

