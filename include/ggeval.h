@@ -172,6 +172,33 @@ ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* batch,
                                 uint32_t flags, float* smse, float* a, float* b,
                                 float* mse, void* stream);
 
+/* Outputs of ggeval_evaluate, each an array of n values in the batch's
+ * memory (device or host, as the batch); every pointer but smse may be
+ * NULL.  smse, a, b and mse as for ggeval_eval_batch; nmse = mse / Var(y)
+ * (Eq. 2, population variance); size = the number of active nodes of each
+ * trial (the size objective of multi-objective GP, which the Conclusion
+ * names as future work: error and size come from the same launch
+ * sequence, the size from the packer that linearises the trial anyway);
+ * size_evaluated = the nodes evaluated on every row after constant
+ * subtrees are folded (equal to size with GGEVAL_F_NO_FOLD).  An invalid
+ * trial gets NaN in the float outputs and -1 in the sizes. */
+typedef struct {
+  float* smse;
+  float* a;
+  float* b;
+  float* mse;
+  float* nmse;
+  int32_t* size;
+  int32_t* size_evaluated;
+} ggeval_outputs;
+
+/* ggeval_eval_batch with every output: error objectives (scaled MSE, MSE,
+ * NMSE) and the size objective of each trial in one launch sequence
+ * (pack, batched forward, finalise).  Flags and errors as for
+ * ggeval_eval_batch. */
+ggeval_status ggeval_evaluate(ggeval_dataset* ds, const ggeval_batch* batch, uint32_t flags,
+                              const ggeval_outputs* out, void* stream);
+
 /* Per-row values f_i of every trial (float [n][n_rows], batch memory), the
  * quantity each "sub-evaluation" of Section 3.2 squares.  For checking and
  * for building targets: it runs the launch configuration ggeval_eval_batch
@@ -233,6 +260,17 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* batch,
  * of the fitness sums.  Errors: ERR_ARG (bad configuration, empty batch). */
 ggeval_status ggeval_tile_config(ggeval_dataset* ds, const ggeval_batch* batch,
                                  uint32_t flags, const int32_t* set, int32_t* get);
+
+/* Issue-rate microbenchmarks for the roofline denominators (not part of
+ * the evaluation): on `device`, long chains of independent operations, 64
+ * warps per SM, timed with CUDA events on the legacy default stream.
+ * ops_per_s is double [6]: scalar FP32 FMA, packed two-row FMA (counted as
+ * two operations), and the SFU's reciprocal square root, base-2
+ * exponential, base-2 logarithm and sine.  Divide by the SM count and the
+ * SM clock for operations per SM per clock.  `iters` sets the chain length
+ * (the FP32 chains; the SFU chains run iters / 8).  Synchronous.
+ * Errors: ERR_ARG, ERR_CUDA. */
+ggeval_status ggeval_pipe_rates(int32_t device, int32_t iters, double* ops_per_s);
 
 /* Wait for the dataset's work on `stream`, then report and clear the
  * device-side status: GGEVAL_OK, ERR_TEMPLATE, ERR_TIMEOUT or ERR_CHECKED. */

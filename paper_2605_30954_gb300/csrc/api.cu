@@ -102,11 +102,27 @@ struct Plan {
   const void* fn = nullptr;
 };
 
+// the outputs of one evaluation call (any but smse may be null)
+struct Outs {
+  float* f[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // smse, a, b, mse, nmse
+  int32_t* size = nullptr;
+  int32_t* size_eval = nullptr;
+};
+
+Outs outs_of(float* smse, float* a, float* bb, float* mse) {
+  Outs o;
+  o.f[0] = smse;
+  o.f[1] = a;
+  o.f[2] = bb;
+  o.f[3] = mse;
+  return o;
+}
+
 struct GraphKey {
   ggeval_batch b;
   uint32_t flags;
   const void* mask;
-  const void* out[4];
+  const void* out[7];
   const void* ws[8];  // workspace buffers the captured launches point at
   Cfg cfg;
   int kind;
@@ -334,7 +350,8 @@ ggeval_status launch_overlapped(const void* fn, dim3 grid, dim3 block, size_t sm
 
 ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_max, int layout,
                            const Plan& pl, bool with_aux, cudaStream_t st,
-                           const int* count = nullptr, const int* idx = nullptr) {
+                           const int* count = nullptr, const int* idx = nullptr,
+                           int32_t* size = nullptr, int32_t* size_eval = nullptr) {
   gg::PackParams pp{};
   pp.op = db.op;
   pp.cval = db.cval;
@@ -354,6 +371,8 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
   pp.idx = idx;
   pp.allow_pow = pl.pow ? 1 : 0;
   pp.fold = pl.fold ? 1 : 0;
+  pp.size_active = size;
+  pp.size_eval = size_eval;
   return launch(gg::pack_ptr(), dim3((n + gg::PACK_WARPS - 1) / gg::PACK_WARPS),
                 dim3(32 * gg::PACK_WARPS), gg::PACK_WARPS * gg::pack_warp_bytes(pl.stride), st,
                 &pp);
@@ -409,9 +428,8 @@ constexpr size_t PROF_MAX = 4096;
 // 0 .. count-1 on the device (counters[2] = count, ds->idx = their indices), so
 // the forward kernel's work items cover only them.
 ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_batch* b,
-                           const Plan& pl, float* smse, float* a, float* bb, float* mse,
-                           bool with_aux, cudaStream_t st, bool profile = false,
-                           const uint8_t* mask = nullptr) {
+                           const Plan& pl, const Outs& o, bool with_aux, cudaStream_t st,
+                           bool profile = false, const uint8_t* mask = nullptr) {
   const int n = b->n;
   // counters[0]: the work counter; counters[2]: the compacted count;
   // counters[8 + slot]: the slot's trial found non-finite
@@ -429,7 +447,8 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
     count = ds->counters + 2;
     idx = ds->idx;
   }
-  GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st, count, idx));
+  GG_TRY(enqueue_pack(ds, db, n, b->max_height, b->layout, pl, with_aux, st, count, idx,
+                      o.size, o.size_eval));
   gg::FwdParams fp = fwd_params(ds, n, pl);
   fp.dead = ds->counters + 8;
   fp.count = count;
@@ -449,7 +468,8 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   if (ev) GG_TRY(launch(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   else GG_TRY(launch_overlapped(pl.fn, dim3(pl.grid), dim3(pl.cfg.warps * 32), pl.smem, st, &fp));
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
-  gg::FinParams q = fin_params(ds, n, pl, smse, a, bb, mse);
+  gg::FinParams q = fin_params(ds, n, pl, o.f[0], o.f[1], o.f[2], o.f[3]);
+  q.nmse = o.f[4];
   q.dead = fp.dead;
   q.count = count;
   q.idx = idx;
@@ -601,12 +621,21 @@ void ggeval_destroy(ggeval_dataset* ds) {
 }
 
 static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
-                                     float* smse, float* a, float* bb, float* mse, void* stream,
-                                     const uint8_t* mask);
+                                     const Outs& o, void* stream, const uint8_t* mask);
 
 ggeval_status ggeval_eval_batch(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
                                 float* smse, float* a, float* bb, float* mse, void* stream) {
-  return eval_batch_impl(ds, b, flags, smse, a, bb, mse, stream, nullptr);
+  return eval_batch_impl(ds, b, flags, outs_of(smse, a, bb, mse), stream, nullptr);
+}
+
+ggeval_status ggeval_evaluate(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
+                              const ggeval_outputs* out, void* stream) {
+  if (!out) return fail(GGEVAL_ERR_ARG, "outputs is NULL");
+  Outs o = outs_of(out->smse, out->a, out->b, out->mse);
+  o.f[4] = out->nmse;
+  o.size = out->size;
+  o.size_eval = out->size_evaluated;
+  return eval_batch_impl(ds, b, flags, o, stream, nullptr);
 }
 
 ggeval_status ggeval_eval_batch_masked(ggeval_dataset* ds, const ggeval_batch* b,
@@ -615,15 +644,14 @@ ggeval_status ggeval_eval_batch_masked(ggeval_dataset* ds, const ggeval_batch* b
   if (!mask) return fail(GGEVAL_ERR_ARG, "mask is NULL");
   if (b && b->memory != GGEVAL_MEM_DEVICE)
     return fail(GGEVAL_ERR_ARG, "eval_batch_masked needs a device batch");
-  return eval_batch_impl(ds, b, flags, smse, a, bb, mse, stream, mask);
+  return eval_batch_impl(ds, b, flags, outs_of(smse, a, bb, mse), stream, mask);
 }
 
 static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
-                                     float* smse, float* a, float* bb, float* mse, void* stream,
-                                     const uint8_t* mask) {
+                                     const Outs& o, void* stream, const uint8_t* mask) {
   GG_TRY(check_batch(ds, b));
   if (b->n == 0) return GGEVAL_OK;
-  if (!smse) return fail(GGEVAL_ERR_ARG, "smse is NULL");
+  if (!o.f[0]) return fail(GGEVAL_ERR_ARG, "smse is NULL");
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan pl;
@@ -633,11 +661,16 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
   const bool host = b->memory == GGEVAL_MEM_HOST;
   DevBatch db;
   unsigned char* scratch = nullptr;
-  GG_TRY(stage_batch(ds, b, host ? (size_t)b->n * 16 : 0, st, &db, &scratch));
-  float* outs[4] = {smse, a, bb, mse};
-  float* dev[4] = {smse, a, bb, mse};
-  if (host)
-    for (int i = 0; i < 4; ++i) dev[i] = outs[i] ? reinterpret_cast<float*>(scratch) + (size_t)i * b->n : nullptr;
+  // a host batch's outputs are written to device staging first: 7 arrays of
+  // n 4-byte values
+  GG_TRY(stage_batch(ds, b, host ? (size_t)b->n * 4 * 7 : 0, st, &db, &scratch));
+  Outs dev = o;
+  if (host) {
+    auto slot = [&](int i) { return scratch + (size_t)i * b->n * 4; };
+    for (int i = 0; i < 5; ++i) dev.f[i] = o.f[i] ? reinterpret_cast<float*>(slot(i)) : nullptr;
+    dev.size = o.size ? reinterpret_cast<int32_t*>(slot(5)) : nullptr;
+    dev.size_eval = o.size_eval ? reinterpret_cast<int32_t*>(slot(6)) : nullptr;
+  }
 
   if ((flags & GGEVAL_F_GRAPH) && !host) {
     GraphKey key;
@@ -645,7 +678,9 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
     key.b = *b;
     key.flags = flags;
     key.mask = mask;
-    for (int i = 0; i < 4; ++i) key.out[i] = outs[i];
+    for (int i = 0; i < 5; ++i) key.out[i] = o.f[i];
+    key.out[5] = o.size;
+    key.out[6] = o.size_eval;
     const void* ws[8] = {ds->prog, ds->len,   ds->part,   ds->ab,
                          ds->counters, ds->stage, ds->status, ds->idx};
     std::memcpy(key.ws, ws, sizeof ws);
@@ -655,8 +690,7 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
       drop_graph(ds);
       cudaGraph_t g = nullptr;
       GG_CU(cudaStreamBeginCapture(ds->cap_stream, cudaStreamCaptureModeThreadLocal));
-      ggeval_status s = enqueue_eval(ds, db, b, pl, dev[0], dev[1], dev[2], dev[3], false,
-                                     ds->cap_stream, false, mask);
+      ggeval_status s = enqueue_eval(ds, db, b, pl, dev, false, ds->cap_stream, false, mask);
       cudaError_t e = cudaStreamEndCapture(ds->cap_stream, &g);
       if (s != GGEVAL_OK) {
         if (g) cudaGraphDestroy(g);
@@ -674,12 +708,17 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
     GG_CU(cudaGraphLaunch(ds->gexec, st));
     return GGEVAL_OK;
   }
-  GG_TRY(enqueue_eval(ds, db, b, pl, dev[0], dev[1], dev[2], dev[3], false, st,
-                      (flags & GGEVAL_F_PROFILE) != 0, mask));
-  if (host)
-    for (int i = 0; i < 4; ++i)
-      if (outs[i])
-        GG_CU(cudaMemcpyAsync(outs[i], dev[i], (size_t)b->n * 4, cudaMemcpyDeviceToHost, st));
+  GG_TRY(enqueue_eval(ds, db, b, pl, dev, false, st, (flags & GGEVAL_F_PROFILE) != 0, mask));
+  if (host) {
+    for (int i = 0; i < 5; ++i)
+      if (o.f[i])
+        GG_CU(cudaMemcpyAsync(o.f[i], dev.f[i], (size_t)b->n * 4, cudaMemcpyDeviceToHost, st));
+    if (o.size)
+      GG_CU(cudaMemcpyAsync(o.size, dev.size, (size_t)b->n * 4, cudaMemcpyDeviceToHost, st));
+    if (o.size_eval)
+      GG_CU(cudaMemcpyAsync(o.size_eval, dev.size_eval, (size_t)b->n * 4,
+                            cudaMemcpyDeviceToHost, st));
+  }
   return GGEVAL_OK;
 }
 
@@ -768,7 +807,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   GG_TRY(stage_batch(ds, b, host ? gcount * 4 + (size_t)b->n * 4 : 0, st, &db, &scratch));
   float* dg = host ? reinterpret_cast<float*>(scratch) : dcval;
   float* ds_smse = smse ? (host ? dg + gcount : smse) : nullptr;
-  GG_TRY(enqueue_eval(ds, db, b, pl, ds_smse, nullptr, nullptr, nullptr, true, st));
+  GG_TRY(enqueue_eval(ds, db, b, pl, outs_of(ds_smse, nullptr, nullptr, nullptr), true, st));
   // adjoint.  Each warp holds its own copy of the program, R rows x 32 lanes
   // of values per instruction and its stack, so shared memory bounds the
   // resident warps.  For each R (rows per lane) take the CTA size (1..8
@@ -925,13 +964,13 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
     if (make_plan(ds, b->n, b->max_height, c, &pl, has_pow(flags)) != GGEVAL_OK) continue;
     pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
     if ((result = ensure_ws(ds, b->n, pl, false)) != GGEVAL_OK) break;
-    if ((result = enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st)) !=
-        GGEVAL_OK)
+    if ((result = enqueue_eval(ds, db, b, pl, outs_of(out, nullptr, nullptr, nullptr), false,
+                               st)) != GGEVAL_OK)
       break;
     const int reps = best_ms < 40.f ? 2 : 1;  // one timed run for slow batches
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps; ++r)
-      enqueue_eval(ds, db, b, pl, out, nullptr, nullptr, nullptr, false, st);
+      enqueue_eval(ds, db, b, pl, outs_of(out, nullptr, nullptr, nullptr), false, st);
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       result = fail(GGEVAL_ERR_CUDA, "autotune run failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -100,20 +100,29 @@ __device__ __forceinline__ void unop_cold_rows(float (&A)[R]) {
   for (int r = 0; r < R; ++r) A[r] = t.v[r];
 }
 
+// The CUDA library's sin (shift 0) or cos (shift 1), out of line.
+static __device__ __noinline__ float sincos_library(float x, int shift) {
+  return shift ? cosf(x) : sinf(x);
+}
+
 // sin and cos on the R rows of a lane: the branch-free form of gmath.cuh,
 // on row pairs as packed instructions when R is even.  One test of the
 // rows' largest magnitude sends a group with an argument beyond the
-// reduction's range (|x| > 2^17 or inf) to the library function on the
-// cold path (a NaN row stays on the fast path, whose result is NaN too).  `shift` is 0 for sin and
-// 1 for cos (a run-time value in the interpreter: both share one body).
+// reduction's range (|x| > 2^17 or inf, or NaN in every row) to the cold
+// path, which takes the library function for exactly those rows (a row's
+// value depends only on its own argument).  `shift` is 0 for sin and 1 for
+// cos (a run-time value in the interpreter: both share one body).
 template <int R>
 __device__ __forceinline__ void sincos_rows(float (&A)[R], int shift) {
   float mx = fabsf(A[0]);
 #pragma unroll
   for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
   if (__builtin_expect(!(mx <= TRIG_RANGE), 0)) {
-    if (shift) unop_cold_rows<U_COS, R>(A);
-    else unop_cold_rows<U_SIN, R>(A);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      const float x = A[r];
+      A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
+    }
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -129,8 +138,8 @@ __device__ __forceinline__ void sincos_rows(float (&A)[R], int shift) {
 
 // log (LOG) or sqrt on the R rows of a lane, after `mask` is applied to the
 // bits (0x7fffffff for log|x| and sqrt|x|, all ones for the unprotected
-// forms): the branch-free forms of gmath.cuh for positive normal finite
-// arguments, the library function on the cold path otherwise.
+// forms): the branch-free forms of gmath.cuh on row pairs when every row is
+// a positive normal number, else log_total / sqrt_total row by row.
 template <int R, bool LOG>
 __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
   bool special = false;
@@ -141,8 +150,9 @@ __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
     special |= outside_positive_normal(b);
   }
   if (__builtin_expect(special, 0)) {
-    if constexpr (LOG) unop_cold_rows<U_LOG, R>(A);
-    else unop_cold_rows<U_SQRT, R>(A);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      A[r] = LOG ? log_total(__float_as_uint(A[r])) : sqrt_total(A[r]);
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -160,15 +170,16 @@ __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
 constexpr uint32_t ABS_MASK = 0x7fffffffu;
 
 // exp on the R rows of a lane: the own form of gmath.cuh (exp_ex2), on row
-// pairs as packed instructions when R is even; a group whose largest |x|
-// exceeds 87 (or is NaN in every row) takes the library function.
+// pairs as packed instructions when every |x| <= 87, else exp_total row by
+// row.
 template <int R>
 __device__ __forceinline__ void exp_rows(float (&A)[R]) {
   float mx = fabsf(A[0]);
 #pragma unroll
   for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
   if (__builtin_expect(!(mx <= EXP_RANGE), 0)) {
-    unop_cold_rows<U_EXP, R>(A);
+#pragma unroll
+    for (int r = 0; r < R; ++r) A[r] = exp_total(A[r]);
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -556,28 +567,26 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 #include "interp_asm.inc"
 
 // One instruction the PTX interpreter left (opcode `code`, operand word
-// `arg`), run by the C++ bodies of run_program.  Out of line: the rare
-// cases stay off the hot loop's instruction stream.
+// `arg`), run by the C++ bodies of run_program: sin or cos with an argument
+// beyond the reduction's range, and pow.  Out of line: the rare cases stay
+// off the hot loop's instruction stream.
 template <int R, bool POW>
 __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R],
                                        uint32_t& sp, const float* xs) {
   constexpr uint32_t SLOTB = 32 * R * 4;
   switch (code) {
     case I_UN + U_SIN:
-    case I_UN + U_COS:
-      sincos_rows<R>(A, (int)(code - (I_UN + U_SIN)));
+    case I_UN + U_COS: {
+      // sincos_rows' cold branch, one row at a time: loops left rolled keep
+      // this callee's registers (which the caller saves around the call) few
+      const int shift = (int)(code - (I_UN + U_SIN));
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const float x = A[r];
+        A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
+      }
       break;
-    case I_UN + U_EXP:
-      exp_rows<R>(A);
-      break;
-    case I_UN + U_LOG_ABS:
-    case I_UN + U_LOG:
-      logsqrt_rows<R, true>(A, code == I_UN + U_LOG ? ~0u : ABS_MASK);
-      break;
-    case I_UN + U_SQRT_ABS:
-    case I_UN + U_SQRT:
-      logsqrt_rows<R, false>(A, code == I_UN + U_SQRT ? ~0u : ABS_MASK);
-      break;
+    }
     default:
       if constexpr (POW) {
         // pow(left, right): the operands into (A, t) = (left, right)
@@ -615,7 +624,7 @@ __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R
             load_rows<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), t);
             break;
         }
-#pragma unroll
+#pragma unroll 1
         for (int r = 0; r < R; ++r) A[r] = binop<K_POW>(A[r], t[r]);
       }
       break;

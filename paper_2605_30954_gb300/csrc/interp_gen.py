@@ -11,12 +11,13 @@ inline-PTX statement: every case ends by fetching the next instruction word
 
 Semantics are those of ``run_program`` in device.cuh, bit for bit: the same
 FP32 operations in the same order, two rows at a time as packed
-``.f32x2`` instructions.  Instructions the PTX does not finish leave the
-statement with their opcode, and the C++ caller runs them (``exec_cold``)
-and re-enters: the end of the program (NOP), pow, and a unary operator whose
-arguments fall outside the domain of its own-math form (the CUDA library
-function then takes the whole group of rows, exactly as ``run_program``
-decides).
+``.f32x2`` instructions, and row by row (gmath.cuh's ``*_total`` forms) for
+a group of rows in which some argument lies outside the common domain of
+exp, log or sqrt.  Instructions the PTX does not finish leave the statement
+with their opcode, and the C++ caller runs them (``exec_cold``) and
+re-enters: the end of the program (NOP), pow, and sin or cos with an
+argument beyond the reduction's range (the CUDA library function then takes
+those rows).
 
 Run by build.py before the CUDA sources are compiled; writes
 ``_build/gen/interp_asm.inc``.
@@ -212,10 +213,8 @@ class Gen:
         self.label("GG_SINCOS")
         self.unpack_a("x")
         for r in range(R):
-            self.o(f"abs.f32 y{r}, x{r};")
-        self.o("mov.f32 m, y0;")
-        for r in range(1, R):
-            self.o(f"max.f32 m, m, y{r};")
+            self.o(f"abs.f32 s0, x{r};")
+            self.o("mov.f32 m, s0;" if r == 0 else "max.f32 m, m, s0;")
         self.o(f"setp.gtu.f32 p, m, {f(TRIG_RANGE)};")
         self.o("@p bra GG_EXIT;")
         for i in range(NP):
@@ -263,83 +262,189 @@ class Gen:
             self.o(f"mov.b64 a{i}, {{z0, z1}};")
         self.next()
 
-    def logsqrt_check(self):
-        """Apply the mask (|x| or x) to every row's bits into b0..; leave for
-        the cold path (with A unchanged) unless every row is a positive
-        normal finite number."""
+    def logsqrt_check(self, special):
+        """Apply the mask (|x| or x) to every row's bits into b0..; go to the
+        row-by-row body `special` unless every row is a positive normal
+        finite number."""
         R = self.R
         self.unpack_a("x")
         for r in range(R):
             self.o(f"mov.b32 b{r}, x{r};")
             self.o(f"and.b32 b{r}, b{r}, msk;")
-            self.o(f"sub.u32 d{r}, b{r}, 0x00800000;")
-        self.o("mov.u32 mm, d0;")
-        for r in range(1, R):
-            self.o(f"max.u32 mm, mm, d{r};")
+            self.o(f"sub.u32 k, b{r}, 0x00800000;")
+            self.o("mov.u32 mm, k;" if r == 0 else "max.u32 mm, mm, k;")
         self.o("setp.ge.u32 p, mm, 0x7F000000;")
-        self.o("@p bra GG_EXIT;")
+        self.o(f"@p bra {special};")
+
+    def repack_x(self):
+        for i in range(self.NP):
+            self.o(f"mov.b64 a{i}, {{x{2 * i}, x{2 * i + 1}}};")
+
+    def log_special_body(self):
+        """gmath.cuh log_total row by row, on row pairs (each half of a packed
+        operation rounds as the scalar one): a zero or subnormal argument is
+        scaled by 2^24 with the exponent corrected, then the special values
+        replace the results of zeros, infinities, NaN and negatives."""
+        self.label("GG_LOG_SP")
+        o = self.o
+        for i in range(self.NP):
+            for e in (0, 1):
+                r = 2 * i + e
+                o(f"setp.lt.u32 p, b{r}, 0x00800000;")         # subnormal or zero
+                o(f"mov.b32 s0, b{r};")
+                o(f"mul.rn.f32 s1, s0, {f('16777216.0')};")
+                o(f"selp.f32 s0, s1, s0, p;")                   # x, scaled by 2^24
+                o("selp.s32 ea, -24, 0, p;")
+                o("mov.b32 k, s0;")
+                o(f"sub.s32 kk, k, {SQRT_HALF_BITS};")
+                o(f"shr.s32 e{e}, kk, 23;")
+                o(f"shl.b32 kk, e{e}, 23;")
+                o("sub.s32 kk, k, kk;")
+                o(f"mov.b32 z{e}, kk;")                         # m
+                o(f"add.s32 ee, e{e}, ea;")
+                o(f"cvt.rn.f32.s32 w{e}, ee;")
+            self.log_pair(i)
+            o(f"mov.b64 {{s0, s1}}, a{i};")
+            for e in (0, 1):
+                r = 2 * i + e
+                o(f"and.b32 k, b{r}, 0x7FFFFFFF;")
+                o("setp.eq.u32 p, k, 0;")
+                o(f"selp.f32 s{e}, 0fFF800000, s{e}, p;")       # log(+-0) = -inf
+                o(f"setp.eq.u32 p, b{r}, 0x7F800000;")
+                o(f"selp.f32 s{e}, 0f7F800000, s{e}, p;")       # log(inf) = inf
+                o(f"setp.gt.u32 p, b{r}, 0x7F800000;")
+                o(f"selp.f32 s{e}, 0f7FFFFFFF, s{e}, p;")       # NaN, negatives: NaN
+            o(f"mov.b64 a{i}, {{s0, s1}};")
+        self.next()
+
+    def sqrt_special_body(self):
+        """gmath.cuh sqrt_total row by row: the Newton form on positive
+        normal rows, the IEEE square root on the others."""
+        self.label("GG_SQRT_SP")
+        o = self.o
+        for i in range(self.NP):
+            self.sqrt_pair(i)
+            o(f"mov.b64 {{s0, s1}}, a{i};")
+            for e in (0, 1):
+                r = 2 * i + e
+                o(f"mov.b32 s2, b{r};")
+                o("sqrt.rn.f32 s2, s2;")                       # IEEE
+                o(f"sub.u32 k, b{r}, 0x00800000;")
+                o("setp.lt.u32 p, k, 0x7F000000;")             # positive normal
+                o(f"selp.f32 s{e}, s{e}, s2, p;")
+            o(f"mov.b64 a{i}, {{s0, s1}};")
+        self.next()
+
+    def exp_special_body(self):
+        """gmath.cuh exp_total row by row, on row pairs."""
+        self.label("GG_EXP_SP")
+        o = self.o
+        for i in range(self.NP):
+            o(f"mov.b64 {{x0, x1}}, a{i};")                     # the arguments
+            o(f"mov.b64 c1, {f2(LOG2E_HI)};")
+            o(f"mul.rn.f32x2 v0, a{i}, c1;")                   # hi
+            o(f"mov.b64 c2, {f2('-1.0')};")
+            o("mul.rn.f32x2 v1, v0, c2;")
+            o(f"fma.rn.f32x2 v1, a{i}, c1, v1;")
+            o(f"mov.b64 c2, {f2(LOG2E_LO)};")
+            o(f"fma.rn.f32x2 v1, a{i}, c2, v1;")               # lo
+            o(f"mov.b64 c2, {f2('0.5')};")
+            o("mul.rn.f32x2 v2, v0, c2;")                      # hi / 2
+            o("mov.b64 {z0, z1}, v0;")
+            o("mov.b64 {z2, z3}, v2;")
+            for e in (0, 1):
+                o(f"ex2.approx.f32 s{e}, z{e};")               # 2^hi
+                o(f"ex2.approx.f32 s{2 + e}, z{2 + e};")
+                o(f"mul.rn.f32 s{2 + e}, s{2 + e}, s{2 + e};")   # (2^(hi/2))^2
+                o(f"abs.f32 s4, x{e};")
+                o(f"setp.le.f32 p, s4, {f(EXP_RANGE)};")
+                o(f"selp.f32 s{e}, s{e}, s{2 + e}, p;")
+            o("mov.b64 v0, {s0, s1};")                         # e
+            o(f"mov.b64 c1, {f2(LN2_HI)};")
+            o("mul.rn.f32x2 v1, v1, c1;")
+            o("fma.rn.f32x2 v0, v0, v1, v0;")
+            o("mov.b64 {s0, s1}, v0;")
+            for e in (0, 1):
+                o(f"setp.eq.f32 p, x{e}, 0f7F800000;")
+                o(f"selp.f32 s{e}, 0f7F800000, s{e}, p;")       # exp(inf) = inf
+                o(f"setp.eq.f32 p, x{e}, 0fFF800000;")
+                o(f"selp.f32 s{e}, 0f00000000, s{e}, p;")       # exp(-inf) = 0
+            o(f"mov.b64 a{i}, {{s0, s1}};")
+        self.next()
+
+    def log_pair(self, i):
+        """log_normal2 of pair i from m in (z0, z1) and the exponents as
+        floats in (w0, w1); the result into a{i}."""
+        o = self.o
+        o("mov.b64 v0, {z0, z1};")                         # m
+        o(f"mov.b64 c1, {f2('-1.0')};")
+        o("add.rn.f32x2 v1, v0, c1;")                      # f = m - 1
+        o(f"mov.b64 c2, {f2('1.0')};")
+        o("add.rn.f32x2 v2, v0, c2;")                      # d = m + 1
+        o("mov.b64 {z0, z1}, v2;")
+        o("rcp.approx.ftz.f32 z0, z0;")
+        o("rcp.approx.ftz.f32 z1, z1;")
+        o("mov.b64 v2, {z0, z1};")                         # rc
+        o("mul.rn.f32x2 v3, v1, v2;")                      # s
+        o(f"mov.b64 c2, {f2('-2.0')};")
+        o("fma.rn.f32x2 v4, v3, c2, v1;")                  # t = fma(s, -2, f)
+        o("mul.rn.f32x2 v5, v3, c1;")                      # -s
+        o("fma.rn.f32x2 v4, v5, v1, v4;")                  # fma(-s, f, t)
+        o("fma.rn.f32x2 v3, v4, v2, v3;")                  # s
+        o("mul.rn.f32x2 v4, v3, v3;")                      # z
+        o(f"mov.b64 c1, {f2(ATANH_C[0])};")
+        o(f"mov.b64 c2, {f2(ATANH_C[1])};")
+        o("fma.rn.f32x2 v5, v4, c1, c2;")                  # p
+        for k in (2, 3):
+            o(f"mov.b64 c1, {f2(ATANH_C[k])};")
+            o("fma.rn.f32x2 v5, v4, v5, c1;")
+        o("mul.rn.f32x2 v0, v3, v4;")                      # s z
+        o("add.rn.f32x2 v1, v3, v3;")                      # s + s
+        o("fma.rn.f32x2 v0, v0, v5, v1;")                  # u
+        o("mov.b64 v1, {w0, w1};")                         # e as float
+        o(f"mov.b64 c1, {f2(LN2_LO)};")
+        o("fma.rn.f32x2 v0, v1, c1, v0;")
+        o(f"mov.b64 c1, {f2(LN2_HI)};")
+        o(f"fma.rn.f32x2 a{i}, v1, c1, v0;")
 
     def log_body(self):
         """gmath.cuh log_normal2 on every pair of the masked rows."""
         self.label("GG_LOG")
-        self.logsqrt_check()
+        self.logsqrt_check("GG_LOG_SP")
+        o = self.o
         for i in range(self.NP):
             for e in (0, 1):
                 r = 2 * i + e
-                self.o(f"sub.s32 k, b{r}, {SQRT_HALF_BITS};")
-                self.o(f"shr.s32 e{e}, k, 23;")
-                self.o(f"shl.b32 k, e{e}, 23;")
-                self.o(f"sub.s32 k, b{r}, k;")
-                self.o(f"mov.b32 z{e}, k;")
-                self.o(f"cvt.rn.f32.s32 w{e}, e{e};")
-            self.o("mov.b64 v0, {z0, z1};")                         # m
-            self.o(f"mov.b64 c1, {f2('-1.0')};")
-            self.o("add.rn.f32x2 v1, v0, c1;")                      # f = m - 1
-            self.o(f"mov.b64 c2, {f2('1.0')};")
-            self.o("add.rn.f32x2 v2, v0, c2;")                      # d = m + 1
-            self.o("mov.b64 {z0, z1}, v2;")
-            self.o("rcp.approx.ftz.f32 z0, z0;")
-            self.o("rcp.approx.ftz.f32 z1, z1;")
-            self.o("mov.b64 v2, {z0, z1};")                         # rc
-            self.o("mul.rn.f32x2 v3, v1, v2;")                      # s
-            self.o(f"mov.b64 c2, {f2('-2.0')};")
-            self.o("fma.rn.f32x2 v4, v3, c2, v1;")                  # t = fma(s, -2, f)
-            self.o("mul.rn.f32x2 v5, v3, c1;")                      # -s
-            self.o("fma.rn.f32x2 v4, v5, v1, v4;")                  # fma(-s, f, t)
-            self.o("fma.rn.f32x2 v3, v4, v2, v3;")                  # s
-            self.o("mul.rn.f32x2 v4, v3, v3;")                      # z
-            self.o(f"mov.b64 c1, {f2(ATANH_C[0])};")
-            self.o(f"mov.b64 c2, {f2(ATANH_C[1])};")
-            self.o("fma.rn.f32x2 v5, v4, c1, c2;")                  # p
-            for k in (2, 3):
-                self.o(f"mov.b64 c1, {f2(ATANH_C[k])};")
-                self.o("fma.rn.f32x2 v5, v4, v5, c1;")
-            self.o("mul.rn.f32x2 v0, v3, v4;")                      # s z
-            self.o("add.rn.f32x2 v1, v3, v3;")                      # s + s
-            self.o("fma.rn.f32x2 v0, v0, v5, v1;")                  # u
-            self.o("mov.b64 v1, {w0, w1};")                         # e as float
-            self.o(f"mov.b64 c1, {f2(LN2_LO)};")
-            self.o("fma.rn.f32x2 v0, v1, c1, v0;")
-            self.o(f"mov.b64 c1, {f2(LN2_HI)};")
-            self.o(f"fma.rn.f32x2 a{i}, v1, c1, v0;")
+                o(f"sub.s32 kk, b{r}, {SQRT_HALF_BITS};")
+                o(f"shr.s32 e{e}, kk, 23;")
+                o(f"shl.b32 kk, e{e}, 23;")
+                o(f"sub.s32 kk, b{r}, kk;")
+                o(f"mov.b32 z{e}, kk;")
+                o(f"cvt.rn.f32.s32 w{e}, e{e};")
+            self.log_pair(i)
         self.next()
+
+    def sqrt_pair(self, i):
+        """sqrt_newton2 of the masked rows of pair i into a{i}."""
+        o = self.o
+        o(f"mov.b64 v0, {{b{2 * i}, b{2 * i + 1}}};")      # x (masked)
+        o(f"rsqrt.approx.f32 z0, b{2 * i};")
+        o(f"rsqrt.approx.f32 z1, b{2 * i + 1};")
+        o("mov.b64 v1, {z0, z1};")                         # rs
+        o("mul.rn.f32x2 v2, v0, v1;")                      # s
+        o(f"mov.b64 c1, {f2('-1.0')};")
+        o("mul.rn.f32x2 v3, v2, c1;")                      # -s
+        o("fma.rn.f32x2 v3, v3, v2, v0;")                  # e
+        o(f"mov.b64 c1, {f2('0.5')};")
+        o("mul.rn.f32x2 v1, c1, v1;")                      # 0.5 rs
+        o(f"fma.rn.f32x2 a{i}, v3, v1, v2;")
 
     def sqrt_body(self):
         """gmath.cuh sqrt_newton2 on every pair of the masked rows."""
         self.label("GG_SQRT")
-        self.logsqrt_check()
+        self.logsqrt_check("GG_SQRT_SP")
         for i in range(self.NP):
-            self.o(f"mov.b64 v0, {{b{2 * i}, b{2 * i + 1}}};")      # x (masked)
-            self.o(f"rsqrt.approx.f32 z0, b{2 * i};")
-            self.o(f"rsqrt.approx.f32 z1, b{2 * i + 1};")
-            self.o("mov.b64 v1, {z0, z1};")                         # rs
-            self.o("mul.rn.f32x2 v2, v0, v1;")                      # s
-            self.o(f"mov.b64 c1, {f2('-1.0')};")
-            self.o("mul.rn.f32x2 v3, v2, c1;")                      # -s
-            self.o("fma.rn.f32x2 v3, v3, v2, v0;")                  # e
-            self.o(f"mov.b64 c1, {f2('0.5')};")
-            self.o("mul.rn.f32x2 v1, c1, v1;")                      # 0.5 rs
-            self.o(f"fma.rn.f32x2 a{i}, v3, v1, v2;")
+            self.sqrt_pair(i)
         self.next()
 
     def exp_body(self):
@@ -349,12 +454,10 @@ class Gen:
         self.label("GG_EXP")
         self.unpack_a("x")
         for r in range(R):
-            self.o(f"abs.f32 y{r}, x{r};")
-        self.o("mov.f32 m, y0;")
-        for r in range(1, R):
-            self.o(f"max.f32 m, m, y{r};")
+            self.o(f"abs.f32 s0, x{r};")
+            self.o("mov.f32 m, s0;" if r == 0 else "max.f32 m, m, s0;")
         self.o(f"setp.gtu.f32 p, m, {f(EXP_RANGE)};")
-        self.o("@p bra GG_EXIT;")
+        self.o("@p bra GG_EXP_SP;")
         for i in range(self.NP):
             self.o(f"mov.b64 c1, {f2(LOG2E_HI)};")
             self.o(f"mul.rn.f32x2 v0, a{i}, c1;")                   # hi
@@ -379,8 +482,9 @@ class Gen:
         o(f".reg .b64 a<{NP}>, t<{NP}>, u<{NP}>, v<6>, c1, c2;")
         o(f".reg .f32 x<{R}>, y<{R}>, w<2>, m;")
         o(f".reg .b32 z<4>, b<{R}>;")
-        o(f".reg .u32 opc, arg, nopc, narg, ad, sh, msk, k, q<2>, mm, d<{R}>;")
-        o(".reg .s32 e<2>;")
+        o(".reg .u32 opc, arg, nopc, narg, ad, sh, msk, k, q<2>, mm;")
+        o(".reg .s32 e<2>, ea, ee, kk;")
+        o(".reg .f32 s<5>;")
         o(".reg .pred p;")
         for i in range(NP):
             o(f"mov.b64 a{i}, {{{self.A[2 * i]}, {self.A[2 * i + 1]}}};")
@@ -473,6 +577,9 @@ class Gen:
         self.log_body()
         self.sqrt_body()
         self.exp_body()
+        self.log_special_body()
+        self.sqrt_special_body()
+        self.exp_special_body()
         # exit: the opcode that stopped and its operand word; pc already
         # points at the next instruction
         self.label("GG_EXIT")

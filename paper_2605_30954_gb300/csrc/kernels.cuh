@@ -22,6 +22,9 @@ struct PackParams {
   const int* idx;        // with count: the trial packed into each slot
   int allow_pow;         // 0: an active pow node makes the trial invalid
   int fold;              // fold constant subtrees (ignored when aux is set)
+  int* size_active;      // [n] by trial, or null: active nodes (-1 if invalid)
+  int* size_eval;        // [n] by trial, or null: nodes evaluated per row after
+                         // folding (a folded subtree counts as one constant)
 };
 
 // pack_kernel (pack.cu): one warp per trial, PACK_WARPS warps per block.
@@ -377,6 +380,7 @@ struct FinParams {
   float* a;
   float* b;
   float* mse;
+  float* nmse;         // nullable: mse / Var(y) (Eq. 2)
   double* ab;          // [P][4]: a* - ybar, b*, finite flag, 0 (adjoint), nullable
   const int* dead;     // [P] or null: 1 for a trial the forward kernel found
                        // non-finite (some of its tile records were skipped)

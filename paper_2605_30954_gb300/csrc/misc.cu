@@ -132,6 +132,10 @@ __global__ void fin_kernel(const FinParams p) {
   if (p.a) p.a[tt] = (float)a;
   if (p.b) p.b[tt] = (float)b;
   if (p.mse) p.mse[tt] = (float)mse;
+  if (p.nmse) {  // Eq. 2: MSE over the population variance of y
+    const double N = (double)p.N;
+    p.nmse[tt] = (float)(mse / ((p.sycyc - p.syc * p.syc / N) / N));
+  }
   if (p.ab) {
     p.ab[4 * tt] = ac;
     p.ab[4 * tt + 1] = bo;

@@ -83,11 +83,16 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
   uint8_t* need = fl + S;
 
   const int h = p.height ? (int)p.height[trial] : p.h_max;
-  if (h < 0 || h > p.h_max) {
+  auto invalid = [&]() {
     if (lane == 0) {
       p.len[t] = -1;
+      if (p.size_active) p.size_active[trial] = -1;
+      if (p.size_eval) p.size_eval[trial] = -1;
       atomicOr(p.status, ST_TEMPLATE);
     }
+  };
+  if (h < 0 || h > p.h_max) {
+    invalid();
     return;
   }
   const int n = (1 << (h + 1)) - 1;
@@ -128,11 +133,14 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
     __syncwarp();
   }
   if (__any_sync(0xffffffffu, bad)) {
-    if (lane == 0) {
-      p.len[t] = -1;
-      atomicOr(p.status, ST_TEMPLATE);
-    }
+    invalid();
     return;
+  }
+  if (p.size_active) {  // the trial's size: its active node count
+    int cnt = 0;
+    for (int i = lane; i < n; i += 32) cnt += (fl[i] & N_ACT) != 0;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) p.size_active[trial] = cnt;
   }
 
   // B: constants, fusion, stack need and instruction counts, bottom-up
@@ -186,10 +194,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
   }
   const int L = size[0];
   if (L > p.lstride - 1 || need[0] > p.max_slots) {
-    if (lane == 0) {
-      p.len[t] = -1;
-      atomicOr(p.status, ST_TEMPLATE);
-    }
+    invalid();
     return;
   }
 
@@ -222,6 +227,13 @@ __global__ void __launch_bounds__(PACK_WARPS * 32) pack_kernel(const PackParams 
       }
     }
     __syncwarp();
+  }
+
+  if (p.size_eval) {  // nodes evaluated per row: active ones not inside a folded subtree
+    int cnt = 0;
+    for (int i = lane; i < n; i += 32) cnt += (fl[i] & N_ACT) && !(fl[i] & N_INSIDE);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) p.size_eval[trial] = cnt;
   }
 
   // D: emission

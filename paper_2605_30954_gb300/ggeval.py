@@ -31,13 +31,19 @@ SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggev
            "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc",
            "ggeval_eval_batch_masked", "ggeval_gom_donate", "ggeval_gom_changed",
            "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info",
-           "ggeval_tile_config")
+           "ggeval_tile_config", "ggeval_pipe_rates", "ggeval_evaluate")
 
 
 class GGEvalError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"ggeval status {status}: {msg}")
         self.status = status
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("smse", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("mse", ctypes.c_void_p), ("nmse", ctypes.c_void_p), ("size", ctypes.c_void_p),
+                ("size_evaluated", ctypes.c_void_p)]
 
 
 class Batch(ctypes.Structure):
@@ -78,6 +84,8 @@ def load_library(path: str = LIB_PATH):
         "ggeval_gom_accept": [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "ggeval_trial_sizes": [bp, i32, vp, vp],
         "ggeval_tile_config": [vp, bp, u32, vp, vp],
+        "ggeval_pipe_rates": [i32, i32, vp],
+        "ggeval_evaluate": [vp, bp, u32, ctypes.POINTER(Outputs), vp],
         "ggeval_dataset_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
@@ -187,6 +195,28 @@ class Dataset:
                                        _stream_handle(stream)))
         return outs
 
+    #: the outputs of evaluate(), in the order of ggeval_outputs
+    OUTPUTS = ("smse", "a", "b", "mse", "nmse", "size", "size_evaluated")
+
+    def evaluate(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None,
+                 want=OUTPUTS, out=None):
+        """Every objective of every trial in one launch sequence: a dict
+        name -> tensor [n] (float32; int32 for the sizes) on op's device,
+        for the names in ``want`` (``out`` may supply the tensors)."""
+        b = make_batch(op, cval, heights, layout=layout)
+        kw = dict(device=op.device)
+        if not op.is_cuda:
+            kw["pin_memory"] = True
+        res = dict(out or {})
+        for name in want:
+            if name not in res:
+                dt = torch.int32 if name.startswith("size") else torch.float32
+                res[name] = torch.empty(b.n, dtype=dt, **kw)
+        o = Outputs(*[_ptr(res.get(name)) for name in self.OUTPUTS])
+        _check(lib().ggeval_evaluate(self._h, ctypes.byref(b), flags, ctypes.byref(o),
+                                     _stream_handle(stream)))
+        return res
+
     def eval_plain(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None,
                    out=None):
         b = make_batch(op, cval, heights, layout=layout)
@@ -269,16 +299,23 @@ class Dataset:
                                          ctypes.byref(m), ctypes.byref(v)))
         return n.value, f.value, m.value, v.value
 
-    def nmse(self, mse):
-        """NMSE (Eq. 2) from MSE values: mse / Var(y)."""
-        return mse / self.info()[3]
-
     def profile_read(self):
         """(total forward-kernel ms, launches) since the last read."""
         ms = ctypes.c_double()
         n = ctypes.c_int64()
         _check(lib().ggeval_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+PIPE_KINDS = ("ffma", "ffma2", "rsqrt", "ex2", "lg2", "sin")
+
+
+def pipe_rates(device=0, iters=1 << 14):
+    """Operations per second of the issue-rate microbenchmarks, by kind
+    (see ggeval_pipe_rates)."""
+    out = (ctypes.c_double * len(PIPE_KINDS))()
+    _check(lib().ggeval_pipe_rates(int(device), int(iters), out))
+    return dict(zip(PIPE_KINDS, list(out)))
 
 
 def adam_step(op, cval, grad, m, v, t, lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8,
