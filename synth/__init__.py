@@ -5,8 +5,9 @@ and the GPU tests) and the FP64 oracle take their inputs from.  It draws
 random numbers and lays them out; it holds none of the method's arithmetic:
 it never evaluates a tree and never computes a fitness.  The target ``y`` of
 every workload comes from evaluating a seeded generator tree, and that
-evaluation is done by whoever consumes the workload (the oracle in tests,
-the library in the benchmark), then passed to :func:`make_target`.
+evaluation is done by the consumer of the workload (the oracle, in the
+tests and in the benchmark's oracle leg), then passed to
+:func:`make_target`.
 
 Template format (the library's input format, Section 3.1 of the paper: a
 fixed-shape template tree whose inactive nodes are introns):
@@ -170,8 +171,9 @@ def _x(rng, n, f, dist):
     raise ValueError(dist)
 
 
-#: The five workloads.  Sizes follow the benchmark configurations; the
-#: tree-shape recipe (half "full", half "grow" trials) is stated in the design doc.
+#: The five workloads.  Sizes follow the benchmark configurations; half the
+#: trials are "full" trees (every non-leaf position a function) and half
+#: "grow" trees (a function with probability 1/2), unless stated.
 CONFIGS = {
     "c1": dict(index=0, name="plain-256xh3-1000x5", P=256, h=3, funcs=BASIC_SET,
                N=1_000, F=5, x=("uniform", -1.0, 1.0), y_h=3, y_funcs=BASIC_SET,
@@ -202,6 +204,10 @@ for _i, _name in enumerate(("addition", "division", "subtraction", "multiplicati
                             "squaring")):
     CONFIGS["l_" + _name[:3]] = dict(
         index=5 + _i, name=f"ladder-{_name}-2000xh6-100000x9", P=2_000, h=6, funcs=EXP3_SET,
+        N=100_000, F=9, x=("uniform", 1.0, 5.0), target=_name, noise=0.0, fos=False)
+    # the same ladder with the depth-8 templates (511 nodes) of Table 2
+    CONFIGS["l8_" + _name[:3]] = dict(
+        index=11 + _i, name=f"ladder-{_name}-2000xh8-100000x9", P=2_000, h=8, funcs=EXP3_SET,
         N=100_000, F=9, x=("uniform", 1.0, 5.0), target=_name, noise=0.0, fos=False)
 
 

@@ -62,10 +62,13 @@ def test_nmse_and_dataset_info(gg):
     y = w["y"].astype(np.float64)
     assert (n, f) == (5000, 8)
     np.testing.assert_allclose([ym, yv], [y.mean(), y.var()], rtol=1e-6)
-    mse = ds.eval_batch(torch.from_numpy(w["op"]).cuda(), torch.from_numpy(w["cval"]).cuda())[3]
-    nmse = ds.nmse(mse).cpu().numpy()
+    res = ds.evaluate(torch.from_numpy(w["op"]).cuda(), torch.from_numpy(w["cval"]).cuda(),
+                      want=("smse", "mse", "nmse"))
+    mse, nmse = res["mse"].cpu().numpy(), res["nmse"].cpu().numpy()
     ds.sync()
     ds.close()
+    fin = np.isfinite(mse)
+    np.testing.assert_allclose(nmse[fin], mse[fin] / yv, rtol=2e-7)
     checked = 0
     for p in range(30):
         t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
@@ -78,8 +81,54 @@ def test_nmse_and_dataset_info(gg):
     assert checked >= 10
 
 
-@pytest.mark.parametrize("cfg", ["l_add", "l_squ", "l_sub"])
+@pytest.mark.parametrize("fold", [True, False])
+def test_error_and_size_objectives_in_one_call(gg, fold):
+    """evaluate() returns every objective of every trial from one launch
+    sequence: scaled MSE, MSE and NMSE as eval_batch computes them, and the
+    size objective (active nodes, the oracle's active set) with the nodes
+    evaluated per row after folding (the host packer's count); an invalid
+    trial gets size -1.  Device and pinned host batches agree."""
+    w = PA.build("c3", 3001, 120)
+    w["op"][7, 0] = 200  # an invalid root
+    ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
+    op, cv = torch.from_numpy(w["op"]).cuda(), torch.from_numpy(w["cval"]).cuda()
+    hs = torch.from_numpy(w["heights"]).cuda()
+    flags = 0 if fold else gg.F_NO_FOLD
+    res = {k: v.cpu().numpy() for k, v in ds.evaluate(op, cv, hs, flags=flags).items()}
+    ref = [t.cpu().numpy() for t in ds.eval_batch(op, cv, hs, flags=flags)]
+    with pytest.raises(gg.GGEvalError):
+        ds.sync()
+    host = ds.evaluate(torch.from_numpy(w["op"]).pin_memory(),
+                       torch.from_numpy(w["cval"]).pin_memory(),
+                       torch.from_numpy(w["heights"]).pin_memory(), flags=flags)
+    torch.cuda.synchronize()
+    with pytest.raises(gg.GGEvalError):
+        ds.sync()
+    ds.close()
+    for k, r in zip(("smse", "a", "b", "mse"), ref):
+        np.testing.assert_array_equal(res[k], r)
+    for k, v in host.items():
+        assert not v.is_cuda
+        np.testing.assert_array_equal(v.numpy(), res[k])
+    st = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
+                        torch.from_numpy(w["heights"]), n_features=w["F"]).numpy()
+    for p in range(w["P"]):
+        if p == 7:
+            assert res["size"][p] == -1 and res["size_evaluated"][p] == -1
+            assert np.isnan(res["smse"][p])
+            continue
+        assert res["size"][p] == int(O.active_mask(PA.template(w, p)).sum()), p
+        want_eval = st[p, 13] if fold else st[p, 0]
+        assert res["size_evaluated"][p] == want_eval, p
+    if fold:
+        assert (res["size_evaluated"] < res["size"]).any()
+
+
+@pytest.mark.parametrize("cfg", ["l_add", "l_squ", "l_sub", "l8_add", "l8_div", "l8_sub",
+                                 "l8_mul", "l8_squ"])
 def test_ladder_parity(gg, cfg):
+    """The Experiment III ladder (Table 1 targets) with the depth-6 and
+    depth-8 templates (127 and 511 nodes) of Table 2, on 4,000-row slices."""
     w = PA.build(cfg, 4000, 40)
     X, y = torch.from_numpy(w["X"]), torch.from_numpy(w["y"])
     ds = gg.Dataset(X, y)
@@ -95,6 +144,7 @@ def test_ladder_parity(gg, cfg):
         t, f64, f32, fit64, fit32, cond, bounds = PA.oracle_trial(w, p)
         PA.check_fit(float(smse[p]), float(mse[p]), fit64, fit32, var_y, mean_y2, tf,
                      tag=f"trial {p}", bounds=bounds)
+    PA.report(f"ladder {w['name']} (4,000 rows, 40 trials)", "trials", tf)
     assert tf.failed == 0, repr(tf)
     assert tf.checked >= 20, repr(tf)
 
