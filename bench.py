@@ -66,6 +66,13 @@ OPS_FP32 = {"term": 0, "addsubmul": 1, "aq": 2, "div": 1, "sincos": 2, "exp": 1,
 OPS_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, "log": 1,
            "sqrt": 1, "square": 0, "pow": 2}
 ACC_FP32 = 4
+# the adjoint's reverse sweep, per node by class: the local derivatives and
+# the adjoint times each of them (one per operand); the forward recompute
+# counts as OPS_FP32 / OPS_SFU on the unfolded program
+OPS_REV_FP32 = {"term": 0, "addsubmul": 2, "aq": 6, "div": 3, "sincos": 3, "exp": 2, "log": 1,
+                "sqrt": 2, "square": 2, "pow": 3}
+OPS_REV_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 1, "exp": 1, "log": 1,
+               "sqrt": 1, "square": 0, "pow": 4}
 TUNE_STEPS = 20  # Adam steps of the constant-tuning report (grad mode)
 PARITY_TRIALS = 64  # timed trials compared with the oracle per workload
 # DRAM bytes (read + write) of one batched-forward launch from an ncu
@@ -85,7 +92,7 @@ def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_30954_gb300", "csrc")
     files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
-                   if f.endswith((".cu", ".cuh", ".h")))
+                   if f.endswith((".cu", ".cuh", ".h", ".py")))
     files.append(os.path.join(ROOT, "include", "ggeval.h"))
     for f in files:
         with open(f, "rb") as fh:
@@ -490,6 +497,44 @@ def run_extra_mode(a, gg, torch):
         v = torch.zeros_like(cv)
         smse = torch.empty(P, device="cuda")
         dc = torch.empty_like(cv)
+        # the adjoint kernel alone: CUDA events around it (roofline)
+        st_ = gg.batch_stats(torch.from_numpy(w["op"]), torch.from_numpy(w["cval"]),
+                             torch.from_numpy(w["heights"]) if hs is not None else None,
+                             n_features=w["F"]).numpy()
+        ok = st_[:, 0] >= 0
+        alg_fp32 = sum((OPS_FP32[k] + OPS_REV_FP32[k]) * int(st_[ok, c].sum())
+                       for k, c in STAT_COLS.items()) * N
+        alg_sfu = sum((OPS_SFU[k] + OPS_REV_SFU[k]) * int(st_[ok, c].sum())
+                      for k, c in STAT_COLS.items()) * N
+        with torch.cuda.stream(st):
+            for _ in range(2):
+                ds.grad_batch(op, cv.clone(), hs, flags=PF | gg.F_PROFILE, stream=st,
+                              smse=smse, dcval=dc)
+        st.synchronize()
+        ds.profile_read()
+        clocks = Clocks(dev)
+        clocks.start()
+        time.sleep(0.3)
+        with torch.cuda.stream(st):
+            for _ in range(a.steps):
+                ds.grad_batch(op, cv.clone(), hs, flags=PF | gg.F_PROFILE, stream=st,
+                              smse=smse, dcval=dc)
+        st.synchronize()
+        ck = clocks.stop()
+        adj_ms, launches = ds.profile_read()
+        adj_avg = adj_ms / max(launches, 1)
+        sm_mhz = (ck or {}).get("sm_mhz") or 1477.0
+        peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9
+        peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
+        line["roofline"] = {
+            "bound": "alu", "kernel": "adjoint_kernel (forward recompute + reverse sweep)",
+            "kernel_ms": adj_avg, "unit": "Gop/s",
+            "achieved": alg_fp32 / (adj_avg * 1e-3) / 1e9, "peak": peak_fp32,
+            "frac": alg_fp32 / (adj_avg * 1e-3) / 1e9 / peak_fp32,
+            "sfu": {"achieved": alg_sfu / (adj_avg * 1e-3) / 1e9, "peak": peak_sfu,
+                    "frac": alg_sfu / (adj_avg * 1e-3) / 1e9 / peak_sfu},
+            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz",
+            "traffic": None, "clocks": ck}
 
         def step(t):
             ds.grad_batch(op, cv, hs, flags=PF, stream=st, smse=smse, dcval=dc)

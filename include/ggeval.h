@@ -124,20 +124,31 @@ enum {
   GGEVAL_F_GRAD_MSE = 1u << 2,/* ggeval_grad_batch: gradient of plain MSE
                                  instead of scaled MSE                     */
   GGEVAL_F_PROFILE = 1u << 3, /* record CUDA events around the batched
-                                 forward kernel (not with GGEVAL_F_GRAPH);
-                                 read them with ggeval_profile_read        */
+                                 forward kernel (not with GGEVAL_F_GRAPH),
+                                 or around the adjoint kernel in
+                                 ggeval_grad_batch; read them with
+                                 ggeval_profile_read                       */
   GGEVAL_F_POW = 1u << 4,     /* the batch may hold active POW nodes: run
                                  the kernel builds that include pow.
                                  Without it an active POW node is an
                                  invalid template (GGEVAL_ERR_TEMPLATE); the
                                  other kernels leave the pow code out
                                  because it costs them registers and speed */
-  GGEVAL_F_NO_FOLD = 1u << 5  /* evaluate constant subtrees on every row.
+  GGEVAL_F_NO_FOLD = 1u << 5, /* evaluate constant subtrees on every row.
                                  By default the packer folds each active
                                  subtree without a feature into one constant,
                                  computed once per trial with the same FP32
                                  functions, so the outputs are bit-identical
                                  either way; the gradient never folds      */
+  GGEVAL_F_TEST_STALL = 1u << 6 /* test hook for failure detection
+                                 (ggeval_eval_batch / ggeval_evaluate): the
+                                 batched forward kernel issues no tile copy,
+                                 so every bounded wait for a tile gives up
+                                 after a short limit (milliseconds); nothing
+                                 is left in flight, ggeval_sync() then
+                                 reports GGEVAL_ERR_TIMEOUT and the call's
+                                 outputs are unspecified.  The device stays
+                                 usable for the next call.               */
 };
 
 /* Create a dataset from X (n_rows x n_features, float32, row-major when
@@ -394,10 +405,12 @@ ggeval_status ggeval_dataset_info(const ggeval_dataset* ds, int64_t* n_rows,
  *    GGEVAL_NOALLOC_MAX_TILES row tiles that fit in shared memory; larger
  *    requests return GGEVAL_ERR_UNSUPPORTED with a message and launch
  *    nothing.  Host-memory batches return GGEVAL_ERR_ARG.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.  Later calls only launch kernels and one
- *    memset, so they may be captured.
+ *  - A call made outside a stream capture looks up the array's device
+ *    address (cudaGetSymbolAddress) with the dataset's device current, so
+ *    after a device reset the new context's address is used; a call made
+ *    during a capture uses the address from that device's last call outside
+ *    one.  So make the first call on each device (and the first after a
+ *    reset) before any stream capture.
  *  - Every call on a device shares the one array and it keeps the previous
  *    call's contents (the call zeroes what must start at zero).  Calls whose
  *    GPU work overlaps (different streams, or different datasets on the

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see the package docstring).  Every function cites
 the passage of the paper it follows; readings of points the paper leaves
-open are marked READING and listed in the design doc.
+open are marked READING.
 """
 from __future__ import annotations
 

@@ -311,18 +311,36 @@ def _rows_task(items):
 
 
 def _grad_task(items):
+    """Worker: the gradient of each (trial, mode, GPU gradient row, GPU smse)
+    against the oracle's reverse mode.  A trial whose fitness is excluded as
+    ill-conditioned, whose FP32 evaluation overflows at an intermediate node,
+    or whose FP64 gradient is not finite is excluded; one with infinite
+    fitness (or b* = 0 for smse) must have a zero gradient."""
     w = _W
-    t = Tally()
-    n_floor = 0
-    for p, mode, g in items:
-        tt = template(w, p)
+    y = w["y"].astype(np.float64)
+    var_y, mean_y2 = float(np.var(y)), float(np.mean(y * y))
+    t, tf, n_floor = Tally(), Tally(), 0
+    for p, mode, g, g_smse in items:
+        tt, f64, f32, fit64, fit32, cond, bounds = oracle_trial(w, p)
+        before = tf.excluded
+        check_fit(g_smse, None, fit64, fit32, var_y, mean_y2, tf, tag=f"trial {p}",
+                  bounds=bounds)
+        if tf.excluded != before or not intermediates_finite_f32(tt, w["X"]):
+            t.excluded += 1
+            continue
         r, fit, rabs = O.grad(tt, w["X"], w["y"], mode, with_abs=True)
-        if not (fit["finite"] and np.all(np.isfinite(r))):
+        if not fit64["finite"] or (mode == "smse" and fit64["b"] == 0.0):
+            t.checked += 1
+            if not np.all(g == 0.0):
+                t.failed += 1
+                t.msgs.append(f"trial {p}: gradient should be 0")
+            continue
+        if not np.all(np.isfinite(r)):  # a derivative is infinite at some row
             t.excluded += 1
             continue
         n_floor += floor_only_entries(g, r, rabs)
         check_grad(g, r, t, tag=f"trial {p}", rabs=rabs)
-    return t, n_floor
+    return t, tf, n_floor
 
 
 def _pool_map(w, fn, items, processes, chunk):
@@ -372,13 +390,16 @@ def check_rows_many(w, trials, rows, processes=None, chunk=1):
     return out
 
 
-def check_gradients(w, trials, dcval, mode="smse", processes=None, chunk=1):
+def check_gradients(w, trials, dcval, smse, mode="smse", processes=None, chunk=1):
     """Check GPU gradients (rows of dcval) of the listed trials against the
-    oracle's reverse mode; returns (Tally, entries that pass only through
-    the FP32 floor term of the tolerance)."""
-    items = [(int(p), mode, np.asarray(dcval[p], dtype=np.float64)) for p in trials]
-    out, floor = Tally(), 0
-    for t, nf in _pool_map(w, _grad_task, items, processes, chunk):
+    oracle's reverse mode on the process pool; returns (gradient Tally,
+    fitness Tally, gradient entries that pass only through the FP32 floor
+    term GRAD_FLOOR * G_k of the tolerance)."""
+    items = [(int(p), mode, np.asarray(dcval[p], dtype=np.float64), float(smse[p]))
+             for p in trials]
+    out, fout, floor = Tally(), Tally(), 0
+    for t, tf, nf in _pool_map(w, _grad_task, items, processes, chunk):
         out.merge(t)
+        fout.merge(tf)
         floor += nf
-    return out, floor
+    return out, fout, floor

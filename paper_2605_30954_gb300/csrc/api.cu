@@ -14,11 +14,23 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ggeval.h"
 #include "gom.cuh"
 #include "misc.cuh"
 
 namespace {
+
+// An NVTX range over a scope (a profiler's timeline shows where the host
+// side of each call spends its time; without a tool attached it costs a
+// load and a branch).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 thread_local std::string g_err = "no error";
 
@@ -97,6 +109,7 @@ struct Plan {
   Cfg cfg;
   bool pow = false;  // kernels with the pow instructions; the packer accepts pow
   bool fold = true;  // the packer folds constant subtrees (not GGEVAL_F_NO_FOLD)
+  bool stall = false;  // GGEVAL_F_TEST_STALL
   int slots = 0, stride = 0, lstride = 0, n_tiles = 0, n_items = 0, grid = 0;
   size_t smem = 0;
   const void* fn = nullptr;
@@ -209,6 +222,19 @@ ggeval_status check_batch(const ggeval_dataset* ds, const ggeval_batch* b) {
   return GGEVAL_OK;
 }
 
+// Trials per work item for row tiles of `tile` rows: about 32 work items per
+// SM, and at least `warps` trials per item.
+int group_for(const ggeval_dataset* ds, int n, int warps, int tile) {
+  const double target = 16.0 * ds->sms * 2;
+  const int n_tiles = (int)((ds->N + tile - 1) / tile);
+  long long n_groups = (long long)std::ceil(target / n_tiles);
+  const long long max_groups = (n + warps - 1) / warps;
+  if (n_groups > max_groups) n_groups = max_groups;
+  if (n_groups < 1) n_groups = 1;
+  const int g = (int)((n + n_groups - 1) / n_groups);
+  return g < 1 ? 1 : g;
+}
+
 // Default tile shape: enough work items for every SM several times over, X
 // tiles as large as the work allows (each tile is reused by `group` trials).
 Cfg default_cfg(const ggeval_dataset* ds, int n, int h_max, uint32_t flags) {
@@ -228,13 +254,7 @@ Cfg default_cfg(const ggeval_dataset* ds, int n, int h_max, uint32_t flags) {
   int tile = rpp;
   while (tile < max_tile && tile < want && tile < ds->N) tile *= 2;
   c.tile_rows = tile;
-  const int n_tiles = (int)((ds->N + tile - 1) / tile);
-  long long n_groups = (long long)std::ceil(target / n_tiles);
-  const long long max_groups = (n + c.warps - 1) / c.warps;
-  if (n_groups > max_groups) n_groups = max_groups;
-  if (n_groups < 1) n_groups = 1;
-  c.group = (int)((n + n_groups - 1) / n_groups);
-  if (c.group < 1) c.group = 1;
+  c.group = group_for(ds, n, c.warps, tile);
   return c;
 }
 
@@ -352,6 +372,7 @@ ggeval_status enqueue_pack(ggeval_dataset* ds, const DevBatch& db, int n, int h_
                            const Plan& pl, bool with_aux, cudaStream_t st,
                            const int* count = nullptr, const int* idx = nullptr,
                            int32_t* size = nullptr, int32_t* size_eval = nullptr) {
+  Range r("ggeval pack");
   gg::PackParams pp{};
   pp.op = db.op;
   pp.cval = db.cval;
@@ -397,6 +418,9 @@ gg::FwdParams fwd_params(ggeval_dataset* ds, int n, const Plan& pl) {
   fp.counter = ds->counters;
   fp.status = ds->status;
   fp.rows_out = nullptr;
+  fp.wait_limit = gg::WAIT_LIMIT;
+  fp.stall = pl.stall ? 1 : 0;
+  if (pl.stall) fp.wait_limit = 1u << 12;  // the test hook gives up soon
   return fp;
 }
 
@@ -430,6 +454,7 @@ constexpr size_t PROF_MAX = 4096;
 ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_batch* b,
                            const Plan& pl, const Outs& o, bool with_aux, cudaStream_t st,
                            bool profile = false, const uint8_t* mask = nullptr) {
+  Range r("ggeval enqueue evaluation");
   const int n = b->n;
   // counters[0]: the work counter; counters[2]: the compacted count;
   // counters[8 + slot]: the slot's trial found non-finite
@@ -649,6 +674,7 @@ ggeval_status ggeval_eval_batch_masked(ggeval_dataset* ds, const ggeval_batch* b
 
 static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
                                      const Outs& o, void* stream, const uint8_t* mask) {
+  Range range("ggeval_eval_batch");
   GG_TRY(check_batch(ds, b));
   if (b->n == 0) return GGEVAL_OK;
   if (!o.f[0]) return fail(GGEVAL_ERR_ARG, "smse is NULL");
@@ -657,6 +683,7 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
   Plan pl;
   GG_TRY(make_plan(ds, b->n, b->max_height, pick_cfg(ds, b, flags), &pl, has_pow(flags)));
   pl.fold = (flags & GGEVAL_F_NO_FOLD) == 0;
+  pl.stall = (flags & GGEVAL_F_TEST_STALL) != 0;
   GG_TRY(ensure_ws(ds, b->n, pl, false));
   const bool host = b->memory == GGEVAL_MEM_HOST;
   DevBatch db;
@@ -687,6 +714,7 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
     key.cfg = pl.cfg;
     key.kind = 1;
     if (!ds->gexec || !same_key(key, ds->gkey)) {
+      Range rc("ggeval graph capture");
       drop_graph(ds);
       cudaGraph_t g = nullptr;
       GG_CU(cudaStreamBeginCapture(ds->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -705,7 +733,10 @@ static ggeval_status eval_batch_impl(ggeval_dataset* ds, const ggeval_batch* b, 
       }
       ds->gkey = key;
     }
-    GG_CU(cudaGraphLaunch(ds->gexec, st));
+    {
+      Range rl("ggeval graph launch");
+      GG_CU(cudaGraphLaunch(ds->gexec, st));
+    }
     return GGEVAL_OK;
   }
   GG_TRY(enqueue_eval(ds, db, b, pl, dev, false, st, (flags & GGEVAL_F_PROFILE) != 0, mask));
@@ -791,6 +822,7 @@ ggeval_status ggeval_eval_plain(ggeval_dataset* ds, const ggeval_batch* b, uint3
 
 ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
                                 float* smse, float* dcval, void* stream) {
+  Range range("ggeval_grad_batch");
   GG_TRY(check_batch(ds, b));
   if (b->n == 0) return GGEVAL_OK;
   if (!dcval) return fail(GGEVAL_ERR_ARG, "dcval is NULL");
@@ -882,7 +914,21 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   long long agrid = (long long)nb * ds->sms;
   const long long need_blocks = (ap.n_items + warps - 1) / warps;
   if (agrid > need_blocks) agrid = need_blocks;
+  // GGEVAL_F_PROFILE: CUDA events around the adjoint kernel (read with
+  // ggeval_profile_read, as the forward kernel's)
+  std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+  if ((flags & GGEVAL_F_PROFILE) && !host && ds->prof_used < PROF_MAX) {
+    if (ds->prof_used == ds->prof_ev.size()) {
+      cudaEvent_t e0, e1;
+      GG_CU(cudaEventCreate(&e0));
+      GG_CU(cudaEventCreate(&e1));
+      ds->prof_ev.push_back({e0, e1});
+    }
+    ev = &ds->prof_ev[ds->prof_used++];
+    GG_CU(cudaEventRecord(ev->first, st));
+  }
   GG_TRY(launch(afn, dim3((unsigned)agrid), dim3(warps * 32), asmem, st, &ap));
+  if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::GradOutParams gp{ds->gacc, ds->len, b->n, pl.stride, dg};
   GG_TRY(launch(gg::gradout_ptr(), dim3((unsigned)((gcount + 255) / 256)), dim3(256), 0, st, &gp));
   if (host) {
@@ -919,6 +965,7 @@ ggeval_status ggeval_adam_step(const ggeval_batch* b, float* cval, const float* 
 
 ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_t flags,
                               void* stream) {
+  Range range("ggeval_autotune");
   GG_TRY(check_batch(ds, b));
   if (b->n == 0) return GGEVAL_OK;
   if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "autotune needs a device batch");
@@ -1270,13 +1317,22 @@ static_assert(NA_LEN_OFF % 256 == 0 && NA_PART_OFF % 256 == 0 && NA_CNT_OFF % 25
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 namespace {
-// device address of g_noalloc_scratch, looked up once per device
-ggeval_status noalloc_scratch(int device, unsigned char** out) {
+// Device address of g_noalloc_scratch on `device` (current).  Outside a
+// stream capture every call looks it up again, so the address of a context
+// created after a device reset is the one used; during a capture the
+// address from the device's last call outside a capture is used.
+ggeval_status noalloc_scratch(int device, cudaStream_t st, unsigned char** out) {
   static std::mutex mu;
   static std::map<int, unsigned char*> addr;
   std::lock_guard<std::mutex> lock(mu);
-  auto it = addr.find(device);
-  if (it != addr.end()) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+  if (cs != cudaStreamCaptureStatusNone) {
+    auto it = addr.find(device);
+    if (it == addr.end())
+      return fail(GGEVAL_ERR_ARG,
+                  "eval_batch_noalloc: the first call on device %d must come before any "
+                  "stream capture", device);
     *out = it->second;
     return GGEVAL_OK;
   }
@@ -1308,9 +1364,12 @@ extern "C" ggeval_status ggeval_eval_batch_noalloc(ggeval_dataset* ds, const gge
   DeviceGuard guard(ds->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char* base = nullptr;
-  GG_TRY(noalloc_scratch(ds->device, &base));
+  GG_TRY(noalloc_scratch(ds->device, st, &base));
   Cfg c = default_cfg(ds, b->n, b->max_height, 0);
-  while ((ds->N + c.tile_rows - 1) / c.tile_rows > GGEVAL_NOALLOC_MAX_TILES) c.tile_rows *= 2;
+  if ((ds->N + c.tile_rows - 1) / c.tile_rows > GGEVAL_NOALLOC_MAX_TILES) {
+    while ((ds->N + c.tile_rows - 1) / c.tile_rows > GGEVAL_NOALLOC_MAX_TILES) c.tile_rows *= 2;
+    c.group = group_for(ds, b->n, c.warps, c.tile_rows);  // for the wider tiles
+  }
   Plan pl;
   if (make_plan(ds, b->n, b->max_height, c, &pl, false) != GGEVAL_OK)
     return fail(GGEVAL_ERR_UNSUPPORTED,

@@ -67,6 +67,8 @@ struct FwdParams {
                        // is non-finite or exceeds 2^50 (its fitness is +inf)
   const int* count;    // null, or the number of trials (slots) to evaluate, set
                        // on the device (masked evaluation; at most P)
+  uint32_t wait_limit; // polls before a tile wait gives up (ST_TIMEOUT)
+  int stall;           // test hook: issue no tile copy, so every wait gives up
 };
 
 // partial record of one (trial, tile): the shift c, (hi, lo) of S_d, S_dd and
@@ -172,15 +174,18 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int n_items, in
     __syncwarp();
     if (lane == 0) {
       ctl[0] = item;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(bar, (uint32_t)((p.F + 1) * ncopy * 4));
-      for (int f = 0; f <= p.F; ++f)
-        bulk_g2s(xs + (size_t)f * p.tile_rows, p.X + (size_t)f * p.ldx + row0,
-                 (uint32_t)(ncopy * 4), bar);
+      if (!p.stall) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)((p.F + 1) * ncopy * 4));
+        for (int f = 0; f <= p.F; ++f)
+          bulk_g2s(xs + (size_t)f * p.tile_rows, p.X + (size_t)f * p.ldx + row0,
+                   (uint32_t)(ncopy * 4), bar);
+      }
     }
   } else if (lane == 0) {
     ctl[0] = item;
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    if (!p.stall)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
   }
 }
 
@@ -250,7 +255,14 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
   constexpr int RPP = 32 * R;  // rows per pass of a warp
   uint32_t parity = 0;         // bit s: phase parity of bar[s] this warp waits for next
   for (int s = 0;; s ^= 1) {
-    if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u, p.status, WAIT_LIMIT)) return;
+    if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u, p.status, p.wait_limit)) {
+      // the wait gave up (ST_TIMEOUT is set): before this warp leaves, give
+      // a copy still in flight into either buffer time to land (bounded
+      // too), so that no bulk copy outlives the CTA's shared memory
+      mbar_wait_bounded(&bar[s ^ 1], (parity >> (s ^ 1)) & 1u, p.status, p.wait_limit);
+      mbar_wait_bounded(&bar[s], (parity >> s) & 1u, p.status, p.wait_limit);
+      return;
+    }
     parity ^= 1u << s;
     int* c = ctl + 4 * s;
     const int item = *reinterpret_cast<volatile int*>(&c[0]);

@@ -19,7 +19,7 @@ OK, ERR_ARG, ERR_TEMPLATE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_CHECKED, ERR_UNSU
     0, -1, -2, -3, -4, -5, -6, -7
 LAYOUT_HEAP, LAYOUT_PREFIX = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
-F_GRAPH, F_EXACT, F_GRAD_MSE, F_PROFILE, F_POW, F_NO_FOLD = 1, 2, 4, 8, 16, 32
+F_GRAPH, F_EXACT, F_GRAD_MSE, F_PROFILE, F_POW, F_NO_FOLD, F_TEST_STALL = 1, 2, 4, 8, 16, 32, 64
 NSTAT = 25
 MAX_HEIGHT = 8
 

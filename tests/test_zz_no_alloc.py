@@ -67,3 +67,15 @@ def test_noalloc_refuses_beyond_limits(gg):
     tall = torch.zeros((2, 255), dtype=torch.uint8, device="cuda")  # height 7
     assert call_noalloc(gg, ds, tall, torch.zeros((2, 255), device="cuda"), outs[:4]) == -7
     ds.close()
+    # rows that do not fit in 64 row tiles of shared-memory size: refused,
+    # nothing launched (the outputs keep their values)
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(rng.uniform(-1, 1, (1_000_000, 10)).astype(np.float32))
+    ds = gg.Dataset(X, torch.from_numpy(rng.standard_normal(1_000_000).astype(np.float32)))
+    op = torch.full((4, 15), 32, dtype=torch.uint8, device="cuda")  # x0
+    outs = [torch.full((4,), float("nan"), device="cuda") for _ in range(4)]
+    assert call_noalloc(gg, ds, op, torch.zeros((4, 15), device="cuda"), outs) == -7
+    assert b"tiles" in gg.lib().ggeval_last_error()
+    ds.sync()
+    assert all(torch.isnan(t).all() for t in outs)
+    ds.close()
