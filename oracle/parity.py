@@ -138,8 +138,10 @@ def check_rows(g, f64, f32, tally, tag="", cond=None):
                           f"gpu {g[i]!r} oracle {f64[i]!r}")
     if bad.any():
         tally.failed += int(bad.sum())
-        i = int(np.argmax(np.where(bad, err / np.maximum(tol, 1e-300), 0)))
-        tally.msgs.append(f"{tag} row {i}: gpu {g[i]!r} oracle {f64[i]!r}")
+        where = np.flatnonzero(bad)
+        i = int(where[np.argmax(err[where] / np.maximum(tol[where], 1e-300))])
+        tally.msgs.append(f"{tag} row {i}: gpu {g[i]!r} oracle {f64[i]!r} "
+                          f"({int(bad.sum())} rows)")
     ok = ~ill
     if ok.any():
         tally.worst = max(tally.worst, float(np.max(err[ok] / np.maximum(tol[ok], 1e-300))))

