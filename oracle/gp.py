@@ -392,7 +392,8 @@ def _dapply(o, a, b, out):
     raise InvalidTemplate(o)
 
 
-def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs: bool = False):
+def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs: bool = False,
+         perturb=None):
     """Reverse-mode FP64 gradient of smse (or mse) with respect to the
     constant of every active ERC node; 0 at every other template position.
 
@@ -405,11 +406,14 @@ def grad(t: Template, X: np.ndarray, y: np.ndarray, mode: str = "smse", with_abs
     also, per entry, sum_i s_i |d f_i / d c| with s_i = (2/N)|b*|(|a*| +
     |b* f_i| + |y_i|) (smse) or (2/N)(|f_i| + |y_i|) (mse): the size of the
     terms whose rounding in FP32 an FP32 gradient cannot avoid (the residual
-    a + b f - y is a difference of such terms)."""
+    a + b f - y is a difference of such terms).  ``perturb`` = (rel, rng)
+    multiplies every function node's value by (1 +- rel) as
+    eval_tree_perturbed does (a probe of the gradient's FP32 conditioning;
+    a* and b* then belong to the perturbed values)."""
     X = np.asarray(X)
     y = np.asarray(y, dtype=np.float64)
     vals = {}
-    f = _eval(t, X, np.float64, store=vals)
+    f = _eval(t, X, np.float64, store=vals, perturb=perturb)
     fit = fitness(f, y)
     g = np.zeros(t.op.size, dtype=np.float64)
     gabs = np.zeros(t.op.size, dtype=np.float64)

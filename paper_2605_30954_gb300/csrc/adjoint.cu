@@ -134,10 +134,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
     if (L <= 0) continue;
     const double* ab = p.ab + 4 * (size_t)trial;
     if (ab[2] == 0.0 || (!p.mse_mode && ab[1] == 0.0)) continue;
-    const float a_c = (float)ab[0];
-    const float bb = (float)ab[1];
+    // a* - mean(y), b* and mean(y) as FP32 (hi, lo) pairs of their FP64 values
+    const float a_hi = (float)ab[0], a_lo = (float)(ab[0] - (double)a_hi);
+    const float b_hi = (float)ab[1], b_lo = (float)(ab[1] - (double)b_hi);
+    const float yb_hi = (float)p.ybar, yb_lo = (float)(p.ybar - (double)yb_hi);
     const float two_n = (float)(2.0 / (double)p.N);
-    const float ybar = (float)p.ybar;
     const uint2* src = p.prog + (size_t)trial * p.lstride;
     const Aux* asrc = p.aux + (size_t)trial * p.lstride;
     for (int k = lane; k <= L; k += 32) {
@@ -159,12 +160,27 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = 0.f;
       run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
-      float yc[R];
+      float yc[R], yl[R];
       load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
+      load_rows<R>(p.ylo + row0, yl);
       float w[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        w[r] = p.mse_mode ? two_n * (A[r] - ybar - yc[r]) : two_n * bb * (a_c + bb * A[r] - yc[r]);
+        // the residual a* + b* f - y (smse) or f - y (mse) in double-float:
+        // TwoProd / TwoSum keep the rounding of every term, so only f's own
+        // FP32 error remains (y = mean(y) + yc + yl exactly to FP64 accuracy)
+        float s, e1, e2, t, lo;
+        if (p.mse_mode) {
+          two_sum(A[r], -yb_hi, s, e1);
+          lo = -yb_lo;
+        } else {
+          const float pr = __fmul_rn(b_hi, A[r]);  // never contracted into an FMA
+          lo = fmaf(b_hi, A[r], -pr) + fmaf(b_lo, A[r], a_lo);
+          two_sum(a_hi, pr, s, e1);
+        }
+        two_sum(s, -yc[r], t, e2);
+        const float res = t + ((e1 + e2) + (lo - yl[r]));
+        w[r] = two_n * (p.mse_mode ? res : b_hi * res);
         w[r] = valid[r] ? w[r] : 0.f;
       }
       store_rows<R>(V + (size_t)SLOT * (L - 1), w);  // the output's value becomes its adjoint

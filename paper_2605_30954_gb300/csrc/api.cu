@@ -155,6 +155,7 @@ struct ggeval_dataset {
   int F = 0, ldx = 0;
   size_t smem_optin = 0;
   float* X = nullptr;        // [F + 1][ldx], row F = y - mean(y)
+  float* ylo = nullptr;      // [ldx]: the FP32 rounding error of row F (adjoint residuals)
   float2* pref = nullptr;    // [N + 1] prefix sums of the stored centred target (hi, lo)
   double ybar = 0, syc = 0, sycyc = 0;
   cudaStream_t cap_stream = nullptr;
@@ -553,8 +554,11 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
   std::vector<double> pref((size_t)N + 1);
   pref[0] = 0;
   double s2 = 0;
+  std::vector<float> ylo((size_t)N);
   for (int64_t i = 0; i < N; ++i) {
-    yh[i] = (float)((double)yh[i] - ds->ybar);
+    const double yc = (double)yh[i] - ds->ybar;
+    yh[i] = (float)yc;
+    ylo[i] = (float)(yc - (double)yh[i]);
     pref[i + 1] = pref[i] + (double)yh[i];
     s2 += (double)yh[i] * (double)yh[i];
   }
@@ -581,6 +585,7 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
   ds->smem_optin = (size_t)optin;
   const size_t xbytes = (size_t)(F + 1) * ds->ldx * 4;
   if ((e = cudaMalloc(&ds->X, xbytes)) || (e = cudaMalloc(&ds->pref, ((size_t)N + 1) * 8)) ||
+      (e = cudaMalloc(&ds->ylo, (size_t)ds->ldx * 4)) ||
       (e = cudaMalloc(&ds->status, sizeof(unsigned)))) {
     fail(GGEVAL_ERR_OOM, "dataset allocation: %s", cudaGetErrorString(e));
     return cleanup(GGEVAL_ERR_OOM);
@@ -608,6 +613,9 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
     if ((e = cudaMemcpyAsync(ds->pref, pref2.data(), ((size_t)N + 1) * 8, cudaMemcpyHostToDevice,
                              st)))
       break;
+    if ((e = cudaMemsetAsync(ds->ylo, 0, (size_t)ds->ldx * 4, st))) break;
+    if ((e = cudaMemcpyAsync(ds->ylo, ylo.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st)))
+      break;
     e = cudaStreamSynchronize(st);
   } while (0);
   if (tmp) cudaFree(tmp);
@@ -627,6 +635,7 @@ void ggeval_destroy(ggeval_dataset* ds) {
   drop_graph(ds);
   cudaFree(ds->X);
   cudaFree(ds->pref);
+  cudaFree(ds->ylo);
   cudaFree(ds->status);
   cudaFree(ds->prog);
   cudaFree(ds->aux);
@@ -890,6 +899,7 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   n_chunks = (ds->N + chunk_rows - 1) / chunk_rows;
   gg::AdjParams ap{};
   ap.X = ds->X;
+  ap.ylo = ds->ylo;
   ap.N = (int)ds->N;
   ap.F = ds->F;
   ap.ldx = ds->ldx;

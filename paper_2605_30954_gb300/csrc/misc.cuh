@@ -11,6 +11,7 @@ namespace gg {
 
 struct AdjParams {
   const float* X;      // [F + 1][ldx], row F = centred target
+  const float* ylo;    // [ldx]: (y - mean(y)) - the stored centred target (FP32)
   int N, F, ldx;
   const uint2* prog;   // [P][lstride]
   const Aux* aux;      // [P][lstride]

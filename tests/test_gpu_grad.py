@@ -39,9 +39,9 @@ def grad_case(gg, w, mode="smse", sample=None, name=None):
     smse, dc = smse.cpu().numpy(), dc.cpu().numpy()
     ds.close()
     idx = list(range(w["P"])) if sample is None else list(sample)
-    tally, fit_tally, n_floor = PA.check_gradients(w, idx, dc, smse, mode)
+    tally, fit_tally, n_floor, n_ill = PA.check_gradients(w, idx, dc, smse, mode)
     if name:
-        PA.report(f"{name} (floor-only entries: {n_floor})", "grads", tally)
+        PA.report(f"{name} (floor-only {n_floor}, ill-cond. {n_ill})", "grads", tally)
     return tally, fit_tally
 
 

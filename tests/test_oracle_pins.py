@@ -335,6 +335,20 @@ def test_gradient_scale_and_shift_invariance():
         assert abs(g[1]) <= 1e-12 * abs(fit["b"]) + 1e-15
 
 
+def test_gradient_perturbation_probe():
+    """grad's perturb: a zero perturbation is the plain gradient; a
+    perturbation of relative size rel moves a well-conditioned gradient by
+    O(rel)."""
+    rng, X = rand_xy(14)
+    y = np.cos(X[:, 0]) + X[:, 1]
+    t = T(["+", "*", "sin", "x0", "1.7", "x1", None], 2)
+    g0, _ = O.grad(t, X, y)
+    g1, _ = O.grad(t, X, y, perturb=(0.0, rng))
+    np.testing.assert_array_equal(g0, g1)
+    g2, _ = O.grad(t, X, y, perturb=(1e-7, rng))
+    assert 0 < np.max(np.abs(g2 - g0)) <= 1e-4 * np.max(np.abs(g0))
+
+
 def test_envelope_partials_vanish():
     rng, X = rand_xy(9)
     t = T(["aq", "x0", "sin", None, None, "x1"], 2)
