@@ -258,6 +258,19 @@ ggeval_status ggeval_adam_step(const ggeval_batch* batch, float* cval, const flo
 ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* batch,
                               uint32_t flags, void* stream);
 
+/* The autotuner's choices as a file: one JSON object per line, keyed by
+ * the GPU's name and SM count, the dataset's rows and features, and the
+ * batch shape (trials, max_height, layout, flags & (EXACT | POW)), with the
+ * chosen {variant, tile_rows, group, warps}.  ggeval_tuning_save writes
+ * every choice this dataset holds (replacing the file); ggeval_tuning_load
+ * takes the entries that match this dataset's GPU and shape (n_loaded may
+ * be NULL; a missing file holds none).  With the environment variable
+ * GGEVAL_TUNE_CACHE naming such a file, ggeval_autotune uses a matching
+ * entry instead of timing candidates, and appends the choices it makes.
+ * Host-side only.  Errors: ERR_ARG (NULL, a file that cannot be opened). */
+ggeval_status ggeval_tuning_save(ggeval_dataset* ds, const char* path);
+ggeval_status ggeval_tuning_load(ggeval_dataset* ds, const char* path, int32_t* n_loaded);
+
 /* The launch configuration of ggeval_eval_batch for batches of this shape
  * (n, max_height, layout, flags & (EXACT | POW)): int32 [4] = {variant,
  * rows per tile, trials per work item, warps per CTA}.  variant: 0 = 8

@@ -151,6 +151,7 @@ bool same_key(const GraphKey& x, const GraphKey& y) {
 
 struct ggeval_dataset {
   int device = 0, sms = 0;
+  char gpu_name[256] = {0};
   int64_t N = 0;
   int F = 0, ldx = 0;
   size_t smem_optin = 0;
@@ -504,6 +505,85 @@ ggeval_status enqueue_eval(ggeval_dataset* ds, const DevBatch& db, const ggeval_
   return GGEVAL_OK;
 }
 
+// ------------------------------------------------------ tuning cache file
+// One JSON object per line:
+//   {"gpu": "NVIDIA GB300", "sms": 152, "rows": 100000, "features": 8,
+//    "trials": 4096, "max_height": 4, "layout": 0, "flags": 0,
+//    "variant": 0, "tile_rows": 2048, "group": 82, "warps": 24}
+// A dataset takes the entries whose GPU name, SM count, rows and features
+// match its own.
+using TuneKey = std::tuple<int, int, int, int>;
+
+bool json_int(const char* line, const char* key, long long* out) {
+  char pat[64];
+  std::snprintf(pat, sizeof pat, "\"%s\":", key);
+  const char* p = std::strstr(line, pat);
+  if (!p) return false;
+  p += std::strlen(pat);
+  char* end = nullptr;
+  const long long v = std::strtoll(p, &end, 10);
+  if (end == p) return false;
+  *out = v;
+  return true;
+}
+
+bool json_str(const char* line, const char* key, std::string* out) {
+  char pat[64];
+  std::snprintf(pat, sizeof pat, "\"%s\":", key);
+  const char* p = std::strstr(line, pat);
+  if (!p) return false;
+  p = std::strchr(p + std::strlen(pat), '"');
+  if (!p) return false;
+  const char* q = std::strchr(p + 1, '"');
+  if (!q) return false;
+  out->assign(p + 1, q);
+  return true;
+}
+
+// entries of `path` for this dataset (a missing file holds none)
+ggeval_status load_tuning(ggeval_dataset* ds, const char* path, int* taken) {
+  *taken = 0;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return GGEVAL_OK;
+  char line[1024];
+  while (std::fgets(line, sizeof line, f)) {
+    std::string gpu;
+    long long sms, rows, feat, n, h, lay, fl, v, tile, group, warps;
+    if (!json_str(line, "gpu", &gpu) || !json_int(line, "sms", &sms) ||
+        !json_int(line, "rows", &rows) || !json_int(line, "features", &feat) ||
+        !json_int(line, "trials", &n) || !json_int(line, "max_height", &h) ||
+        !json_int(line, "layout", &lay) || !json_int(line, "flags", &fl) ||
+        !json_int(line, "variant", &v) || !json_int(line, "tile_rows", &tile) ||
+        !json_int(line, "group", &group) || !json_int(line, "warps", &warps))
+      continue;  // not an entry
+    if (gpu != ds->gpu_name || sms != ds->sms || rows != ds->N || feat != ds->F) continue;
+    Cfg c;
+    c.variant = (int)v;
+    c.tile_rows = (int)tile;
+    c.group = (int)group;
+    c.warps = (int)warps;
+    if (!gg::fitness_variant(c.variant)) continue;
+    ds->tuned[TuneKey((int)n, (int)h, (int)lay, (int)fl)] = c;
+    ++*taken;
+  }
+  std::fclose(f);
+  return GGEVAL_OK;
+}
+
+ggeval_status append_tuning(const ggeval_dataset* ds, const char* path, const TuneKey& k,
+                            const Cfg& c) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return fail(GGEVAL_ERR_ARG, "cannot open tuning cache %s", path);
+  std::fprintf(f,
+               "{\"gpu\": \"%s\", \"sms\": %d, \"rows\": %lld, \"features\": %d, "
+               "\"trials\": %d, \"max_height\": %d, \"layout\": %d, \"flags\": %d, "
+               "\"variant\": %d, \"tile_rows\": %d, \"group\": %d, \"warps\": %d}\n",
+               ds->gpu_name, ds->sms, (long long)ds->N, ds->F, std::get<0>(k), std::get<1>(k),
+               std::get<2>(k), std::get<3>(k), c.variant, c.tile_rows, c.group, c.warps);
+  std::fclose(f);
+  return GGEVAL_OK;
+}
+
 void drop_graph(ggeval_dataset* ds) {
   if (ds->gexec) cudaGraphExecDestroy(ds->gexec);
   ds->gexec = nullptr;
@@ -583,6 +663,11 @@ ggeval_status ggeval_create_dataset(const float* X, const float* y, int64_t n_ro
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   ds->smem_optin = (size_t)optin;
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess)
+      std::snprintf(ds->gpu_name, sizeof ds->gpu_name, "%s", prop.name);
+  }
   const size_t xbytes = (size_t)(F + 1) * ds->ldx * 4;
   if ((e = cudaMalloc(&ds->X, xbytes)) || (e = cudaMalloc(&ds->pref, ((size_t)N + 1) * 8)) ||
       (e = cudaMalloc(&ds->ylo, (size_t)ds->ldx * 4)) ||
@@ -980,6 +1065,17 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   if (b->n == 0) return GGEVAL_OK;
   if (b->memory != GGEVAL_MEM_DEVICE) return fail(GGEVAL_ERR_ARG, "autotune needs a device batch");
   DeviceGuard guard(ds->device);
+  const TuneKey tkey(b->n, b->max_height, b->layout,
+                     (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW)));
+  const char* cache = getenv("GGEVAL_TUNE_CACHE");
+  if (cache && cache[0]) {  // a cached choice for this GPU, dataset and batch shape
+    int taken = 0;
+    GG_TRY(load_tuning(ds, cache, &taken));
+    if (ds->tuned.count(tkey)) {
+      drop_graph(ds);
+      return GGEVAL_OK;
+    }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Cfg base = default_cfg(ds, b->n, b->max_height, flags);
   std::vector<int> variants;
@@ -1051,9 +1147,27 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   cudaEventDestroy(e1);
   cudaFree(out);
   if (result != GGEVAL_OK) return result;
-  ds->tuned[{b->n, b->max_height, b->layout, (int)(flags & (GGEVAL_F_EXACT | GGEVAL_F_POW))}] =
-      best;
+  ds->tuned[tkey] = best;
   drop_graph(ds);
+  if (cache && cache[0]) GG_TRY(append_tuning(ds, cache, tkey, best));
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_tuning_save(ggeval_dataset* ds, const char* path) {
+  if (!ds || !path) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(GGEVAL_ERR_ARG, "cannot open %s", path);
+  std::fclose(f);
+  for (const auto& kv : ds->tuned) GG_TRY(append_tuning(ds, path, kv.first, kv.second));
+  return GGEVAL_OK;
+}
+
+ggeval_status ggeval_tuning_load(ggeval_dataset* ds, const char* path, int32_t* n_loaded) {
+  if (!ds || !path) return fail(GGEVAL_ERR_ARG, "NULL argument");
+  int taken = 0;
+  GG_TRY(load_tuning(ds, path, &taken));
+  if (n_loaded) *n_loaded = taken;
+  if (taken) drop_graph(ds);
   return GGEVAL_OK;
 }
 

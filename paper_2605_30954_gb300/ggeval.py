@@ -31,7 +31,8 @@ SYMBOLS = ("ggeval_create_dataset", "ggeval_destroy", "ggeval_eval_batch", "ggev
            "ggeval_version", "ggeval_profile_read", "ggeval_eval_batch_noalloc",
            "ggeval_eval_batch_masked", "ggeval_gom_donate", "ggeval_gom_changed",
            "ggeval_gom_accept", "ggeval_trial_sizes", "ggeval_dataset_info",
-           "ggeval_tile_config", "ggeval_pipe_rates", "ggeval_evaluate")
+           "ggeval_tile_config", "ggeval_pipe_rates", "ggeval_evaluate", "ggeval_tuning_save",
+           "ggeval_tuning_load")
 
 
 class GGEvalError(RuntimeError):
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         "ggeval_trial_sizes": [bp, i32, vp, vp],
         "ggeval_tile_config": [vp, bp, u32, vp, vp],
         "ggeval_pipe_rates": [i32, i32, vp],
+        "ggeval_tuning_save": [vp, ctypes.c_char_p],
+        "ggeval_tuning_load": [vp, ctypes.c_char_p, ctypes.POINTER(i32)],
         "ggeval_evaluate": [vp, bp, u32, ctypes.POINTER(Outputs), vp],
         "ggeval_dataset_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -287,6 +290,16 @@ class Dataset:
     def autotune(self, op, cval, heights=None, layout=LAYOUT_HEAP, flags=0, stream=None):
         b = make_batch(op, cval, heights, layout=layout)
         _check(lib().ggeval_autotune(self._h, ctypes.byref(b), flags, _stream_handle(stream)))
+
+    def tuning_save(self, path):
+        """Write the autotuner's choices for this dataset to `path` (JSON lines)."""
+        _check(lib().ggeval_tuning_save(self._h, os.fsencode(path)))
+
+    def tuning_load(self, path):
+        """Take the matching choices from `path`; returns how many."""
+        n = ctypes.c_int32()
+        _check(lib().ggeval_tuning_load(self._h, os.fsencode(path), ctypes.byref(n)))
+        return n.value
 
     def sync(self, stream=None):
         _check(lib().ggeval_sync(self._h, _stream_handle(stream)))
