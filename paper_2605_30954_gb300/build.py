@@ -86,5 +86,26 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False, out: str =
     return out
 
 
+CHECKED_OUT = os.path.join(HERE, "_lib", "libggeval_checked.so")
+CHECKED_BUILD = os.path.join(HERE, "_build_checked")
+
+
+def build_checked(verbose: bool = False, force: bool = False) -> str:
+    """The checked library: the C++ interpreter with every shared-memory
+    stack and feature access and every tile copy bounds-checked
+    (GGEVAL_CHECKED; a violation is recorded in the status word, never
+    trapped).  For tests on small cases."""
+    return build(verbose, ["-DGGEVAL_CHECKED", "-DGG_INTERP_CXX"], force, CHECKED_OUT,
+                 CHECKED_BUILD)
+
+
+def build_all(verbose: bool = False, force: bool = False):
+    """The library and its checked build, compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        a = ex.submit(build, verbose, (), force)
+        b = ex.submit(build_checked, verbose, force)
+        return a.result(), b.result()
+
+
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build_all(verbose="-v" in sys.argv, force="-f" in sys.argv))

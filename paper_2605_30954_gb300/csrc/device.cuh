@@ -255,6 +255,30 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
     reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// Bounds of the checked build (GGEVAL_CHECKED): a lane's stack slots and
+// the tile's feature rows.  Every stack and feature access of the C++
+// interpreter is tested first; an access outside records ST_CHECKED in the
+// status word and reads or writes the region's first entry instead (no
+// trap, no access out of bounds).
+struct Checks {
+  const float* stk_lo;
+  const float* stk_hi;
+  const float* feat_lo;
+  const float* feat_hi;
+  unsigned* status;
+};
+static __device__ __noinline__ void record_violation(unsigned* status) {
+  atomicOr(status, 4u);  // ST_CHECKED
+}
+#ifdef GGEVAL_CHECKED
+#define GG_IN(ptr, lo, hi)                                                          \
+  (cb && !((ptr) >= cb->lo && (ptr) + R <= cb->hi) ? (record_violation(cb->status), \
+                                                      const_cast<float*>(cb->lo))  \
+                                                   : (ptr))
+#else
+#define GG_IN(ptr, lo, hi) (ptr)
+#endif
+
 // The feature row `byte_off` bytes past xs (the staged words' offsets).
 __device__ __forceinline__ const float* feature_at(const float* xs, uint32_t byte_off) {
   return reinterpret_cast<const float*>(reinterpret_cast<const char*>(xs) + byte_off);
@@ -282,7 +306,8 @@ template <int R, bool TAPE = false, bool PRESCALED = false, bool POW = false>
 __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int L,
                                             const float* __restrict__ xs, int ts,
                                             float (&A)[R], float* __restrict__ stk,
-                                            float* __restrict__ tape = nullptr) {
+                                            float* __restrict__ tape = nullptr,
+                                            const Checks* cb = nullptr) {
   constexpr int SLOT = 32 * R;  // floats per stack slot
   float* sp = stk;              // next free slot of this lane
   {
@@ -290,7 +315,8 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     // load without a push exactly there), so it is peeled off the switch
     const uint2 first = prog[0];
     if ((PRESCALED ? first.x : first.x & 0xffu) == I_LDF0) {
-      load_rows<R>(PRESCALED ? feature_at(xs, first.y) : xs + (first.x >> 8) * ts, A);
+      load_rows<R>(GG_IN(PRESCALED ? feature_at(xs, first.y) : xs + (first.x >> 8) * ts,
+                         feat_lo, feat_hi), A);
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = __uint_as_float(first.y);
@@ -312,7 +338,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;
 #define GG_BIN_AT(kd, off)                                                  \
   case I_BF + kd + (off):                                                \
-    load_rows<R>(xf, t);                                              \
+    load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
     binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_BC + kd + (off):                                                \
@@ -320,7 +346,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_LF + kd + (off):                                                \
-    load_rows<R>(xf, t);                                              \
+    load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
     binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_LC + kd + (off):                                                \
@@ -329,24 +355,24 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;                                                            \
   case I_BS + kd + (off):                                                \
     sp -= SLOT;                                                       \
-    load_rows<R>(sp, t);                                              \
+    load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
     binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_RS + kd + (off):                                                \
     sp -= SLOT;                                                       \
-    load_rows<R>(sp, t);                                              \
+    load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
     binop_rows<kd, R>(A, t, A);                                       \
     break;
 
 #define GG_BIN(kd) GG_BIN_AT(kd, 0u)
     switch (opc) {
       case I_PSF:
-        store_rows<R>(sp, A);
+        store_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
         sp += SLOT;
-        load_rows<R>(xf, A);
+        load_rows<R>(GG_IN(xf, feat_lo, feat_hi), A);
         break;
       case I_PSC:
-        store_rows<R>(sp, A);
+        store_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
         sp += SLOT;
         GG_ROWS A[r] = c;
         break;
@@ -386,7 +412,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
           switch (opc) {
             case I_PW + 0:
             case I_BF + K_DIV:
-              load_rows<R>(xf, t);
+              load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);
               break;
             case I_PW + 1:
             case I_BC + K_DIV:
@@ -395,7 +421,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
             case I_PW + 2:
             case I_LF + K_DIV:
               GG_ROWS t[r] = A[r];
-              load_rows<R>(xf, A);
+              load_rows<R>(GG_IN(xf, feat_lo, feat_hi), A);
               break;
             case I_PW + 3:
             case I_LC + K_DIV:
@@ -408,12 +434,12 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
             case I_BS + K_DIV:
               sp -= SLOT;
               GG_ROWS t[r] = A[r];
-              load_rows<R>(sp, A);
+              load_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
               break;
             case I_PWR:
             case I_RS + K_DIV:
               sp -= SLOT;
-              load_rows<R>(sp, t);
+              load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);
               break;
             default:  // the packer emits only the opcodes above
               __builtin_unreachable();

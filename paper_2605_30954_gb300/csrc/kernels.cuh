@@ -172,6 +172,19 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int n_items, in
       }
     }
     __syncwarp();
+#ifdef GGEVAL_CHECKED
+    // the copy must stay inside the dataset and the tile buffer: otherwise
+    // record the violation and complete the barrier without copying
+    const bool copy_ok = row0 + ncopy <= p.ldx && ncopy <= p.tile_rows;
+    if (!copy_ok) {
+      if (lane == 0) {
+        record_violation(p.status);
+        ctl[0] = item;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+      }
+      return;
+    }
+#endif
     if (lane == 0) {
       ctl[0] = item;
       if (!p.stall) {
@@ -306,7 +319,9 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * R;
 #ifdef GG_INTERP_CXX
-        run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk);
+        const Checks cb{stk, stk + (size_t)p.slots * 32 * R, xs + r0,
+                        xs + r0 + (size_t)p.F * p.tile_rows, p.status};
+        run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk, nullptr, &cb);
 #else
         run_program_fast<R, POW>(wprog, xs + r0, A, stk);
 #endif
