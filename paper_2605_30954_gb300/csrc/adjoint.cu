@@ -106,6 +106,14 @@ __device__ __forceinline__ void dun_rows(int u, const float (&g)[R], float (&x)[
   }
 }
 
+// Whether an instruction carries an ERC: a constant load, or a constant
+// fused into a binary instruction.
+template <bool POW>
+__device__ __forceinline__ bool carries_erc(uint32_t opc) {
+  return opc == I_LDC0 || opc == I_PSC || (opc >= I_BC && opc < I_BC + NKIND) ||
+         (opc >= I_LC && opc < I_LC + NKIND) || (POW && (opc == I_PW + 1 || opc == I_PW + 3));
+}
+
 // R rows per lane: each lane runs rows row0 .. row0 + R - 1 of a 32 R-row
 // group (feature-major X, so a lane's rows are one aligned R-wide load).
 // Values and adjoints live at V[instruction][lane][row]; rows past the
@@ -119,9 +127,13 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots, R);
   uint2* wprog = reinterpret_cast<uint2*>(base);
   Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
-  float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per instruction
-  float* V = reinterpret_cast<float*>(wg + p.lstride) + lane * R;  // [lstride][32][R]
-  float* stk = V + (size_t)p.lstride * SLOT;                         // [slots][32][R]
+  float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per ERC ordinal
+  uint16_t* eord = reinterpret_cast<uint16_t*>(wg + p.lstride);  // instruction -> ordinal
+  uint16_t* ek = eord + p.lstride;                                // ordinal -> instruction
+  float* V0 = reinterpret_cast<float*>(base + adj_head_bytes(p.lstride));
+  float* V = V0 + lane * R;                                  // [lstride][32][R]
+  float* stk = V + (size_t)p.lstride * SLOT;                 // [slots][32][R]
+  float* part = V0 + (size_t)(p.lstride + p.slots) * SLOT;   // [lstride / 2][33]
 
   for (;;) {
     int item = 0;
@@ -145,6 +157,20 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       wprog[k] = src[k];
       waux[k] = asrc[k];
       wg[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    // ordinals of the instructions that carry an ERC, in program order
+    int n_erc = 0;
+    for (int k0 = 0; k0 < L; k0 += 32) {
+      const int k = k0 + lane;
+      const bool has = k < L && carries_erc<POW>(wprog[k].x & 0xffu);
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        const int o = n_erc + __popc(m & ((1u << lane) - 1u));
+        eord[k] = (uint16_t)o;
+        ek[o] = (uint16_t)k;
+      }
+      n_erc += __popc(m);
     }
     __syncwarp();
 
@@ -255,31 +281,36 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
           store_rows<R>(vb, b);
         }
         if (has_erc) {  // warp-uniform: the same instruction on every lane
+          // this lane's rows summed; the 32 lanes are summed after the sweep
           float sm = 0.f;
 #pragma unroll
           for (int r = 0; r < R; ++r) sm += valid[r] ? ge[r] : 0.f;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
-          if (lane == 0) {
-            float2 acc = wg[k];
-            acc_add(acc.x, acc.y, sm);
-            wg[k] = acc;
-          }
+          part[(size_t)eord[k] * 33 + lane] = sm;
         }
         __syncwarp();
       }
+      // the pass's ERC sums: lane o adds up the 32 lane partials of the ERCs
+      // o, o + 32, ... (rows padded to 33 floats: no bank conflicts) into
+      // its error-free accumulators (one transposed reduction per pass
+      // instead of a shuffle reduction per ERC instruction)
+      for (int o = lane; o < n_erc; o += 32) {
+        const float* q = part + (size_t)o * 33;
+        float sm = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) sm += q[j];
+        float2 acc = wg[o];
+        acc_add(acc.x, acc.y, sm);
+        wg[o] = acc;
+      }
+      __syncwarp();
     }
     __syncwarp();
-    for (int k = lane; k < L; k += 32) {
+    for (int o = lane; o < n_erc; o += 32) {
+      const int k = ek[o];
       const uint32_t opc = wprog[k].x & 0xffu;
-      int tp = -1;
-      if (opc == I_LDC0 || opc == I_PSC) tp = waux[k].tpos;
-      else if ((opc >= I_BC && opc < I_BC + NKIND) || (opc >= I_LC && opc < I_LC + NKIND) ||
-               (POW && (opc == I_PW + 1 || opc == I_PW + 3)))
-        tp = waux[k].tpos_fused;
-      const double gk = (double)wg[k].x + (double)wg[k].y;
-      if (tp >= 0 && tp != NONE16 && gk != 0.0)
-        atomicAdd(p.gacc + (size_t)trial * p.stride + tp, gk);
+      const int tp = (opc == I_LDC0 || opc == I_PSC) ? waux[k].tpos : waux[k].tpos_fused;
+      const double gk = (double)wg[o].x + (double)wg[o].y;
+      if (tp != NONE16 && gk != 0.0) atomicAdd(p.gacc + (size_t)trial * p.stride + tp, gk);
     }
     __syncwarp();
   }

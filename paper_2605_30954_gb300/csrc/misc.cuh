@@ -49,11 +49,20 @@ struct TransposeParams {
   int N, F, ldx;
 };
 
-// per warp and program instruction: word, side information, (hi, lo)
-// gradient accumulator, and one value or adjoint for each of 32 lanes x R
-// rows; then the warp's stack of `slots` x 32 x R floats
+// per warp: for each program instruction its word, side information, an
+// (hi, lo) gradient accumulator (indexed by ERC ordinal) and two 16-bit
+// ERC maps (instruction -> ordinal, ordinal -> instruction), padded to 16
+// bytes; one value or adjoint per instruction for each of 32 lanes x R
+// rows; the stack of `slots` x 32 x R floats; and the per-pass ERC partial
+// sums, 33 floats (32 lanes, padded) for each of at most lstride / 2 ERCs
+// (a tree of height h has at most 2^h active terminals)
+__host__ __device__ inline size_t adj_head_bytes(int lstride) {
+  return ((size_t)lstride * (8 + 8 + 8 + 2 + 2) + 15) & ~(size_t)15;
+}
 __host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots, int rows) {
-  return (size_t)lstride * (8 + 8 + 8 + 32 * 4 * (size_t)rows) + (size_t)slots * 32 * 4 * rows;
+  const size_t b = adj_head_bytes(lstride) + (size_t)lstride * 32 * 4 * rows +
+                   (size_t)slots * 32 * 4 * rows + (size_t)(lstride / 2) * 33 * 4;
+  return (b + 15) & ~(size_t)15;  // the next warp's value array stays 16-byte aligned
 }
 inline size_t adj_smem_bytes(int warps, int lstride, int slots, int rows) {
   return (size_t)warps * adj_warp_bytes(lstride, slots, rows) + 16;

@@ -54,7 +54,9 @@ class Batch(ctypes.Structure):
                 ("height", ctypes.c_void_p)]
 
 
-def load_library(path: str = LIB_PATH):
+def load_library(path: str = LIB_PATH, strict: bool = True):
+    """Load the library at `path`; with strict False, entry points the build
+    does not export are left out (an older build)."""
     if not os.path.exists(path):
         raise ImportError(f"ggeval CUDA library not built: {path} is missing "
                           "(run __graft_entry__.build())")
@@ -93,6 +95,8 @@ def load_library(path: str = LIB_PATH):
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
+        if not strict and not hasattr(lib, name):
+            continue
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
