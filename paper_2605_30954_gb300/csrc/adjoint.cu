@@ -118,13 +118,34 @@ __device__ __forceinline__ bool carries_erc(uint32_t opc) {
 // group (feature-major X, so a lane's rows are one aligned R-wide load).
 // Values and adjoints live at V[instruction][lane][row]; rows past the
 // chunk's end are evaluated on in-bounds data and left out of every sum.
+// The forward half as the PTX interpreter with a value tape (4 rows per
+// lane): the instruction the PTX leaves is run and taped here.
 template <int R, bool POW>
+__device__ __forceinline__ void run_program_tape(const uint2* prog, const float* xs,
+                                                 float (&A)[R], float* stk, float* tape) {
+  uint32_t pc = smem_u32(prog), sp = smem_u32(stk), code = 0, arg = 0, tp = smem_u32(tape);
+  const uint32_t xb = smem_u32(xs);
+  for (;;) {
+    interp_tape_asm<R>(A, pc, sp, xb, code, arg, tp);
+    if (code == I_NOP || code >= I_COUNT) break;
+    exec_cold<R, POW>(code, arg, A, sp, xs);
+    store_rows<R>(static_cast<float*>(__cvta_shared_to_generic(tp)), A);
+    tp += 32 * R * 4;
+  }
+}
+
+// FAST (4 rows per lane, at most ADJ_FTILE_MAX features): each pass stages
+// the lanes' rows of every feature into a shared-memory tile and runs the
+// forward half with the PTX interpreter (run_program_tape); otherwise the
+// C++ interpreter reads the features from global memory.
+template <int R, bool POW, bool FAST>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int SLOT = 32 * R;
-  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots, R);
+  const int ftile = FAST ? p.F : 0;
+  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots, R, ftile);
   uint2* wprog = reinterpret_cast<uint2*>(base);
   Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
   float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per ERC ordinal
@@ -134,6 +155,14 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   float* V = V0 + lane * R;                                  // [lstride][32][R]
   float* stk = V + (size_t)p.lstride * SLOT;                 // [slots][32][R]
   float* part = V0 + (size_t)(p.lstride + p.slots) * SLOT;   // [lstride / 2][33]
+  // FAST: the staged program and the feature tile [F][32][R], after the above
+  unsigned char* fast_base =
+      base + ((adj_head_bytes(p.lstride) + (size_t)p.lstride * 32 * 4 * R +
+               (size_t)p.slots * 32 * 4 * R + (size_t)(p.lstride / 2) * 33 * 4 + 15) &
+              ~(size_t)15);
+  uint2* sprog = reinterpret_cast<uint2*>(fast_base);
+  float* xt = reinterpret_cast<float*>(fast_base + (((size_t)(p.lstride + 1) * 8 + 15) &
+                                                    ~(size_t)15));  // 16-byte aligned
 
   for (;;) {
     int item = 0;
@@ -154,10 +183,16 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
     const uint2* src = p.prog + (size_t)trial * p.lstride;
     const Aux* asrc = p.aux + (size_t)trial * p.lstride;
     for (int k = lane; k <= L; k += 32) {
-      wprog[k] = src[k];
+      const uint2 w = src[k];
+      wprog[k] = w;
       waux[k] = asrc[k];
       wg[k] = make_float2(0.f, 0.f);
+      if constexpr (FAST) {  // the interpreter's staged form: bare opcode, feature byte offset
+        const uint32_t op = w.x & 0xffu;
+        sprog[k] = make_uint2(op, reads_feature(op) ? (w.x >> 8) * (uint32_t)(SLOT * 4) : w.y);
+      }
     }
+    if (FAST && lane == 0) sprog[L + 1] = make_uint2(I_NOP, 0u);  // read ahead, never run
     __syncwarp();
     // ordinals of the instructions that carry an ERC, in program order
     int n_erc = 0;
@@ -185,7 +220,17 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       float A[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = 0.f;
-      run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
+      if constexpr (FAST) {
+        for (int f = 0; f < p.F; ++f) {
+          float v[R];
+          load_rows<R>(p.X + (size_t)f * p.ldx + row0, v);
+          store_rows<R>(xt + (size_t)f * SLOT + lane * R, v);
+        }
+        __syncwarp();
+        run_program_tape<R, POW>(sprog, xt + lane * R, A, stk, V);
+      } else {
+        run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
+      }
       float yc[R], yl[R];
       load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
       load_rows<R>(p.ylo + row0, yl);
@@ -316,14 +361,18 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   }
 }
 
-const void* adj_ptr(int rows, bool pow) {
+const void* adj_ptr(int rows, bool pow, bool fast) {
   switch (rows) {
-    case 4: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<4, false>);
-    case 2: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<2, true>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<2, false>);
-    default: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<1, true>)
-                        : reinterpret_cast<const void*>(&adjoint_kernel<1, false>);
+    case 4:
+      if (fast)
+        return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true, true>)
+                   : reinterpret_cast<const void*>(&adjoint_kernel<4, false, true>);
+      return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true, false>)
+                 : reinterpret_cast<const void*>(&adjoint_kernel<4, false, false>);
+    case 2: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<2, true, false>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<2, false, false>);
+    default: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<1, true, false>)
+                        : reinterpret_cast<const void*>(&adjoint_kernel<1, false, false>);
   }
 }
 

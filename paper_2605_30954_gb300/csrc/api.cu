@@ -945,15 +945,18 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   // 1,000,000 rows 2.20 / 1.78 / 1.90 s (10 / 6 / 3 warps).
   const void* afn = nullptr;
   int rows = 0, warps = 0, nb = 0;
+  int ftile = 0;  // > 0: the 4-row adjoint stages features and runs the PTX forward
   for (int R : {4, 2, 1}) {
-    const void* fn = gg::adj_ptr(R, pl.pow);
+    const int ft = (R == 4 && ds->F <= gg::ADJ_FTILE_MAX) ? ds->F : 0;
+    const void* fn = gg::adj_ptr(R, pl.pow, ft > 0);
     GG_TRY(prepare_kernel(ds->device, fn));
     int wR = 0, nR = 0;
-    const int wmax = (int)((ds->smem_optin - 64) / gg::adj_warp_bytes(pl.lstride, pl.slots, R));
+    const int wmax =
+        (int)((ds->smem_optin - 64) / gg::adj_warp_bytes(pl.lstride, pl.slots, R, ft));
     for (int w = wmax < 8 ? wmax : 8; w >= 1; --w) {
       int n = 0;
       GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, fn, w * 32, gg::adj_smem_bytes(w, pl.lstride, pl.slots, R)));
+          &n, fn, w * 32, gg::adj_smem_bytes(w, pl.lstride, pl.slots, R, ft)));
       if (n * w > nR * wR) {
         wR = w;
         nR = n;
@@ -965,11 +968,12 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
       rows = R;
       warps = wR;
       nb = nR;
+      ftile = ft;
       if (nR * wR >= 6) break;
     }
   }
   if (!afn) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
-  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride, pl.slots, rows);
+  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride, pl.slots, rows, ftile);
   if (const char* env = getenv("GGEVAL_VERBOSE"))
     if (env[0] == '1')
       fprintf(stderr, "ggeval adjoint: %d rows per lane, %d warps per CTA, %d CTAs per SM\n", rows,

@@ -105,6 +105,29 @@ static __device__ __noinline__ float sincos_library(float x, int shift) {
   return shift ? cosf(x) : sinf(x);
 }
 
+// The row-by-row forms for a group of rows of which some lie outside the
+// own-math forms' common domain: out of line, with rolled loops, so that the
+// interpreter's switch stays compact and this cold code holds few registers
+// (the caller saves the ones it clobbers around the call).
+template <int R>
+__device__ __noinline__ void sincos_special(float (&A)[R], int shift) {
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    const float x = A[r];
+    A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
+  }
+}
+template <int R, bool LOG>
+__device__ __noinline__ void logsqrt_special(float (&A)[R]) {
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) A[r] = LOG ? log_total(__float_as_uint(A[r])) : sqrt_total(A[r]);
+}
+template <int R>
+__device__ __noinline__ void exp_special(float (&A)[R]) {
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) A[r] = exp_total(A[r]);
+}
+
 // sin and cos on the R rows of a lane: the branch-free form of gmath.cuh,
 // on row pairs as packed instructions when R is even.  One test of the
 // rows' largest magnitude sends a group with an argument beyond the
@@ -118,11 +141,7 @@ __device__ __forceinline__ void sincos_rows(float (&A)[R], int shift) {
 #pragma unroll
   for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
   if (__builtin_expect(!(mx <= TRIG_RANGE), 0)) {
-#pragma unroll 1
-    for (int r = 0; r < R; ++r) {
-      const float x = A[r];
-      A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
-    }
+    sincos_special<R>(A, shift);
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -150,9 +169,7 @@ __device__ __forceinline__ void logsqrt_rows(float (&A)[R], uint32_t mask) {
     special |= outside_positive_normal(b);
   }
   if (__builtin_expect(special, 0)) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      A[r] = LOG ? log_total(__float_as_uint(A[r])) : sqrt_total(A[r]);
+    logsqrt_special<R, LOG>(A);
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -178,8 +195,7 @@ __device__ __forceinline__ void exp_rows(float (&A)[R]) {
 #pragma unroll
   for (int r = 1; r < R; ++r) mx = fmaxf(mx, fabsf(A[r]));
   if (__builtin_expect(!(mx <= EXP_RANGE), 0)) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) A[r] = exp_total(A[r]);
+    exp_special<R>(A);
   } else if constexpr (R % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
@@ -593,24 +609,32 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 #include "interp_asm.inc"
 
 // One instruction the PTX interpreter left (opcode `code`, operand word
-// `arg`), run by the C++ bodies of run_program: sin or cos with an argument
-// beyond the reduction's range, and pow.  Out of line: the rare cases stay
-// off the hot loop's instruction stream.
+// `arg`), run by the C++ bodies of run_program: a group of rows of sin, cos,
+// exp, log or sqrt of which some lie outside the own-math forms' common
+// domain (row by row; the 4-row PTX finishes exp, log and sqrt itself), and
+// pow.  Out of line: the rare cases stay off the hot loop's instruction
+// stream.
 template <int R, bool POW>
 __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R],
                                        uint32_t& sp, const float* xs) {
   constexpr uint32_t SLOTB = 32 * R * 4;
   switch (code) {
     case I_UN + U_SIN:
-    case I_UN + U_COS: {
-      // sincos_rows' cold branch, one row at a time: loops left rolled keep
-      // this callee's registers (which the caller saves around the call) few
-      const int shift = (int)(code - (I_UN + U_SIN));
+    case I_UN + U_COS:
+      sincos_special<R>(A, (int)(code - (I_UN + U_SIN)));
+      break;
+    case I_UN + U_EXP:
+      exp_special<R>(A);
+      break;
+    case I_UN + U_LOG_ABS:
+    case I_UN + U_LOG:
+    case I_UN + U_SQRT_ABS:
+    case I_UN + U_SQRT: {
+      const uint32_t mask = (code == I_UN + U_LOG || code == I_UN + U_SQRT) ? ~0u : ABS_MASK;
 #pragma unroll 1
-      for (int r = 0; r < R; ++r) {
-        const float x = A[r];
-        A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
-      }
+      for (int r = 0; r < R; ++r) A[r] = __uint_as_float(__float_as_uint(A[r]) & mask);
+      if (code == I_UN + U_LOG_ABS || code == I_UN + U_LOG) logsqrt_special<R, true>(A);
+      else logsqrt_special<R, false>(A);
       break;
     }
     default:

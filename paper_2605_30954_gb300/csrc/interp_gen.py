@@ -85,16 +85,24 @@ def f2(s: str) -> str:
 
 
 class Gen:
-    def __init__(self, R: int):
+    def __init__(self, R: int, special: bool = True, tape: bool = False):
+        """special: finish the row-by-row forms of exp, log and sqrt inside
+        the PTX (else their groups leave it for the C++ cold path).  tape:
+        store the accumulator after every instruction at the tape address
+        (advanced by one slot each time): the forward half of the adjoint."""
         assert R in (4, 8)
         self.R = R
+        self.special = special
+        self.tape = tape
         self.NP = R // 2          # row pairs per lane
         self.NQ = R // 4          # 16-byte shared-memory accesses per row group
         self.SLOTB = 32 * R * 4   # bytes per stack slot (32 lanes x R rows)
         self.lines = []
-        # asm operands: %0 pc, %1 sp, %2 code, %3 arg, %4.. A[0..R-1], then xs
+        # asm operands: %0 pc, %1 sp, %2 code, %3 arg, %4.. A[0..R-1], then
+        # (with tape) the tape address, then xs
         self.A = [f"%{4 + r}" for r in range(R)]
-        self.XS = f"%{4 + R}"
+        self.TP = f"%{4 + R}" if tape else None
+        self.XS = f"%{5 + R}" if tape else f"%{4 + R}"
 
     def o(self, s):
         self.lines.append(s)
@@ -117,8 +125,12 @@ class Gen:
             self.o(f"mov.b64 {dst}{i}, {dst}0;")
 
     def next(self):
-        """Fetch the prefetched instruction, prefetch the one after it and
-        branch through the table (an out-of-range opcode goes to BAD)."""
+        """(With tape: store the finished instruction's rows.)  Fetch the
+        prefetched instruction, prefetch the one after it and branch through
+        the table (an out-of-range opcode goes to BAD)."""
+        if self.tape:
+            self.store("a", self.TP)
+            self.o(f"add.u32 {self.TP}, {self.TP}, {self.SLOTB};")
         self.o("min.u32 opc, nopc, %d;" % I_COUNT)
         self.o("mov.u32 arg, narg;")
         self.o("add.u32 %0, %0, 8;")
@@ -410,7 +422,7 @@ class Gen:
     def log_body(self):
         """gmath.cuh log_normal2 on every pair of the masked rows."""
         self.label("GG_LOG")
-        self.logsqrt_check("GG_LOG_SP")
+        self.logsqrt_check("GG_LOG_SP" if self.special else "GG_EXIT")
         o = self.o
         for i in range(self.NP):
             for e in (0, 1):
@@ -442,7 +454,7 @@ class Gen:
     def sqrt_body(self):
         """gmath.cuh sqrt_newton2 on every pair of the masked rows."""
         self.label("GG_SQRT")
-        self.logsqrt_check("GG_SQRT_SP")
+        self.logsqrt_check("GG_SQRT_SP" if self.special else "GG_EXIT")
         for i in range(self.NP):
             self.sqrt_pair(i)
         self.next()
@@ -457,7 +469,7 @@ class Gen:
             self.o(f"abs.f32 s0, x{r};")
             self.o("mov.f32 m, s0;" if r == 0 else "max.f32 m, m, s0;")
         self.o(f"setp.gtu.f32 p, m, {f(EXP_RANGE)};")
-        self.o("@p bra GG_EXP_SP;")
+        self.o("@p bra GG_EXP_SP;" if self.special else "@p bra GG_EXIT;")
         for i in range(self.NP):
             self.o(f"mov.b64 c1, {f2(LOG2E_HI)};")
             self.o(f"mul.rn.f32x2 v0, a{i}, c1;")                   # hi
@@ -577,9 +589,10 @@ class Gen:
         self.log_body()
         self.sqrt_body()
         self.exp_body()
-        self.log_special_body()
-        self.sqrt_special_body()
-        self.exp_special_body()
+        if self.special:
+            self.log_special_body()
+            self.sqrt_special_body()
+            self.exp_special_body()
         # exit: the opcode that stopped and its operand word; pc already
         # points at the next instruction
         self.label("GG_EXIT")
@@ -591,16 +604,19 @@ class Gen:
         return self.lines
 
 
-def emit(R: int) -> str:
-    g = Gen(R)
+def emit(R: int, special: bool, tape: bool = False) -> str:
+    g = Gen(R, special, tape)
     lines = g.build()
     body = "\n".join('      "' + ln + '\\n\\t"' for ln in lines)
     outs = ", ".join(f'"+f"(A[{r}])' for r in range(R))
+    name, extra_param, extra_op = "interp_asm", "", ""
+    if tape:
+        name, extra_param, extra_op = "interp_tape_asm", ", uint32_t& tp", ', "+r"(tp)'
     return (f"template <>\n"
-            f"__device__ __forceinline__ void interp_asm<{R}>(float (&A)[{R}], uint32_t& pc,\n"
-            f"    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg) {{\n"
+            f"__device__ __forceinline__ void {name}<{R}>(float (&A)[{R}], uint32_t& pc,\n"
+            f"    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg{extra_param}) {{\n"
             f"  asm volatile(\n{body}\n"
-            f'      : "+r"(pc), "+r"(sp), "+r"(code), "+r"(arg), {outs}\n'
+            f'      : "+r"(pc), "+r"(sp), "+r"(code), "+r"(arg), {outs}{extra_op}\n'
             f'      : "r"(xs)\n'
             f'      : "memory");\n'
             f"}}\n")
@@ -608,11 +624,22 @@ def emit(R: int) -> str:
 
 def generate() -> str:
     head = ("// Generated by interp_gen.py (run by build.py); do not edit.\n"
-            "// The interpreter's dispatch loop as inline PTX for 8 and 4 rows per lane.\n"
+            "// The interpreter's dispatch loop as inline PTX for 8 and 4 rows per lane,\n"
+            "// and with a value tape (the adjoint's forward half) for 4 rows per lane.\n"
             "template <int R>\n"
             "__device__ __forceinline__ void interp_asm(float (&A)[R], uint32_t& pc,\n"
-            "    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg);\n\n")
-    return head + emit(8) + "\n" + emit(4)
+            "    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg);\n"
+            "template <int R>\n"
+            "__device__ __forceinline__ void interp_tape_asm(float (&A)[R], uint32_t& pc,\n"
+            "    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg, uint32_t& tp);\n\n")
+    # The 8-row PTX leaves the rare row-by-row groups of exp, log and sqrt to
+    # the C++ cold path: their bodies, four row pairs long, made the hot
+    # code larger than the instruction cache serves well (measured on the
+    # largest workload: 53.0 ms per step without them, 66.9 ms with).  The
+    # 4-row PTX, half the size, keeps them (the autotuner picks it for the
+    # operator sets whose unprotected log and sqrt often meet negatives).
+    return (head + emit(8, special=False) + "\n" + emit(4, special=True) + "\n" +
+            emit(4, special=True, tape=True))
 
 
 def main(out_path: str) -> None:

@@ -59,19 +59,28 @@ struct TransposeParams {
 __host__ __device__ inline size_t adj_head_bytes(int lstride) {
   return ((size_t)lstride * (8 + 8 + 8 + 2 + 2) + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots, int rows) {
-  const size_t b = adj_head_bytes(lstride) + (size_t)lstride * 32 * 4 * rows +
-                   (size_t)slots * 32 * 4 * rows + (size_t)(lstride / 2) * 33 * 4;
+// With ftile > 0 (the PTX forward recompute) also the program in the
+// interpreter's staged form (lstride + 1 words) and a tile of ftile
+// feature rows x 32 lanes x R rows.
+__host__ __device__ inline size_t adj_warp_bytes(int lstride, int slots, int rows, int ftile = 0) {
+  size_t b = adj_head_bytes(lstride) + (size_t)lstride * 32 * 4 * rows +
+             (size_t)slots * 32 * 4 * rows + (size_t)(lstride / 2) * 33 * 4;
+  b = (b + 15) & ~(size_t)15;
+  if (ftile > 0) b += (((size_t)(lstride + 1) * 8 + 15) & ~(size_t)15) +
+                     (size_t)ftile * 32 * 4 * rows;
   return (b + 15) & ~(size_t)15;  // the next warp's value array stays 16-byte aligned
 }
-inline size_t adj_smem_bytes(int warps, int lstride, int slots, int rows) {
-  return (size_t)warps * adj_warp_bytes(lstride, slots, rows) + 16;
+inline size_t adj_smem_bytes(int warps, int lstride, int slots, int rows, int ftile = 0) {
+  return (size_t)warps * adj_warp_bytes(lstride, slots, rows, ftile) + 16;
 }
+// feature counts up to which the 4-rows-per-lane adjoint stages a feature
+// tile and runs its forward recompute with the PTX interpreter
+constexpr int ADJ_FTILE_MAX = 16;
 
 const void* pack_ptr();
 const void* fin_ptr();
 const void* compact_ptr();
-const void* adj_ptr(int rows, bool pow);
+const void* adj_ptr(int rows, bool pow, bool fast);
 const void* gradout_ptr();
 const void* adam_ptr();
 const void* transpose_ptr();
