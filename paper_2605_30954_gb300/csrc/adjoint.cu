@@ -1,10 +1,12 @@
 // Reverse-mode adjoint: d(scaled MSE)/d(constant) for every ERC leaf of
 // every trial.
 //
-// Work item = (trial, chunk of rows); warps claim items from a global
-// counter.  For 32 rows at a time (one per lane) a warp re-runs the trial's
-// program forward, storing the value of every instruction in a shared-memory
-// array V, seeds the output adjoint with
+// The trials are binned by program length (adj_bin_kernel); one launch per
+// length class sizes its per-warp shared memory for the class.  Work item
+// = (trial, chunk of rows); warps claim items from the class's counter.
+// For 32 R rows at a time (R per lane) a warp re-runs the trial's program
+// forward, storing the value of every instruction in a shared-memory array
+// V, seeds the output adjoint with
 //   w_i = (2 b*/N) (a* + b* f_i - y_i)          (scaled MSE; envelope theorem)
 //   w_i = (2/N) (f_i - y_i)                     (plain MSE)
 // and sweeps the program backwards.  Every instruction's value has exactly
@@ -14,13 +16,14 @@
 // adjoint while its own operands still hold values.  The operators whose
 // derivative uses their own output (exp, sqrt, division) recompute it from
 // the operands.  The contribution of an ERC (pushed, or fused into its
-// parent) is summed over the warp's 32 rows with shuffles and added into a
+// parent) is summed over the lane's rows into a per-pass partial; after
+// the sweep the 32 lanes' partials are summed per ERC and added into a
 // per-warp error-free FP32 (hi, lo) accumulator; at the end of the item the
 // accumulators go to the trial's FP64 gradient row with atomics.  Node
-// values live only in shared memory for 32 rows at a time: nothing of size
-// rows x nodes is stored in HBM, so any dataset size works (recomputation
-// instead of storage).  The paper evaluates fitness only; this kernel is an
-// addition.
+// values live only in shared memory for 32 R rows at a time: nothing of
+// size rows x nodes is stored in HBM, so any dataset size works
+// (recomputation instead of storage).  The paper evaluates fitness only;
+// this kernel is an addition.
 #include "misc.cuh"
 
 namespace gg {
@@ -114,103 +117,152 @@ __device__ __forceinline__ bool carries_erc(uint32_t opc) {
          (opc >= I_LC && opc < I_LC + NKIND) || (POW && (opc == I_PW + 1 || opc == I_PW + 3));
 }
 
-// R rows per lane: each lane runs rows row0 .. row0 + R - 1 of a 32 R-row
-// group (feature-major X, so a lane's rows are one aligned R-wide load).
-// Values and adjoints live at V[instruction][lane][row]; rows past the
-// chunk's end are evaluated on in-bounds data and left out of every sum.
-// The forward half as the PTX interpreter with a value tape (4 rows per
-// lane): the instruction the PTX leaves is run and taped here.
-template <int R, bool POW>
-__device__ __forceinline__ void run_program_tape(const uint2* prog, const float* xs,
-                                                 float (&A)[R], float* stk, float* tape) {
-  uint32_t pc = smem_u32(prog), sp = smem_u32(stk), code = 0, arg = 0, tp = smem_u32(tape);
-  const uint32_t xb = smem_u32(xs);
-  for (;;) {
-    interp_tape_asm<R>(A, pc, sp, xb, code, arg, tp);
-    if (code == I_NOP || code >= I_COUNT) break;
-    exec_cold<R, POW>(code, arg, A, sp, xs);
-    store_rows<R>(static_cast<float*>(__cvta_shared_to_generic(tp)), A);
-    tp += 32 * R * 4;
+// Work items of one length class: about target_items of them (trial x
+// chunk of rows), a chunk a multiple of the rows a warp runs per pass.
+struct Chunking {
+  int chunk_rows, n_chunks, n_items;
+};
+__device__ __forceinline__ Chunking chunking(const AdjParams& p, int count, int group) {
+  Chunking c;
+  const int max_chunks = (p.N + group - 1) / group;
+  int n = count > 0 ? (p.target_items + count - 1) / count : 1;
+  n = max(1, min(n, max_chunks));
+  c.chunk_rows = ((p.N + n - 1) / n + group - 1) / group * group;
+  c.n_chunks = (p.N + c.chunk_rows - 1) / c.chunk_rows;
+  c.n_items = count * c.n_chunks;
+  return c;
+}
+
+// The output adjoint of R rows: (2 b*/N) (a* + b* f - y) (scaled MSE) or
+// (2/N) (f - y) (plain MSE), 0 for rows past the chunk's end.  The
+// residual is formed in double-float: TwoProd / TwoSum keep the rounding of
+// every term, so only f's own FP32 error remains (y = mean(y) + yc + yl
+// exactly to FP64 accuracy).
+template <int R>
+__device__ __forceinline__ void seed_rows(const AdjParams& p, const double* ab,
+                                          const float (&A)[R], const float (&yc)[R],
+                                          const float (&yl)[R], const bool (&valid)[R],
+                                          float (&w)[R]) {
+  // a* - mean(y), b* and mean(y) as FP32 (hi, lo) pairs of their FP64 values
+  const float a_hi = (float)ab[0], a_lo = (float)(ab[0] - (double)a_hi);
+  const float b_hi = (float)ab[1], b_lo = (float)(ab[1] - (double)b_hi);
+  const float yb_hi = (float)p.ybar, yb_lo = (float)(p.ybar - (double)yb_hi);
+  const float two_n = (float)(2.0 / (double)p.N);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float s, e1, e2, t, lo;
+    if (p.mse_mode) {
+      two_sum(A[r], -yb_hi, s, e1);
+      lo = -yb_lo;
+    } else {
+      const float pr = __fmul_rn(b_hi, A[r]);  // never contracted into an FMA
+      lo = fmaf(b_hi, A[r], -pr) + fmaf(b_lo, A[r], a_lo);
+      two_sum(a_hi, pr, s, e1);
+    }
+    two_sum(s, -yc[r], t, e2);
+    const float res = t + ((e1 + e2) + (lo - yl[r]));
+    w[r] = two_n * (p.mse_mode ? res : b_hi * res);
+    w[r] = valid[r] ? w[r] : 0.f;
   }
 }
 
-// FAST (4 rows per lane, at most ADJ_FTILE_MAX features): each pass stages
-// the lanes' rows of every feature into a shared-memory tile and runs the
-// forward half with the PTX interpreter (run_program_tape); otherwise the
-// C++ interpreter reads the features from global memory.
-template <int R, bool POW, bool FAST>
+// The pass's ERC sums: lane o adds up the 32 lane partials of the ERCs
+// o, o + 32, ... (rows padded to 33 floats: no bank conflicts) into its
+// error-free accumulators (one transposed reduction per pass instead of a
+// shuffle reduction per ERC instruction).
+__device__ __forceinline__ void reduce_erc(const float* part, float2* wg, int n_erc, int lane) {
+  for (int o = lane; o < n_erc; o += 32) {
+    const float* q = part + (size_t)o * 33;
+    float sm = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) sm += q[j];
+    float2 acc = wg[o];
+    acc_add(acc.x, acc.y, sm);
+    wg[o] = acc;
+  }
+}
+
+// The item's gradient: ERC ordinal o goes to template position ek[o].
+__device__ __forceinline__ void write_grad(const AdjParams& p, int trial, const float2* wg,
+                                           const uint16_t* ek, int n_erc, int lane) {
+  for (int o = lane; o < n_erc; o += 32) {
+    const int tp = ek[o];
+    const double gk = (double)wg[o].x + (double)wg[o].y;
+    if (tp != NONE16 && gk != 0.0) atomicAdd(p.gacc + (size_t)trial * p.stride + tp, gk);
+  }
+}
+
+__device__ __forceinline__ bool adj_skip(const AdjParams& p, int trial) {
+  const double* ab = p.ab + 4 * (size_t)trial;
+  return p.len[trial] <= 0 || ab[2] == 0.0 || (!p.mse_mode && ab[1] == 0.0);
+}
+
+// Generic form, R rows per lane: each lane runs rows row0 .. row0 + R - 1
+// of a 32 R-row group (feature-major X, so a lane's rows are one aligned
+// R-wide load); the forward recompute is the C++ interpreter reading the
+// features from global memory.  Values and adjoints live at
+// V[instruction][lane][row], private to the lane; rows past the chunk's end
+// are evaluated on in-bounds data and left out of every sum.
+template <int R, bool POW>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int SLOT = 32 * R;
-  const int ftile = FAST ? p.F : 0;
-  unsigned char* base = smem + (size_t)warp * adj_warp_bytes(p.lstride, p.slots, R, ftile);
-  uint2* wprog = reinterpret_cast<uint2*>(base);
-  Aux* waux = reinterpret_cast<Aux*>(wprog + p.lstride);
-  float2* wg = reinterpret_cast<float2*>(waux + p.lstride);  // (hi, lo) per ERC ordinal
-  uint16_t* eord = reinterpret_cast<uint16_t*>(wg + p.lstride);  // instruction -> ordinal
-  uint16_t* ek = eord + p.lstride;                                // ordinal -> instruction
-  float* V0 = reinterpret_cast<float*>(base + adj_head_bytes(p.lstride));
-  float* V = V0 + lane * R;                                  // [lstride][32][R]
-  float* stk = V + (size_t)p.lstride * SLOT;                 // [slots][32][R]
-  float* part = V0 + (size_t)(p.lstride + p.slots) * SLOT;   // [lstride / 2][33]
-  // FAST: the staged program and the feature tile [F][32][R], after the above
-  unsigned char* fast_base =
-      base + ((adj_head_bytes(p.lstride) + (size_t)p.lstride * 32 * 4 * R +
-               (size_t)p.slots * 32 * 4 * R + (size_t)(p.lstride / 2) * 33 * 4 + 15) &
-              ~(size_t)15);
-  uint2* sprog = reinterpret_cast<uint2*>(fast_base);
-  float* xt = reinterpret_cast<float*>(fast_base + (((size_t)(p.lstride + 1) * 8 + 15) &
-                                                    ~(size_t)15));  // 16-byte aligned
+  const AdjLayout lay = adj_layout(p.lcap, p.ecap, p.slots, R, false, 0);
+  unsigned char* base = smem + (size_t)warp * lay.total;
+  uint2* wprog = reinterpret_cast<uint2*>(base + lay.prog);
+  Aux* waux = reinterpret_cast<Aux*>(base + lay.aux);
+  float2* wg = reinterpret_cast<float2*>(base + lay.wg);        // (hi, lo) per ERC ordinal
+  uint16_t* eord = reinterpret_cast<uint16_t*>(base + lay.eord);  // instruction -> ordinal
+  uint16_t* ek = reinterpret_cast<uint16_t*>(base + lay.ek);      // ordinal -> template position
+  float* V = reinterpret_cast<float*>(base + lay.V) + lane * R;   // [lcap][32][R]
+  float* stk = reinterpret_cast<float*>(base + lay.stk) + lane * R;
+  float* part = reinterpret_cast<float*>(base + lay.part);        // [ecap][33]
+  const Chunking ch = chunking(p, *p.count, SLOT);
 
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(p.counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= p.n_items) break;
-    const int trial = item / p.n_chunks;
-    const int chunk = item - trial * p.n_chunks;
+    if (item >= ch.n_items) break;
+    const int trial = p.list[item / ch.n_chunks];
+    const int chunk = item % ch.n_chunks;
+    if (adj_skip(p, trial)) continue;
     const int L = p.len[trial];
-    if (L <= 0) continue;
     const double* ab = p.ab + 4 * (size_t)trial;
-    if (ab[2] == 0.0 || (!p.mse_mode && ab[1] == 0.0)) continue;
-    // a* - mean(y), b* and mean(y) as FP32 (hi, lo) pairs of their FP64 values
-    const float a_hi = (float)ab[0], a_lo = (float)(ab[0] - (double)a_hi);
-    const float b_hi = (float)ab[1], b_lo = (float)(ab[1] - (double)b_hi);
-    const float yb_hi = (float)p.ybar, yb_lo = (float)(p.ybar - (double)yb_hi);
-    const float two_n = (float)(2.0 / (double)p.N);
     const uint2* src = p.prog + (size_t)trial * p.lstride;
     const Aux* asrc = p.aux + (size_t)trial * p.lstride;
-    for (int k = lane; k <= L; k += 32) {
-      const uint2 w = src[k];
-      wprog[k] = w;
-      waux[k] = asrc[k];
-      wg[k] = make_float2(0.f, 0.f);
-      if constexpr (FAST) {  // the interpreter's staged form: bare opcode, feature byte offset
-        const uint32_t op = w.x & 0xffu;
-        sprog[k] = make_uint2(op, reads_feature(op) ? (w.x >> 8) * (uint32_t)(SLOT * 4) : w.y);
-      }
-    }
-    if (FAST && lane == 0) sprog[L + 1] = make_uint2(I_NOP, 0u);  // read ahead, never run
-    __syncwarp();
-    // ordinals of the instructions that carry an ERC, in program order
+    // the program and, in program order, the ordinals of the instructions
+    // that carry an ERC
     int n_erc = 0;
-    for (int k0 = 0; k0 < L; k0 += 32) {
+    for (int k0 = 0; k0 <= L; k0 += 32) {
       const int k = k0 + lane;
-      const bool has = k < L && carries_erc<POW>(wprog[k].x & 0xffu);
+      bool has = false;
+      if (k <= L) {
+        const uint2 w = src[k];
+        wprog[k] = w;
+        if (k < L) {
+          const Aux ax = asrc[k];
+          waux[k] = ax;
+          const uint32_t opc = w.x & 0xffu;
+          has = carries_erc<POW>(opc);
+        }
+      }
       const unsigned m = __ballot_sync(0xffffffffu, has);
       if (has) {
         const int o = n_erc + __popc(m & ((1u << lane) - 1u));
+        const uint32_t opc = wprog[k].x & 0xffu;
         eord[k] = (uint16_t)o;
-        ek[o] = (uint16_t)k;
+        ek[o] = (opc == I_LDC0 || opc == I_PSC) ? waux[k].tpos : waux[k].tpos_fused;
+        wg[o] = make_float2(0.f, 0.f);
       }
       n_erc += __popc(m);
     }
     __syncwarp();
 
-    const int r_beg = chunk * p.chunk_rows;
-    const int r_end = min(p.N, r_beg + p.chunk_rows);
+    const int r_beg = chunk * ch.chunk_rows;
+    const int r_end = min(p.N, r_beg + ch.chunk_rows);
     for (int rb = r_beg; rb < r_end; rb += SLOT) {
       // this lane's first row, kept in bounds (and R-aligned) past the end
       const int row0 = min(rb + lane * R, (r_end - 1) & ~(R - 1));
@@ -220,42 +272,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
       float A[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = 0.f;
-      if constexpr (FAST) {
-        for (int f = 0; f < p.F; ++f) {
-          float v[R];
-          load_rows<R>(p.X + (size_t)f * p.ldx + row0, v);
-          store_rows<R>(xt + (size_t)f * SLOT + lane * R, v);
-        }
-        __syncwarp();
-        run_program_tape<R, POW>(sprog, xt + lane * R, A, stk, V);
-      } else {
-        run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
-      }
-      float yc[R], yl[R];
+      run_program<R, true, false, POW>(wprog, L, p.X + row0, p.ldx, A, stk, V);
+      float yc[R], yl[R], w[R];
       load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
       load_rows<R>(p.ylo + row0, yl);
-      float w[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        // the residual a* + b* f - y (smse) or f - y (mse) in double-float:
-        // TwoProd / TwoSum keep the rounding of every term, so only f's own
-        // FP32 error remains (y = mean(y) + yc + yl exactly to FP64 accuracy)
-        float s, e1, e2, t, lo;
-        if (p.mse_mode) {
-          two_sum(A[r], -yb_hi, s, e1);
-          lo = -yb_lo;
-        } else {
-          const float pr = __fmul_rn(b_hi, A[r]);  // never contracted into an FMA
-          lo = fmaf(b_hi, A[r], -pr) + fmaf(b_lo, A[r], a_lo);
-          two_sum(a_hi, pr, s, e1);
-        }
-        two_sum(s, -yc[r], t, e2);
-        const float res = t + ((e1 + e2) + (lo - yl[r]));
-        w[r] = two_n * (p.mse_mode ? res : b_hi * res);
-        w[r] = valid[r] ? w[r] : 0.f;
-      }
+      seed_rows<R>(p, ab, A, yc, yl, valid, w);
       store_rows<R>(V + (size_t)SLOT * (L - 1), w);  // the output's value becomes its adjoint
-      __syncwarp();
       for (int k = L - 1; k >= 0; --k) {
         const uint2 ins = wprog[k];
         const Aux ax = waux[k];
@@ -332,48 +354,320 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p) {
           for (int r = 0; r < R; ++r) sm += valid[r] ? ge[r] : 0.f;
           part[(size_t)eord[k] * 33 + lane] = sm;
         }
-        __syncwarp();
-      }
-      // the pass's ERC sums: lane o adds up the 32 lane partials of the ERCs
-      // o, o + 32, ... (rows padded to 33 floats: no bank conflicts) into
-      // its error-free accumulators (one transposed reduction per pass
-      // instead of a shuffle reduction per ERC instruction)
-      for (int o = lane; o < n_erc; o += 32) {
-        const float* q = part + (size_t)o * 33;
-        float sm = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) sm += q[j];
-        float2 acc = wg[o];
-        acc_add(acc.x, acc.y, sm);
-        wg[o] = acc;
       }
       __syncwarp();
+      reduce_erc(part, wg, n_erc, lane);
+      __syncwarp();
     }
-    __syncwarp();
-    for (int o = lane; o < n_erc; o += 32) {
-      const int k = ek[o];
-      const uint32_t opc = wprog[k].x & 0xffu;
-      const int tp = (opc == I_LDC0 || opc == I_PSC) ? waux[k].tpos : waux[k].tpos_fused;
-      const double gk = (double)wg[o].x + (double)wg[o].y;
-      if (tp != NONE16 && gk != 0.0) atomicAdd(p.gacc + (size_t)trial * p.stride + tp, gk);
-    }
+    write_grad(p, trial, wg, ek, n_erc, lane);
     __syncwarp();
   }
 }
 
-const void* adj_ptr(int rows, bool pow, bool fast) {
-  switch (rows) {
-    case 4:
-      if (fast)
-        return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true, true>)
-                   : reinterpret_cast<const void*>(&adjoint_kernel<4, false, true>);
-      return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true, false>)
-                 : reinterpret_cast<const void*>(&adjoint_kernel<4, false, false>);
-    case 2: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<2, true, false>)
-                       : reinterpret_cast<const void*>(&adjoint_kernel<2, false, false>);
-    default: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<1, true, false>)
-                        : reinterpret_cast<const void*>(&adjoint_kernel<1, false, false>);
+// ---- the staged kernel: 4 rows per lane, feature tile in shared memory ----
+
+// The forward half as the PTX interpreter with a value tape: the
+// instruction the PTX leaves is run and taped here.
+template <int R, bool POW>
+__device__ __forceinline__ void run_program_tape(const uint2* prog, const float* xs,
+                                                 float (&A)[R], float* stk, float* tape) {
+  uint32_t pc = smem_u32(prog), sp = smem_u32(stk), code = 0, arg = 0, tp = smem_u32(tape);
+  const uint32_t xb = smem_u32(xs);
+  for (;;) {
+    interp_tape_asm<R>(A, pc, sp, xb, code, arg, tp);
+    if (code == I_NOP || code >= I_COUNT) break;
+    exec_cold<R, POW>(code, arg, A, sp, xs);
+    store_rows<R>(static_cast<float*>(__cvta_shared_to_generic(tp)), A);
+    tp += 32 * R * 4;
   }
 }
+
+// Reverse-sweep descriptors.  Only the instructions with work appear (a
+// feature load propagates nothing).  x = form | ERC ordinal << 8 |
+// instruction << 20; y = byte offset of the V operand (a binary node over
+// two subtrees: the left one); z = byte offset of the second operand (the
+// right subtree's V entry, or the feature's row in the tile); w = the
+// constant's bits.
+enum : uint32_t {
+  RV_CONST = 0,       // a pushed ERC: its adjoint is the ERC's contribution
+  RV_UN = 1,          // + u (1..8)
+  RV_BIN = 9,         // + group * 6 + kind, group 0 BF, 1 BC, 2 LF, 3 LC, 4 BS/RS
+  RV_COUNT = 39
+};
+
+// x <- g * d u(x) / dx: the forward kernels' own FP32 forms (the gradient
+// is checked to 1e-3, far above their few-ulp error).
+template <int R, int U>
+__device__ __forceinline__ void rev_un(const float (&g)[R], float* px) {
+  float x[R];
+  load_rows<R>(px, x);
+  if constexpr (U == U_SIN || U == U_COS) {
+    sincos_rows<R>(x, U == U_SIN ? 1 : 0);  // sin' = cos, cos' = -sin
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = U == U_SIN ? g[r] * x[r] : -(g[r] * x[r]);
+  } else if constexpr (U == U_EXP) {
+    exp_rows<R>(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = g[r] * x[r];
+  } else if constexpr (U == U_LOG_ABS || U == U_LOG) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = g[r] * __frcp_rn(x[r]);
+  } else if constexpr (U == U_SQRT_ABS) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      x[r] = x[r] == 0.f ? 0.f : g[r] * copysignf(0.5f * rsqrt_approx(fabsf(x[r])), x[r]);
+  } else if constexpr (U == U_SQUARE) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = g[r] * (2.f * x[r]);
+  } else {  // U_SQRT
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = g[r] * (0.5f * rsqrt_approx(x[r]));
+  }
+  store_rows<R>(px, x);
+}
+
+// A binary node kind(a, b) of group G: the adjoints of its subtree
+// operands, and (BC / LC) its ERC's contribution summed over the lane's
+// valid rows into part[ordinal][lane].
+template <int R, int G, int K>
+__device__ __forceinline__ void rev_bin(const float (&g)[R], unsigned char* vl,
+                                        const unsigned char* xl, const uint4 d, float* partl,
+                                        const bool (&valid)[R]) {
+  float* pv = reinterpret_cast<float*>(vl + d.y);
+  const float c = __uint_as_float(d.w);
+  float a[R], b[R], da[R], db[R];
+  if constexpr (G == 0 || G == 1 || G == 4) load_rows<R>(pv, a);
+  if constexpr (G == 2) load_rows<R>(reinterpret_cast<const float*>(xl + d.z), a);
+  if constexpr (G == 2 || G == 3) load_rows<R>(pv, b);
+  if constexpr (G == 0) load_rows<R>(reinterpret_cast<const float*>(xl + d.z), b);
+  if constexpr (G == 4) load_rows<R>(reinterpret_cast<const float*>(vl + d.z), b);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if constexpr (G == 3) a[r] = c;
+    if constexpr (G == 1) b[r] = c;
+  }
+  dbin_rows<R>(K, a, b, da, db);
+  float o[R];
+  if constexpr (G == 2 || G == 3) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = g[r] * db[r];
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = g[r] * da[r];
+  }
+  store_rows<R>(pv, o);
+  if constexpr (G == 4) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = g[r] * db[r];
+    store_rows<R>(reinterpret_cast<float*>(vl + d.z), o);
+  }
+  if constexpr (G == 1 || G == 3) {
+    float sm = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] * (G == 1 ? db[r] : da[r]) : 0.f;
+    partl[(size_t)((d.x >> 8) & 0xfffu) * 33] = sm;
+  }
+}
+
+// The staged kernel (at most ADJ_FTILE_MAX features): per pass the lanes'
+// rows of every feature go to a shared-memory tile, the forward recompute
+// is the PTX interpreter with a value tape, and the reverse sweep walks
+// precomputed descriptors (one dense switch per instruction, operands at
+// precomputed offsets, feature operands from the tile).  Everything a lane
+// touches during the sweep is its own, so the sweep needs no warp barrier.
+template <bool POW>
+__global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
+  constexpr int R = 4;
+  constexpr int SLOT = 32 * R;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const AdjLayout lay = adj_layout(p.lcap, p.ecap, p.slots, R, true, p.F);
+  unsigned char* base = smem + (size_t)warp * lay.total;
+  uint2* sprog = reinterpret_cast<uint2*>(base + lay.prog);
+  uint4* rins = reinterpret_cast<uint4*>(base + lay.rins);
+  float2* wg = reinterpret_cast<float2*>(base + lay.wg);
+  uint16_t* ek = reinterpret_cast<uint16_t*>(base + lay.ek);
+  unsigned char* vl = base + lay.V + (size_t)lane * R * 4;  // this lane's V, byte-addressed
+  float* V = reinterpret_cast<float*>(vl);
+  float* stk = reinterpret_cast<float*>(base + lay.stk) + lane * R;
+  float* part = reinterpret_cast<float*>(base + lay.part);
+  float* partl = part + lane;
+  float* xt = reinterpret_cast<float*>(base + lay.xt) + lane * R;
+  const unsigned char* xl = reinterpret_cast<const unsigned char*>(xt);
+  const Chunking ch = chunking(p, *p.count, SLOT);
+
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(p.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= ch.n_items) break;
+    const int trial = p.list[item / ch.n_chunks];
+    const int chunk = item % ch.n_chunks;
+    if (adj_skip(p, trial)) continue;
+    const int L = p.len[trial];
+    const double* ab = p.ab + 4 * (size_t)trial;
+    const uint2* src = p.prog + (size_t)trial * p.lstride;
+    const Aux* asrc = p.aux + (size_t)trial * p.lstride;
+    // stage: the interpreter's form of the program, and in program order
+    // the ERC ordinals and the reverse descriptors of the instructions
+    // with work
+    int n_erc = 0, n_rev = 0;
+    for (int k0 = 0; k0 <= L; k0 += 32) {
+      const int k = k0 + lane;
+      bool has = false, work = false;
+      uint4 d = make_uint4(0u, 0u, 0u, 0u);
+      uint16_t tpos = NONE16;
+      if (k <= L) {
+        const uint2 w = src[k];
+        const uint32_t opc = w.x & 0xffu;
+        const uint32_t f = w.x >> 8;
+        sprog[k] = make_uint2(opc, reads_feature(opc) ? f * (uint32_t)(SLOT * 4) : w.y);
+        if (k < L) {
+          const Aux ax = asrc[k];
+          has = carries_erc<POW>(opc);
+          tpos = (opc == I_LDC0 || opc == I_PSC) ? ax.tpos : ax.tpos_fused;
+          const uint32_t sl = (uint32_t)ax.src_l * (SLOT * 4), sr = (uint32_t)ax.src_r * (SLOT * 4);
+          const uint32_t fo = f * (uint32_t)(SLOT * 4);
+          uint32_t rop = RV_COUNT;
+          if (opc == I_LDC0 || opc == I_PSC) {
+            rop = RV_CONST;
+          } else if (opc >= I_UN && opc < I_UN + NUNARY) {
+            rop = RV_UN + (opc - I_UN);
+            d.y = sl;
+          } else if ((opc >= I_BF && opc < I_BS) || (POW && opc >= I_PW && opc < I_PWS)) {
+            const bool pw = POW && opc >= I_PW;
+            const uint32_t grp = pw ? opc - I_PW : (opc - I_BF) / NKIND;
+            const uint32_t kind = pw ? (uint32_t)K_POW : (opc - I_BF) % NKIND;
+            rop = RV_BIN + grp * 6 + kind;
+            d.y = grp <= 1 ? sl : sr;
+            d.z = (grp == 0 || grp == 2) ? fo : 0u;
+            d.w = w.y;
+          } else if ((opc >= I_BS && opc < I_NOP) || (POW && opc >= I_PWS && opc < I_COUNT)) {
+            const uint32_t kind =
+                POW && opc >= I_PWS ? (uint32_t)K_POW : opc - (opc < I_RS ? I_BS : I_RS);
+            rop = RV_BIN + 4 * 6 + kind;
+            d.y = sl;
+            d.z = sr;
+          }
+          work = rop != RV_COUNT;
+          d.x = rop | ((uint32_t)k << 20);
+        }
+      }
+      const unsigned me = __ballot_sync(0xffffffffu, has);
+      const unsigned mw = __ballot_sync(0xffffffffu, work);
+      const unsigned below = (1u << lane) - 1u;
+      if (has) {
+        const int o = n_erc + __popc(me & below);
+        ek[o] = tpos;
+        wg[o] = make_float2(0.f, 0.f);
+        d.x |= (uint32_t)o << 8;
+      }
+      if (work) rins[n_rev + __popc(mw & below)] = d;
+      n_erc += __popc(me);
+      n_rev += __popc(mw);
+    }
+    if (lane == 0) sprog[L + 1] = make_uint2(I_NOP, 0u);  // read ahead, never run
+    __syncwarp();
+
+    const int r_beg = chunk * ch.chunk_rows;
+    const int r_end = min(p.N, r_beg + ch.chunk_rows);
+    for (int rb = r_beg; rb < r_end; rb += SLOT) {
+      const int row0 = min(rb + lane * R, (r_end - 1) & ~(R - 1));
+      bool valid[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) valid[r] = rb + lane * R + r < r_end;
+      for (int f = 0; f < p.F; ++f) {
+        float v[R];
+        load_rows<R>(p.X + (size_t)f * p.ldx + row0, v);
+        store_rows<R>(xt + (size_t)f * SLOT, v);
+      }
+      float yc[R], yl[R], w[R];
+      load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
+      load_rows<R>(p.ylo + row0, yl);
+      float A[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) A[r] = 0.f;
+      run_program_tape<R, POW>(sprog, xt, A, stk, V);
+      seed_rows<R>(p, ab, A, yc, yl, valid, w);
+      store_rows<R>(V + (size_t)SLOT * (L - 1), w);  // the output's value becomes its adjoint
+      uint4 dn = n_rev > 0 ? rins[n_rev - 1] : make_uint4(0u, 0u, 0u, 0u);
+      for (int j = n_rev - 1; j >= 0; --j) {
+        const uint4 d = dn;
+        if (j > 0) dn = rins[j - 1];
+        float g[R];
+        load_rows<R>(reinterpret_cast<const float*>(vl + (d.x >> 20) * (uint32_t)(SLOT * 4)), g);
+        float* pv = reinterpret_cast<float*>(vl + d.y);
+        switch (d.x & 0xffu) {
+          case RV_CONST: {
+            float sm = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] : 0.f;
+            partl[(size_t)((d.x >> 8) & 0xfffu) * 33] = sm;
+            break;
+          }
+#define GG_RV_UN(U) \
+  case RV_UN + U: rev_un<R, U>(g, pv); break;
+          GG_RV_UN(U_SIN) GG_RV_UN(U_COS) GG_RV_UN(U_EXP) GG_RV_UN(U_LOG_ABS)
+          GG_RV_UN(U_SQRT_ABS) GG_RV_UN(U_SQUARE) GG_RV_UN(U_LOG) GG_RV_UN(U_SQRT)
+#undef GG_RV_UN
+#define GG_RV_BIN(G, K) \
+  case RV_BIN + G * 6 + K: rev_bin<R, G, K>(g, vl, xl, d, partl, valid); break;
+#define GG_RV_GRP(G) \
+  GG_RV_BIN(G, K_ADD) GG_RV_BIN(G, K_SUB) GG_RV_BIN(G, K_MUL) GG_RV_BIN(G, K_AQ) GG_RV_BIN(G, K_DIV)
+          GG_RV_GRP(0) GG_RV_GRP(1) GG_RV_GRP(2) GG_RV_GRP(3) GG_RV_GRP(4)
+#undef GG_RV_GRP
+#undef GG_RV_BIN
+          default:
+            if constexpr (POW) {  // the pow forms
+              switch ((d.x & 0xffu) - RV_BIN) {
+                case 0 * 6 + K_POW: rev_bin<R, 0, K_POW>(g, vl, xl, d, partl, valid); break;
+                case 1 * 6 + K_POW: rev_bin<R, 1, K_POW>(g, vl, xl, d, partl, valid); break;
+                case 2 * 6 + K_POW: rev_bin<R, 2, K_POW>(g, vl, xl, d, partl, valid); break;
+                case 3 * 6 + K_POW: rev_bin<R, 3, K_POW>(g, vl, xl, d, partl, valid); break;
+                case 4 * 6 + K_POW: rev_bin<R, 4, K_POW>(g, vl, xl, d, partl, valid); break;
+                default: break;
+              }
+            }
+            break;
+        }
+      }
+      __syncwarp();
+      reduce_erc(part, wg, n_erc, lane);
+      __syncwarp();
+    }
+    write_grad(p, trial, wg, ek, n_erc, lane);
+    __syncwarp();
+  }
+}
+
+// Bins the trials of a batch by program length into the length classes.
+__global__ void __launch_bounds__(256) adj_bin_kernel(const AdjBinParams p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.P) return;
+  const int L = p.len[t];
+  if (L <= 0) return;
+  const double* ab = p.ab + 4 * (size_t)t;
+  if (ab[2] == 0.0 || (!p.mse_mode && ab[1] == 0.0)) return;
+  int c = 0;
+  while (c < p.ncls - 1 && L + 1 > p.caps[c]) ++c;
+  const int pos = atomicAdd(p.count + c, 1);
+  p.list[(size_t)c * p.P + pos] = t;
+}
+
+const void* adj_ptr(int rows, bool pow, bool fast) {
+  if (fast) return pow ? reinterpret_cast<const void*>(&adjoint_fast_kernel<true>)
+                       : reinterpret_cast<const void*>(&adjoint_fast_kernel<false>);
+  switch (rows) {
+    case 4: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<4, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<4, false>);
+    case 2: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<2, true>)
+                       : reinterpret_cast<const void*>(&adjoint_kernel<2, false>);
+    default: return pow ? reinterpret_cast<const void*>(&adjoint_kernel<1, true>)
+                        : reinterpret_cast<const void*>(&adjoint_kernel<1, false>);
+  }
+}
+
+const void* adj_bin_ptr() { return reinterpret_cast<const void*>(&adj_bin_kernel); }
 
 }  // namespace gg

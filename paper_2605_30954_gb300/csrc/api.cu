@@ -175,6 +175,8 @@ struct ggeval_dataset {
   size_t cap_gacc = 0;
   int* counters = nullptr;
   size_t cap_counters = 0;
+  int* adjbin = nullptr;  // adjoint: class counts and counters, then the class lists
+  size_t cap_adjbin = 0;
   int* idx = nullptr;  // masked evaluation: the compacted trial indices
   size_t cap_idx = 0;
   unsigned* status = nullptr;
@@ -339,6 +341,7 @@ ggeval_status ensure_ws(ggeval_dataset* ds, int n, const Plan& pl, bool grad) {
   if (grad) {
     GG_TRY(grow(ds->aux, ds->cap_aux, (size_t)n * pl.lstride));
     GG_TRY(grow(ds->gacc, ds->cap_gacc, (size_t)n * pl.stride));
+    GG_TRY(grow(ds->adjbin, ds->cap_adjbin, (size_t)gg::ADJ_NCLS_MAX * (2 + (size_t)n)));
   }
   return GGEVAL_OK;
 }
@@ -729,6 +732,7 @@ void ggeval_destroy(ggeval_dataset* ds) {
   cudaFree(ds->ab);
   cudaFree(ds->gacc);
   cudaFree(ds->counters);
+  cudaFree(ds->adjbin);
   cudaFree(ds->idx);
   cudaFree(ds->stage);
   for (auto& e : ds->prof_ev) {
@@ -934,86 +938,39 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
   float* dg = host ? reinterpret_cast<float*>(scratch) : dcval;
   float* ds_smse = smse ? (host ? dg + gcount : smse) : nullptr;
   GG_TRY(enqueue_eval(ds, db, b, pl, outs_of(ds_smse, nullptr, nullptr, nullptr), true, st));
-  // adjoint.  Each warp holds its own copy of the program, R rows x 32 lanes
-  // of values per instruction and its stack, so shared memory bounds the
-  // resident warps.  For each R (rows per lane) take the CTA size (1..8
-  // warps) that keeps the most warps resident per SM, the larger CTA on a
-  // tie; then the largest R that keeps at least 6 warps per SM (more rows
-  // share each instruction's decode; fewer warps hide less latency).
-  // Measured per gradient step: 1,024 x h5 over 50,000 rows 7.9 / 6.5 /
-  // 6.4 ms for R = 1 / 2 / 4 (21 / 12 / 6 warps per SM); 16,384 x h6 over
-  // 1,000,000 rows 2.20 / 1.78 / 1.90 s (10 / 6 / 3 warps).
-  const void* afn = nullptr;
-  int rows = 0, warps = 0, nb = 0;
-  int ftile = 0;  // > 0: the 4-row adjoint stages features and runs the PTX forward
-  for (int R : {4, 2, 1}) {
-    const int ft = (R == 4 && ds->F <= gg::ADJ_FTILE_MAX) ? ds->F : 0;
-    const void* fn = gg::adj_ptr(R, pl.pow, ft > 0);
-    GG_TRY(prepare_kernel(ds->device, fn));
-    int wR = 0, nR = 0;
-    const int wmax =
-        (int)((ds->smem_optin - 64) / gg::adj_warp_bytes(pl.lstride, pl.slots, R, ft));
-    for (int w = wmax < 8 ? wmax : 8; w >= 1; --w) {
-      int n = 0;
-      GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &n, fn, w * 32, gg::adj_smem_bytes(w, pl.lstride, pl.slots, R, ft)));
-      if (n * w > nR * wR) {
-        wR = w;
-        nR = n;
-      }
-    }
-    if (wR < 1 || nR < 1) continue;
-    if (!afn || nR * wR >= 6) {
-      afn = fn;
-      rows = R;
-      warps = wR;
-      nb = nR;
-      ftile = ft;
-      if (nR * wR >= 6) break;
-    }
-  }
-  if (!afn) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
-  const size_t asmem = gg::adj_smem_bytes(warps, pl.lstride, pl.slots, rows, ftile);
-  if (const char* env = getenv("GGEVAL_VERBOSE"))
-    if (env[0] == '1')
-      fprintf(stderr, "ggeval adjoint: %d rows per lane, %d warps per CTA, %d CTAs per SM\n", rows,
-              warps, nb);
-  const long long slots = (long long)nb * ds->sms * warps;
-  const int group = 32 * rows;  // rows per warp pass
-  long long n_chunks = (8 * slots + b->n - 1) / b->n;
-  const long long max_chunks = (ds->N + group - 1) / group;
-  if (n_chunks > max_chunks) n_chunks = max_chunks;
-  if (n_chunks < 1) n_chunks = 1;
-  int chunk_rows = (int)(((ds->N + n_chunks - 1) / n_chunks + group - 1) / group * group);
-  n_chunks = (ds->N + chunk_rows - 1) / chunk_rows;
-  gg::AdjParams ap{};
-  ap.X = ds->X;
-  ap.ylo = ds->ylo;
-  ap.N = (int)ds->N;
-  ap.F = ds->F;
-  ap.ldx = ds->ldx;
-  ap.prog = ds->prog;
-  ap.aux = ds->aux;
-  ap.len = ds->len;
-  ap.lstride = pl.lstride;
-  ap.P = b->n;
-  ap.stride = pl.stride;
-  ap.slots = pl.slots;
-  ap.ab = ds->ab;
-  ap.mse_mode = (flags & GGEVAL_F_GRAD_MSE) ? 1 : 0;
-  ap.ybar = ds->ybar;
-  ap.chunk_rows = chunk_rows;
-  ap.n_chunks = (int)n_chunks;
-  if ((long long)b->n * n_chunks > (1ll << 31) - 1) return fail(GGEVAL_ERR_UNSUPPORTED, "too many items");
-  ap.n_items = (int)(b->n * n_chunks);
-  ap.counter = ds->counters + 1;
-  ap.gacc = ds->gacc;
-  GG_CU(cudaMemsetAsync(ds->counters + 1, 0, sizeof(int), st));
+  // adjoint, one launch per length class (programs of at most cap - 1
+  // instructions).  Each warp holds its own copy of the program, R rows x
+  // 32 lanes of values per instruction and its stack, so shared memory
+  // bounds the resident warps.  For each R (rows per lane) take the CTA
+  // size (1..8 warps) that keeps the most warps resident per SM, the larger
+  // CTA on a tie; then the largest R that keeps at least 6 warps per SM
+  // (more rows share each instruction's decode; fewer warps hide less
+  // latency).  With at most ADJ_FTILE_MAX features, R = 4 is the staged
+  // kernel.  GGEVAL_ADJ_ROWS (1, 2 or 4) fixes R.
+  int caps[gg::ADJ_NCLS_MAX];
+  int ncls = 0;
+  for (int c : gg::ADJ_CAPS)
+    if (c < pl.lstride && ncls < gg::ADJ_NCLS_MAX - 1) caps[ncls++] = c;
+  caps[ncls++] = pl.lstride;
+  int* cls_count = ds->adjbin;
+  int* cls_counter = ds->adjbin + gg::ADJ_NCLS_MAX;
+  int* cls_list = ds->adjbin + 2 * gg::ADJ_NCLS_MAX;
+  GG_CU(cudaMemsetAsync(ds->adjbin, 0, sizeof(int) * 2 * gg::ADJ_NCLS_MAX, st));
   GG_CU(cudaMemsetAsync(ds->gacc, 0, gcount * 8, st));
-  long long agrid = (long long)nb * ds->sms;
-  const long long need_blocks = (ap.n_items + warps - 1) / warps;
-  if (agrid > need_blocks) agrid = need_blocks;
-  // GGEVAL_F_PROFILE: CUDA events around the adjoint kernel (read with
+  const int mse_mode = (flags & GGEVAL_F_GRAD_MSE) ? 1 : 0;
+  gg::AdjBinParams bp{};
+  bp.len = ds->len;
+  bp.ab = ds->ab;
+  bp.P = b->n;
+  bp.mse_mode = mse_mode;
+  bp.ncls = ncls;
+  for (int c = 0; c < ncls; ++c) bp.caps[c] = caps[c];
+  bp.count = cls_count;
+  bp.list = cls_list;
+  int force_rows = 0;
+  if (const char* env = getenv("GGEVAL_ADJ_ROWS")) force_rows = atoi(env);
+  const bool verbose = getenv("GGEVAL_VERBOSE") && getenv("GGEVAL_VERBOSE")[0] == '1';
+  // GGEVAL_F_PROFILE: CUDA events around the adjoint's launches (read with
   // ggeval_profile_read, as the forward kernel's)
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if ((flags & GGEVAL_F_PROFILE) && !host && ds->prof_used < PROF_MAX) {
@@ -1026,7 +983,74 @@ ggeval_status ggeval_grad_batch(ggeval_dataset* ds, const ggeval_batch* b, uint3
     ev = &ds->prof_ev[ds->prof_used++];
     GG_CU(cudaEventRecord(ev->first, st));
   }
-  GG_TRY(launch(afn, dim3((unsigned)agrid), dim3(warps * 32), asmem, st, &ap));
+  GG_TRY(launch(gg::adj_bin_ptr(), dim3((unsigned)((b->n + 255) / 256)), dim3(256), 0, st, &bp));
+  for (int c = 0; c < ncls; ++c) {
+    const int lcap = caps[c];
+    const int ecap = lcap < pl.lstride / 2 ? lcap : pl.lstride / 2;
+    const void* afn = nullptr;
+    int rows = 0, warps = 0, nb = 0;
+    bool fast = false;
+    gg::AdjLayout lay{};
+    for (int R : {4, 2, 1}) {
+      if (force_rows && R != force_rows) continue;
+      const bool fs = R == 4 && ds->F <= gg::ADJ_FTILE_MAX;
+      const void* fn = gg::adj_ptr(R, pl.pow, fs);
+      GG_TRY(prepare_kernel(ds->device, fn));
+      const gg::AdjLayout l = gg::adj_layout(lcap, ecap, pl.slots, R, fs, ds->F);
+      int wR = 0, nR = 0;
+      const int wmax = (int)((ds->smem_optin - 64) / l.total);
+      for (int w = wmax < 8 ? wmax : 8; w >= 1; --w) {
+        int n = 0;
+        GG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, w * 32,
+                                                            gg::adj_smem_bytes(w, l)));
+        if (n * w > nR * wR) {
+          wR = w;
+          nR = n;
+        }
+      }
+      if (wR < 1 || nR < 1) continue;
+      if (!afn || nR * wR >= 6) {
+        afn = fn;
+        rows = R;
+        warps = wR;
+        nb = nR;
+        fast = fs;
+        lay = l;
+        if (nR * wR >= 6) break;
+      }
+    }
+    if (!afn) return fail(GGEVAL_ERR_UNSUPPORTED, "template too large for the adjoint");
+    if (verbose)
+      fprintf(stderr, "ggeval adjoint class %d (cap %d): %d rows per lane%s, %d warps per CTA, "
+              "%d CTAs per SM\n", c, lcap, rows, fast ? " (staged)" : "", warps, nb);
+    gg::AdjParams ap{};
+    ap.X = ds->X;
+    ap.ylo = ds->ylo;
+    ap.N = (int)ds->N;
+    ap.F = ds->F;
+    ap.ldx = ds->ldx;
+    ap.prog = ds->prog;
+    ap.aux = ds->aux;
+    ap.len = ds->len;
+    ap.lstride = pl.lstride;
+    ap.P = b->n;
+    ap.stride = pl.stride;
+    ap.lcap = lcap;
+    ap.ecap = ecap;
+    ap.slots = pl.slots;
+    ap.ab = ds->ab;
+    ap.mse_mode = mse_mode;
+    ap.ybar = ds->ybar;
+    ap.list = cls_list + (size_t)c * b->n;
+    ap.count = cls_count + c;
+    const long long slots = (long long)nb * ds->sms * warps;
+    ap.target_items = (int)(8 * slots);
+    ap.counter = cls_counter + c;
+    ap.gacc = ds->gacc;
+    const long long agrid = (long long)nb * ds->sms;
+    GG_TRY(launch(afn, dim3((unsigned)agrid), dim3(warps * 32), gg::adj_smem_bytes(warps, lay), st,
+                  &ap));
+  }
   if (ev) GG_CU(cudaEventRecord(ev->second, st));
   gg::GradOutParams gp{ds->gacc, ds->len, b->n, pl.stride, dg};
   GG_TRY(launch(gg::gradout_ptr(), dim3((unsigned)((gcount + 255) / 256)), dim3(256), 0, st, &gp));
