@@ -49,7 +49,7 @@ __device__ __forceinline__ void dbin_rows(int kind, const float (&a)[R], const f
     case K_AQ:
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float q = rsqrtf(fmaf(b[r], b[r], 1.f));
+        const float q = rsqrt_approx(fmaf(b[r], b[r], 1.f));
         da[r] = q;
         db[r] = -a[r] * b[r] * q * q * q;
       }
@@ -382,103 +382,160 @@ __device__ __forceinline__ void run_program_tape(const uint2* prog, const float*
   }
 }
 
-// Reverse-sweep descriptors.  Only the instructions with work appear (a
-// feature load propagates nothing).  x = form | ERC ordinal << 8 |
-// instruction << 20; y = byte offset of the V operand (a binary node over
-// two subtrees: the left one); z = byte offset of the second operand (the
-// right subtree's V entry, or the feature's row in the tile); w = the
-// constant's bits.
+// Reverse sweep of the staged kernel.  The accumulator discipline of the
+// programs gives the sweep its shape: an instruction that reads A reads the
+// value of the instruction just before it, so the adjoint of instruction
+// k - 1 is produced by instruction k and is the next one the sweep needs.
+// It stays in registers (G).  Only a value that was pushed (the instruction
+// after it is PSF or PSC) is consumed later by a pop; its adjoint goes
+// through V, and the descriptor says so (GSM).  A value has one consumer,
+// so the operand values of the next instruction are never written by the
+// current one: the sweep loads them one instruction ahead.
+//
+// Descriptors (only the instructions with work: a feature load propagates
+// nothing): x = form | GSM | ERC ordinal << 7 | instruction << 16; y, z =
+// byte offsets from the warp's shared-memory base of the two operand rows
+// the form reads (a V entry or the feature's row in the tile; unused ones
+// point at V's first entry); w = the constant's bits.  The PTX sweep
+// (interp_rev_asm, generated by interp_gen.py) runs the forms of +, -, *,
+// AQ, the pushed ERC, square, log and sqrt; rev_cold runs every form (the
+// PTX leaves it sin, cos, exp, division and pow).
 enum : uint32_t {
   RV_CONST = 0,       // a pushed ERC: its adjoint is the ERC's contribution
   RV_UN = 1,          // + u (1..8)
-  RV_BIN = 9,         // + group * 6 + kind, group 0 BF, 1 BC, 2 LF, 3 LC, 4 BS/RS
-  RV_COUNT = 39
+  RV_BIN = 9,         // + group * 6 + kind: group 0 BF, 1 BC, 2 LF, 3 LC, 4 BS, 5 RS
+  RV_COUNT = 45,
+  RV_GSM = 64
 };
 
-// x <- g * d u(x) / dx: the forward kernels' own FP32 forms (the gradient
+// G <- g * d u(x) / dx: the forward kernels' own FP32 forms (the gradient
 // is checked to 1e-3, far above their few-ulp error).
 template <int R, int U>
-__device__ __forceinline__ void rev_un(const float (&g)[R], float* px) {
+__device__ __forceinline__ void rev_un(const float (&g)[R], const float (&xv)[R], float (&G)[R]) {
   float x[R];
-  load_rows<R>(px, x);
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = xv[r];
   if constexpr (U == U_SIN || U == U_COS) {
     sincos_rows<R>(x, U == U_SIN ? 1 : 0);  // sin' = cos, cos' = -sin
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = U == U_SIN ? g[r] * x[r] : -(g[r] * x[r]);
+    for (int r = 0; r < R; ++r) G[r] = U == U_SIN ? g[r] * x[r] : -(g[r] * x[r]);
   } else if constexpr (U == U_EXP) {
     exp_rows<R>(x);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = g[r] * x[r];
+    for (int r = 0; r < R; ++r) G[r] = g[r] * x[r];
   } else if constexpr (U == U_LOG_ABS || U == U_LOG) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = g[r] * __frcp_rn(x[r]);
+    for (int r = 0; r < R; ++r) G[r] = g[r] * __frcp_rn(x[r]);
   } else if constexpr (U == U_SQRT_ABS) {
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      x[r] = x[r] == 0.f ? 0.f : g[r] * copysignf(0.5f * rsqrt_approx(fabsf(x[r])), x[r]);
+      G[r] = x[r] == 0.f ? 0.f : g[r] * copysignf(0.5f * rsqrt_approx(fabsf(x[r])), x[r]);
   } else if constexpr (U == U_SQUARE) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = g[r] * (2.f * x[r]);
+    for (int r = 0; r < R; ++r) G[r] = g[r] * (2.f * x[r]);
   } else {  // U_SQRT
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = g[r] * (0.5f * rsqrt_approx(x[r]));
+    for (int r = 0; r < R; ++r) G[r] = g[r] * (0.5f * rsqrt_approx(x[r]));
   }
-  store_rows<R>(px, x);
 }
 
-// A binary node kind(a, b) of group G: the adjoints of its subtree
-// operands, and (BC / LC) its ERC's contribution summed over the lane's
-// valid rows into part[ordinal][lane].
-template <int R, int G, int K>
-__device__ __forceinline__ void rev_bin(const float (&g)[R], unsigned char* vl,
-                                        const unsigned char* xl, const uint4 d, float* partl,
-                                        const bool (&valid)[R]) {
-  float* pv = reinterpret_cast<float*>(vl + d.y);
+// A binary node kind(a, b) of group GR with operand rows u (at y) and v (at
+// z): G <- the adjoint of its A operand; a popped operand's adjoint goes to
+// its V entry; (BC / LC) its ERC's contribution summed over the lane's valid
+// rows goes to *pe.
+template <int R, int GR, int K>
+__device__ __forceinline__ void rev_bin(const float (&g)[R], const float (&u)[R],
+                                        const float (&v)[R], unsigned char* wl, const uint4 d,
+                                        float* pe, const bool (&valid)[R], float (&G)[R]) {
   const float c = __uint_as_float(d.w);
   float a[R], b[R], da[R], db[R];
-  if constexpr (G == 0 || G == 1 || G == 4) load_rows<R>(pv, a);
-  if constexpr (G == 2) load_rows<R>(reinterpret_cast<const float*>(xl + d.z), a);
-  if constexpr (G == 2 || G == 3) load_rows<R>(pv, b);
-  if constexpr (G == 0) load_rows<R>(reinterpret_cast<const float*>(xl + d.z), b);
-  if constexpr (G == 4) load_rows<R>(reinterpret_cast<const float*>(vl + d.z), b);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    if constexpr (G == 3) a[r] = c;
-    if constexpr (G == 1) b[r] = c;
+    // BF: (A, x)  BC: (A, c)  LF: (x, A)  LC: (c, A)  BS: (pop, A)  RS: (A, pop)
+    a[r] = GR == 2 ? v[r] : GR == 3 ? c : u[r];
+    b[r] = GR == 0 || GR == 4 || GR == 5 ? v[r] : GR == 1 ? c : u[r];
   }
   dbin_rows<R>(K, a, b, da, db);
-  float o[R];
-  if constexpr (G == 2 || G == 3) {
+  constexpr bool a_is_A = GR == 0 || GR == 1 || GR == 5;
 #pragma unroll
-    for (int r = 0; r < R; ++r) o[r] = g[r] * db[r];
-  } else {
+  for (int r = 0; r < R; ++r) G[r] = g[r] * (a_is_A ? da[r] : db[r]);
+  if constexpr (GR == 4 || GR == 5) {  // the popped operand
+    float o[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) o[r] = g[r] * da[r];
+    for (int r = 0; r < R; ++r) o[r] = g[r] * (GR == 4 ? da[r] : db[r]);
+    store_rows<R>(reinterpret_cast<float*>(wl + (GR == 4 ? d.y : d.z)), o);
   }
-  store_rows<R>(pv, o);
-  if constexpr (G == 4) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) o[r] = g[r] * db[r];
-    store_rows<R>(reinterpret_cast<float*>(vl + d.z), o);
-  }
-  if constexpr (G == 1 || G == 3) {
+  if constexpr (GR == 1 || GR == 3) {
     float sm = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] * (G == 1 ? db[r] : da[r]) : 0.f;
-    partl[(size_t)((d.x >> 8) & 0xfffu) * 33] = sm;
+    for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] * (GR == 1 ? db[r] : da[r]) : 0.f;
+    *pe = sm;
+  }
+}
+
+// One descriptor in C++: every form (the PTX sweep leaves it the forms it
+// does not run).  g is the carried adjoint G, or V's entry (GSM).
+template <bool POW>
+__device__ __noinline__ void rev_cold(const uint4 d, float (&G)[4], unsigned char* wl,
+                                      const float* V, float* pel, const bool (&valid)[4]) {
+  constexpr int R = 4;
+  float g[R], u[R], v[R];
+  if (d.x & RV_GSM) {
+    load_rows<R>(V + (size_t)(d.x >> 16) * 32 * R, g);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) g[r] = G[r];
+  }
+  load_rows<R>(reinterpret_cast<const float*>(wl + d.y), u);
+  load_rows<R>(reinterpret_cast<const float*>(wl + d.z), v);
+  float* pe = pel + (size_t)((d.x >> 7) & 0x1ffu) * 33;
+  switch (d.x & 0x3fu) {
+    case RV_CONST: {
+      float sm = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] : 0.f;
+      *pe = sm;
+      break;
+    }
+#define GG_RV_UN(U) \
+  case RV_UN + U: rev_un<R, U>(g, u, G); break;
+    GG_RV_UN(U_SIN) GG_RV_UN(U_COS) GG_RV_UN(U_EXP) GG_RV_UN(U_LOG_ABS)
+    GG_RV_UN(U_SQRT_ABS) GG_RV_UN(U_SQUARE) GG_RV_UN(U_LOG) GG_RV_UN(U_SQRT)
+#undef GG_RV_UN
+#define GG_RV_BIN(GR, K) \
+  case RV_BIN + GR * 6 + K: rev_bin<R, GR, K>(g, u, v, wl, d, pe, valid, G); break;
+#define GG_RV_GRP(GR) \
+  GG_RV_BIN(GR, K_ADD) GG_RV_BIN(GR, K_SUB) GG_RV_BIN(GR, K_MUL) GG_RV_BIN(GR, K_AQ) \
+  GG_RV_BIN(GR, K_DIV)
+    GG_RV_GRP(0) GG_RV_GRP(1) GG_RV_GRP(2) GG_RV_GRP(3) GG_RV_GRP(4) GG_RV_GRP(5)
+#undef GG_RV_GRP
+#undef GG_RV_BIN
+    default:
+      if constexpr (POW) {  // the pow forms
+        switch ((d.x & 0x3fu) - RV_BIN) {
+          case 0 * 6 + K_POW: rev_bin<R, 0, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          case 1 * 6 + K_POW: rev_bin<R, 1, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          case 2 * 6 + K_POW: rev_bin<R, 2, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          case 3 * 6 + K_POW: rev_bin<R, 3, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          case 4 * 6 + K_POW: rev_bin<R, 4, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          case 5 * 6 + K_POW: rev_bin<R, 5, K_POW>(g, u, v, wl, d, pe, valid, G); break;
+          default: break;
+        }
+      }
+      break;
   }
 }
 
 // The staged kernel (at most ADJ_FTILE_MAX features): per pass the lanes'
 // rows of every feature go to a shared-memory tile, the forward recompute
 // is the PTX interpreter with a value tape, and the reverse sweep walks
-// precomputed descriptors (one dense switch per instruction, operands at
-// precomputed offsets, feature operands from the tile).  Everything a lane
-// touches during the sweep is its own, so the sweep needs no warp barrier.
+// precomputed descriptors.  Everything a lane touches during the sweep is
+// its own, so the sweep needs no warp barrier.
 template <bool POW>
 __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
   constexpr int R = 4;
   constexpr int SLOT = 32 * R;
+  constexpr uint32_t SLOTB = SLOT * 4;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -488,13 +545,14 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
   uint4* rins = reinterpret_cast<uint4*>(base + lay.rins);
   float2* wg = reinterpret_cast<float2*>(base + lay.wg);
   uint16_t* ek = reinterpret_cast<uint16_t*>(base + lay.ek);
-  unsigned char* vl = base + lay.V + (size_t)lane * R * 4;  // this lane's V, byte-addressed
-  float* V = reinterpret_cast<float*>(vl);
-  float* stk = reinterpret_cast<float*>(base + lay.stk) + lane * R;
+  unsigned char* wl = base + (size_t)lane * R * 4;  // the warp's base + this lane's row offset
+  float* V = reinterpret_cast<float*>(wl + lay.V);
+  float* stk = reinterpret_cast<float*>(wl + lay.stk);
   float* part = reinterpret_cast<float*>(base + lay.part);
   float* partl = part + lane;
-  float* xt = reinterpret_cast<float*>(base + lay.xt) + lane * R;
-  const unsigned char* xl = reinterpret_cast<const unsigned char*>(xt);
+  float* xt = reinterpret_cast<float*>(wl + lay.xt);
+  const uint32_t oV = (uint32_t)lay.V, oX = (uint32_t)lay.xt;
+  const uint32_t wl32 = smem_u32(wl), pe32 = smem_u32(partl), rbase = smem_u32(rins);
   const Chunking ch = chunking(p, *p.count, SLOT);
 
   for (;;) {
@@ -510,25 +568,25 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
     const uint2* src = p.prog + (size_t)trial * p.lstride;
     const Aux* asrc = p.aux + (size_t)trial * p.lstride;
     // stage: the interpreter's form of the program, and in program order
-    // the ERC ordinals and the reverse descriptors of the instructions
-    // with work
+    // the ERC ordinals and the descriptors of the instructions with work
     int n_erc = 0, n_rev = 0;
     for (int k0 = 0; k0 <= L; k0 += 32) {
       const int k = k0 + lane;
       bool has = false, work = false;
-      uint4 d = make_uint4(0u, 0u, 0u, 0u);
+      uint4 d = make_uint4(0u, oV, oV, 0u);
       uint16_t tpos = NONE16;
       if (k <= L) {
         const uint2 w = src[k];
         const uint32_t opc = w.x & 0xffu;
         const uint32_t f = w.x >> 8;
-        sprog[k] = make_uint2(opc, reads_feature(opc) ? f * (uint32_t)(SLOT * 4) : w.y);
+        sprog[k] = make_uint2(opc, reads_feature(opc) ? f * SLOTB : w.y);
         if (k < L) {
           const Aux ax = asrc[k];
+          const uint32_t next = src[k + 1].x & 0xffu;
           has = carries_erc<POW>(opc);
           tpos = (opc == I_LDC0 || opc == I_PSC) ? ax.tpos : ax.tpos_fused;
-          const uint32_t sl = (uint32_t)ax.src_l * (SLOT * 4), sr = (uint32_t)ax.src_r * (SLOT * 4);
-          const uint32_t fo = f * (uint32_t)(SLOT * 4);
+          const uint32_t sl = oV + (uint32_t)ax.src_l * SLOTB, sr = oV + (uint32_t)ax.src_r * SLOTB;
+          const uint32_t fo = oX + f * SLOTB;
           uint32_t rop = RV_COUNT;
           if (opc == I_LDC0 || opc == I_PSC) {
             rop = RV_CONST;
@@ -540,18 +598,19 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
             const uint32_t grp = pw ? opc - I_PW : (opc - I_BF) / NKIND;
             const uint32_t kind = pw ? (uint32_t)K_POW : (opc - I_BF) % NKIND;
             rop = RV_BIN + grp * 6 + kind;
-            d.y = grp <= 1 ? sl : sr;
-            d.z = (grp == 0 || grp == 2) ? fo : 0u;
+            d.y = grp <= 1 ? sl : sr;  // the A operand
+            if (grp == 0 || grp == 2) d.z = fo;
             d.w = w.y;
           } else if ((opc >= I_BS && opc < I_NOP) || (POW && opc >= I_PWS && opc < I_COUNT)) {
+            const bool rs = POW && opc >= I_PWS ? opc == I_PWR : opc >= I_RS;
             const uint32_t kind =
                 POW && opc >= I_PWS ? (uint32_t)K_POW : opc - (opc < I_RS ? I_BS : I_RS);
-            rop = RV_BIN + 4 * 6 + kind;
+            rop = RV_BIN + (rs ? 5u : 4u) * 6 + kind;
             d.y = sl;
             d.z = sr;
           }
           work = rop != RV_COUNT;
-          d.x = rop | ((uint32_t)k << 20);
+          d.x = rop | ((next == I_PSF || next == I_PSC) ? RV_GSM : 0u) | ((uint32_t)k << 16);
         }
       }
       const unsigned me = __ballot_sync(0xffffffffu, has);
@@ -561,7 +620,7 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
         const int o = n_erc + __popc(me & below);
         ek[o] = tpos;
         wg[o] = make_float2(0.f, 0.f);
-        d.x |= (uint32_t)o << 8;
+        d.x |= (uint32_t)o << 7;
       }
       if (work) rins[n_rev + __popc(mw & below)] = d;
       n_erc += __popc(me);
@@ -582,54 +641,24 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
         load_rows<R>(p.X + (size_t)f * p.ldx + row0, v);
         store_rows<R>(xt + (size_t)f * SLOT, v);
       }
-      float yc[R], yl[R], w[R];
+      float yc[R], yl[R], G[R];
       load_rows<R>(p.X + (size_t)p.F * p.ldx + row0, yc);
       load_rows<R>(p.ylo + row0, yl);
       float A[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = 0.f;
       run_program_tape<R, POW>(sprog, xt, A, stk, V);
-      seed_rows<R>(p, ab, A, yc, yl, valid, w);
-      store_rows<R>(V + (size_t)SLOT * (L - 1), w);  // the output's value becomes its adjoint
-      uint4 dn = n_rev > 0 ? rins[n_rev - 1] : make_uint4(0u, 0u, 0u, 0u);
-      for (int j = n_rev - 1; j >= 0; --j) {
-        const uint4 d = dn;
-        if (j > 0) dn = rins[j - 1];
-        float g[R];
-        load_rows<R>(reinterpret_cast<const float*>(vl + (d.x >> 20) * (uint32_t)(SLOT * 4)), g);
-        float* pv = reinterpret_cast<float*>(vl + d.y);
-        switch (d.x & 0xffu) {
-          case RV_CONST: {
-            float sm = 0.f;
+      seed_rows<R>(p, ab, A, yc, yl, valid, G);  // the root's adjoint, in registers
+      if (n_rev > 0) {
+        uint32_t vmask = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm += valid[r] ? g[r] : 0.f;
-            partl[(size_t)((d.x >> 8) & 0xfffu) * 33] = sm;
-            break;
-          }
-#define GG_RV_UN(U) \
-  case RV_UN + U: rev_un<R, U>(g, pv); break;
-          GG_RV_UN(U_SIN) GG_RV_UN(U_COS) GG_RV_UN(U_EXP) GG_RV_UN(U_LOG_ABS)
-          GG_RV_UN(U_SQRT_ABS) GG_RV_UN(U_SQUARE) GG_RV_UN(U_LOG) GG_RV_UN(U_SQRT)
-#undef GG_RV_UN
-#define GG_RV_BIN(G, K) \
-  case RV_BIN + G * 6 + K: rev_bin<R, G, K>(g, vl, xl, d, partl, valid); break;
-#define GG_RV_GRP(G) \
-  GG_RV_BIN(G, K_ADD) GG_RV_BIN(G, K_SUB) GG_RV_BIN(G, K_MUL) GG_RV_BIN(G, K_AQ) GG_RV_BIN(G, K_DIV)
-          GG_RV_GRP(0) GG_RV_GRP(1) GG_RV_GRP(2) GG_RV_GRP(3) GG_RV_GRP(4)
-#undef GG_RV_GRP
-#undef GG_RV_BIN
-          default:
-            if constexpr (POW) {  // the pow forms
-              switch ((d.x & 0xffu) - RV_BIN) {
-                case 0 * 6 + K_POW: rev_bin<R, 0, K_POW>(g, vl, xl, d, partl, valid); break;
-                case 1 * 6 + K_POW: rev_bin<R, 1, K_POW>(g, vl, xl, d, partl, valid); break;
-                case 2 * 6 + K_POW: rev_bin<R, 2, K_POW>(g, vl, xl, d, partl, valid); break;
-                case 3 * 6 + K_POW: rev_bin<R, 3, K_POW>(g, vl, xl, d, partl, valid); break;
-                case 4 * 6 + K_POW: rev_bin<R, 4, K_POW>(g, vl, xl, d, partl, valid); break;
-                default: break;
-              }
-            }
-            break;
+        for (int r = 0; r < R; ++r) vmask |= valid[r] ? 1u << r : 0u;
+        uint32_t rp = smem_u32(rins + (n_rev - 1)), cnt = (uint32_t)n_rev;
+        for (;;) {
+          uint32_t code, dx, dy, dz, dw;
+          interp_rev_asm(G, rp, cnt, code, dx, dy, dz, dw, wl32, wl32 + oV, pe32, rbase, vmask);
+          if (code == 0) break;
+          rev_cold<POW>(make_uint4(dx, dy, dz, dw), G, wl, V, partl, valid);
         }
       }
       __syncwarp();

@@ -604,6 +604,314 @@ class Gen:
         return self.lines
 
 
+# reverse-sweep descriptor forms of the staged adjoint (adjoint.cu)
+RV_CONST, RV_UN, RV_BIN, RV_COUNT = 0, 1, 9, 45
+RV_GSM = 64
+G_BF, G_BC, G_LF, G_LC, G_BS, G_RS = range(6)
+
+
+class RevGen:
+    """The staged adjoint's reverse sweep for 4 rows per lane (two .f32x2
+    pairs): a loop over the descriptors from the last to the first, the
+    next descriptor and its two operand rows loaded one step ahead, and an
+    indexed branch on the form (table entries 64 + form first load the
+    adjoint of a pushed value from V).  The forms of +, -, *, AQ, the
+    pushed ERC, square, log and sqrt run here; the others (sin, cos, exp,
+    division, pow) leave the statement with the descriptor and the C++
+    caller runs them (rev_cold) and re-enters.
+
+    Operands: %0 rp (next descriptor's address), %1 count left, %2 code
+    (1: a form for the caller, 0: done), %3..%6 the descriptor left with,
+    %7..%10 G (the adjoint carried in registers), %11 the lane's base, %12
+    the lane's base + V, %13 the lane's ERC partial column, %14 the first
+    descriptor's address, %15 the valid-row mask.  Same operations in the
+    same order as adjoint.cu's C++ forms."""
+
+    def __init__(self):
+        self.lines = []
+
+    def o(self, s):
+        self.lines.append(s)
+
+    def label(self, s):
+        self.lines.append(s + ":")
+
+    # -- helpers on the current adjoint g (pairs g0, g1) and operand rows --
+    def rows(self, pair, dst):
+        """Unpack a pair register set into 4 f32 registers dst0..dst3."""
+        self.o(f"mov.b64 {{{dst}0, {dst}1}}, {pair}0;")
+        self.o(f"mov.b64 {{{dst}2, {dst}3}}, {pair}1;")
+
+    def pack(self, src, pair):
+        self.o(f"mov.b64 {pair}0, {{{src}0, {src}1}};")
+        self.o(f"mov.b64 {pair}1, {{{src}2, {src}3}};")
+
+    def neg(self, dst, src):
+        for i in range(2):
+            self.o(f"xor.b64 {dst}{i}, {src}{i}, 0x8000000080000000;")
+
+    def mul(self, dst, a, b):
+        for i in range(2):
+            self.o(f"mul.rn.f32x2 {dst}{i}, {a}{i}, {b}{i};")
+
+    def store(self, src, off):
+        """Store pairs src at the lane's row of the operand at offset off."""
+        self.o(f"add.u32 ad, %11, {off};")
+        self.o(f"st.shared.v2.b64 [ad], {{{src}0, {src}1}};")
+
+    def erc(self, src):
+        """Sum the valid rows of pairs src (in row order from zero, as the
+        C++ does) and store the sum at the descriptor's ERC ordinal."""
+        self.rows(src, "h")
+        for r in range(4):
+            self.o(f"selp.f32 h{r}, h{r}, 0f00000000, pv{r};")
+        self.o("add.rn.f32 s, h0, h1;")
+        self.o("add.rn.f32 s, s, h2;")
+        self.o("add.rn.f32 s, s, h3;")
+        self.o("bfe.u32 kk, x, 7, 9;")
+        self.o("mad.lo.u32 ad, kk, 132, %13;")
+        self.o("st.shared.f32 [ad], s;")
+
+    def cpair(self):
+        self.o("mov.b64 cc0, {w, w};")
+        self.o("mov.b64 cc1, cc0;")
+
+    def aq_q(self, b, q):
+        """q = rsqrt(1 + b^2) row by row (rsqrt.approx, as rsqrt_approx)."""
+        self.rows(b, "r")
+        for r in range(4):
+            self.o(f"fma.rn.f32 r{r}, r{r}, r{r}, 0f3F800000;")
+            self.o(f"rsqrt.approx.f32 r{r}, r{r};")
+        self.pack("r", q)
+
+    def aq_db(self, a, b, q, dst):
+        """dst = ((((-a) b) q) q) q, the C++ order."""
+        self.neg(dst, a)
+        self.mul(dst, dst, b)
+        for _ in range(3):
+            self.mul(dst, dst, q)
+
+    def nxt(self):
+        self.o("bra.uni RV_NEXT;")
+
+    # -- the forms ------------------------------------------------------------
+    def bin_form(self, grp, kind):
+        o = self.o
+        # operands: BF (A=u, x=v)  BC (A=u, c)  LF (x=v, A=u)  LC (c, A=u)
+        #           BS (pop=u, A=v)  RS (A=u, pop=v)
+        if kind == K_ADD:
+            if grp in (G_BC, G_LC):
+                self.erc("g")
+            elif grp == G_BS:
+                self.store("g", "y")
+            elif grp == G_RS:
+                self.store("g", "z")
+        elif kind == K_SUB:
+            if grp == G_BC:
+                self.neg("e", "g")
+                self.erc("e")
+            elif grp == G_LF:
+                self.neg("g", "g")
+            elif grp == G_LC:
+                self.erc("g")
+                self.neg("g", "g")
+            elif grp == G_BS:
+                self.store("g", "y")
+                self.neg("g", "g")
+            elif grp == G_RS:
+                self.neg("e", "g")
+                self.store("e", "z")
+        elif kind == K_MUL:
+            if grp in (G_BF, G_LF):
+                self.mul("g", "g", "v")
+            elif grp in (G_BC, G_LC):
+                self.mul("e", "g", "u")
+                self.erc("e")
+                self.cpair()
+                self.mul("g", "g", "cc")
+            elif grp == G_BS:
+                self.mul("e", "g", "v")
+                self.store("e", "y")
+                self.mul("g", "g", "u")
+            else:  # RS
+                self.mul("e", "g", "u")
+                self.store("e", "z")
+                self.mul("g", "g", "v")
+        else:  # K_AQ: da = q(b), db = -a b q^3
+            if grp == G_BF:
+                self.aq_q("v", "q")
+                self.mul("g", "g", "q")
+            elif grp == G_BC:
+                o("fma.rn.f32 s, cf, cf, 0f3F800000;")
+                o("rsqrt.approx.f32 s, s;")
+                o("mov.b64 q0, {s, s};")
+                o("mov.b64 q1, q0;")
+                self.cpair()
+                self.aq_db("u", "cc", "q", "e")
+                self.mul("e", "g", "e")
+                self.erc("e")
+                self.mul("g", "g", "q")
+            elif grp == G_LF:
+                self.aq_q("u", "q")
+                self.aq_db("v", "u", "q", "e")
+                self.mul("g", "g", "e")
+            elif grp == G_LC:
+                self.aq_q("u", "q")
+                self.mul("e", "g", "q")
+                self.erc("e")
+                self.cpair()
+                self.aq_db("cc", "u", "q", "e")
+                self.mul("g", "g", "e")
+            elif grp == G_BS:
+                self.aq_q("v", "q")
+                self.mul("e", "g", "q")
+                self.store("e", "y")
+                self.aq_db("u", "v", "q", "e")
+                self.mul("g", "g", "e")
+            else:  # RS
+                self.aq_q("v", "q")
+                self.aq_db("u", "v", "q", "e")
+                self.mul("e", "g", "e")
+                self.store("e", "z")
+                self.mul("g", "g", "q")
+        self.nxt()
+
+    def un_form(self, u):
+        o = self.o
+        if u == U_SQUARE:
+            for i in range(2):
+                o(f"add.rn.f32x2 e{i}, u{i}, u{i};")
+            self.mul("g", "g", "e")
+        elif u in (U_LOG_ABS, U_LOG):
+            self.rows("u", "r")
+            for r in range(4):
+                o(f"rcp.rn.f32 r{r}, r{r};")
+            self.pack("r", "e")
+            self.mul("g", "g", "e")
+        elif u == U_SQRT:
+            self.rows("u", "r")
+            for r in range(4):
+                o(f"rsqrt.approx.f32 r{r}, r{r};")
+                o(f"mul.rn.f32 r{r}, r{r}, 0f3F000000;")
+            self.pack("r", "e")
+            self.mul("g", "g", "e")
+        else:  # U_SQRT_ABS: x == 0 ? 0 : g copysign(0.5 rsqrt|x|, x)
+            self.rows("u", "r")
+            self.rows("g", "h")
+            for r in range(4):
+                o(f"abs.f32 s, r{r};")
+                o(f"rsqrt.approx.f32 s, s;")
+                o(f"mul.rn.f32 s, s, 0f3F000000;")
+                o(f"copysign.f32 s, r{r}, s;")
+                o(f"mul.rn.f32 h{r}, h{r}, s;")
+                o(f"setp.eq.f32 p, r{r}, 0f00000000;")
+                o(f"selp.f32 h{r}, 0f00000000, h{r}, p;")
+            self.pack("h", "g")
+        self.nxt()
+
+    def build(self):
+        o = self.o
+        o("{")
+        o(".reg .b64 g<2>, u<2>, v<2>, un<2>, vn<2>, e<2>, q<2>, cc<2>;")
+        o(".reg .f32 r<4>, h<4>, s, cf;")
+        o(".reg .u32 x, y, z, w, nx, ny, nz, nw, opc, ad, pa, kk;")
+        o(".reg .pred p, pv<4>;")
+        o("mov.b64 g0, {%7, %8};")
+        o("mov.b64 g1, {%9, %10};")
+        for r in range(4):
+            o(f"and.b32 kk, %15, {1 << r};")
+            o(f"setp.ne.u32 pv{r}, kk, 0;")
+        o("setp.eq.u32 p, %1, 0;")
+        o("@p bra RV_DONE;")
+        o("ld.shared.v4.u32 {x, y, z, w}, [%0];")
+        o("sub.u32 %0, %0, 16;")
+        o("sub.u32 %1, %1, 1;")
+        o("add.u32 ad, %11, y;")
+        o("ld.shared.v2.b64 {u0, u1}, [ad];")
+        o("add.u32 ad, %11, z;")
+        o("ld.shared.v2.b64 {v0, v1}, [ad];")
+        # the table: forms 0..63, then the same forms after loading g from V
+        hot = {RV_CONST: "RV_CONST"}
+        for u in (U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
+            hot[RV_UN + u] = f"RV_U{u}"
+        for grp in range(6):
+            for kind in (K_ADD, K_SUB, K_MUL, K_AQ):
+                hot[RV_BIN + grp * 6 + kind] = f"RV_B{grp}_{kind}"
+        targets = [hot.get(i, "RV_COLD") for i in range(RV_GSM)]
+        targets += [f"RV_G{i}" if i in hot else "RV_COLD" for i in range(RV_GSM)]
+        o("RV_TBL: .branchtargets " + ", ".join(targets) + ";")
+        self.label("RV_LOOP")
+        o("setp.eq.u32 p, %1, 0;")
+        o("selp.b32 pa, %14, %0, p;")  # nothing left: a harmless in-range read
+        o("ld.shared.v4.u32 {nx, ny, nz, nw}, [pa];")
+        o("add.u32 ad, %11, ny;")
+        o("ld.shared.v2.b64 {un0, un1}, [ad];")
+        o("add.u32 ad, %11, nz;")
+        o("ld.shared.v2.b64 {vn0, vn1}, [ad];")
+        o("mov.b32 cf, w;")
+        o("and.b32 opc, x, 127;")
+        o("brx.idx.uni opc, RV_TBL;")
+        # GSM entries: the adjoint of a pushed value, from its V entry
+        for i in sorted(hot):
+            self.label(f"RV_G{i}")
+            o("shr.u32 kk, x, 16;")
+            o("mad.lo.u32 ad, kk, 512, %12;")
+            o("ld.shared.v2.b64 {g0, g1}, [ad];")
+            o(f"bra.uni {hot[i]};")
+        self.label("RV_CONST")
+        self.erc("g")
+        self.nxt()
+        for u in (U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
+            self.label(f"RV_U{u}")
+            self.un_form(u)
+        for grp in range(6):
+            for kind in (K_ADD, K_SUB, K_MUL, K_AQ):
+                self.label(f"RV_B{grp}_{kind}")
+                self.bin_form(grp, kind)
+        self.label("RV_NEXT")
+        o("setp.eq.u32 p, %1, 0;")
+        o("@p bra RV_DONE;")
+        o("mov.u32 x, nx;")
+        o("mov.u32 y, ny;")
+        o("mov.u32 z, nz;")
+        o("mov.u32 w, nw;")
+        for i in range(2):
+            o(f"mov.b64 u{i}, un{i};")
+            o(f"mov.b64 v{i}, vn{i};")
+        o("sub.u32 %0, %0, 16;")
+        o("sub.u32 %1, %1, 1;")
+        o("bra.uni RV_LOOP;")
+        self.label("RV_COLD")
+        o("mov.u32 %2, 1;")
+        o("mov.u32 %3, x;")
+        o("mov.u32 %4, y;")
+        o("mov.u32 %5, z;")
+        o("mov.u32 %6, w;")
+        o("bra.uni RV_OUT;")
+        self.label("RV_DONE")
+        o("mov.u32 %2, 0;")
+        self.label("RV_OUT")
+        o("mov.b64 {%7, %8}, g0;")
+        o("mov.b64 {%9, %10}, g1;")
+        o("}")
+        return self.lines
+
+
+def emit_rev() -> str:
+    lines = RevGen().build()
+    body = "\n".join('      "' + ln + '\\n\\t"' for ln in lines)
+    return ("__device__ __forceinline__ void interp_rev_asm(float (&G)[4], uint32_t& rp,\n"
+            "    uint32_t& cnt, uint32_t& code, uint32_t& dx, uint32_t& dy, uint32_t& dz,\n"
+            "    uint32_t& dw, uint32_t wl, uint32_t wlv, uint32_t wpe, uint32_t rbase,\n"
+            "    uint32_t vmask) {\n"
+            "  asm volatile(\n" + body + "\n"
+            '      : "+r"(rp), "+r"(cnt), "=r"(code), "=r"(dx), "=r"(dy), "=r"(dz), "=r"(dw),\n'
+            '        "+f"(G[0]), "+f"(G[1]), "+f"(G[2]), "+f"(G[3])\n'
+            '      : "r"(wl), "r"(wlv), "r"(wpe), "r"(rbase), "r"(vmask)\n'
+            '      : "memory");\n'
+            "}\n")
+
+
 def emit(R: int, special: bool, tape: bool = False) -> str:
     g = Gen(R, special, tape)
     lines = g.build()
@@ -625,7 +933,8 @@ def emit(R: int, special: bool, tape: bool = False) -> str:
 def generate() -> str:
     head = ("// Generated by interp_gen.py (run by build.py); do not edit.\n"
             "// The interpreter's dispatch loop as inline PTX for 8 and 4 rows per lane,\n"
-            "// and with a value tape (the adjoint's forward half) for 4 rows per lane.\n"
+            "// and with a value tape (the adjoint's forward half) for 4 rows per lane;\n"
+            "// the staged adjoint's reverse sweep (4 rows per lane).\n"
             "template <int R>\n"
             "__device__ __forceinline__ void interp_asm(float (&A)[R], uint32_t& pc,\n"
             "    uint32_t& sp, uint32_t xs, uint32_t& code, uint32_t& arg);\n"
@@ -639,7 +948,7 @@ def generate() -> str:
     # 4-row PTX, half the size, keeps them (the autotuner picks it for the
     # operator sets whose unprotected log and sqrt often meet negatives).
     return (head + emit(8, special=False) + "\n" + emit(4, special=True) + "\n" +
-            emit(4, special=True, tape=True))
+            emit(4, special=True, tape=True) + "\n" + emit_rev())
 
 
 def main(out_path: str) -> None:
