@@ -84,6 +84,72 @@ def f2(s: str) -> str:
     return "0x%08X%08X" % (b, b)
 
 
+def sincos_pair(o, x, dst):
+    """gmath.cuh sin_or_cos_reduced2 on the pair x into dst (x is read
+    before dst is written): the quadrant shift in sh (0 sin, 1 cos);
+    registers v0..v5, c1, c2, q0, q1, z0..z3, k, p."""
+    o(f"mov.b64 c1, {f2(TWO_OVER_PI)};")
+    o(f"mov.b64 c2, {f2(MAGIC)};")
+    o(f"fma.rn.f32x2 v0, {x}, c1, c2;")               # t
+    o(f"mov.b64 c1, {f2('-' + MAGIC)};")
+    o("add.rn.f32x2 v1, v0, c1;")                      # j
+    o("mov.b64 {q0, q1}, v0;")
+    o("add.u32 q0, q0, sh;")
+    o("add.u32 q1, q1, sh;")
+    o(f"mov.b64 c1, {f2(PIO2_1)};")
+    o(f"fma.rn.f32x2 v2, v1, c1, {x};")                # r
+    o(f"mov.b64 c1, {f2(PIO2_2)};")
+    o("fma.rn.f32x2 v2, v1, c1, v2;")
+    o(f"mov.b64 c1, {f2(PIO2_3)};")
+    o("fma.rn.f32x2 v2, v1, c1, v2;")
+    o("mul.rn.f32x2 v3, v2, v2;")                      # s
+    o(f"mov.b64 c1, {f2(SIN_C[0])};")
+    o(f"mov.b64 c2, {f2(SIN_C[1])};")
+    o("fma.rn.f32x2 v4, v3, c1, c2;")                  # ps
+    for k in (2, 3):
+        o(f"mov.b64 c1, {f2(SIN_C[k])};")
+        o("fma.rn.f32x2 v4, v3, v4, c1;")
+    o("mul.rn.f32x2 v5, v2, v3;")                      # r s
+    o("fma.rn.f32x2 v4, v5, v4, v2;")                  # sr
+    o(f"mov.b64 c1, {f2(COS_C[0])};")
+    o(f"mov.b64 c2, {f2(COS_C[1])};")
+    o("fma.rn.f32x2 v5, v3, c1, c2;")                  # pc
+    for k in (2, 3, 4):
+        o(f"mov.b64 c1, {f2(COS_C[k])};")
+        o("fma.rn.f32x2 v5, v3, v5, c1;")
+    o(f"mov.b64 c1, {f2('1.0')};")
+    o("fma.rn.f32x2 v5, v3, v5, c1;")                  # cr
+    o("mov.b64 {z0, z1}, v4;")
+    o("mov.b64 {z2, z3}, v5;")
+    for e in (0, 1):
+        o(f"and.b32 k, q{e}, 1;")
+        o("setp.ne.u32 p, k, 0;")
+        o(f"selp.b32 z{e}, z{2 + e}, z{e}, p;")
+        o(f"and.b32 k, q{e}, 2;")
+        o("shl.b32 k, k, 30;")
+        o(f"xor.b32 z{e}, z{e}, k;")
+    o(f"mov.b64 {dst}, {{z0, z1}};")
+
+
+def exp_pair(o, x, dst):
+    """gmath.cuh exp_ex2_2 on the pair x into dst (x is read before dst is
+    written); registers v0, v1, c1, c2, z0, z1."""
+    o(f"mov.b64 c1, {f2(LOG2E_HI)};")
+    o(f"mul.rn.f32x2 v0, {x}, c1;")                   # hi
+    o(f"mov.b64 c2, {f2('-1.0')};")
+    o("mul.rn.f32x2 v1, v0, c2;")                      # -hi
+    o(f"fma.rn.f32x2 v1, {x}, c1, v1;")               # x L - hi (exact)
+    o(f"mov.b64 c2, {f2(LOG2E_LO)};")
+    o(f"fma.rn.f32x2 v1, {x}, c2, v1;")               # lo
+    o("mov.b64 {z0, z1}, v0;")
+    o("ex2.approx.f32 z0, z0;")
+    o("ex2.approx.f32 z1, z1;")
+    o("mov.b64 v0, {z0, z1};")                         # 2^hi
+    o(f"mov.b64 c1, {f2(LN2_HI)};")
+    o("mul.rn.f32x2 v1, v1, c1;")                      # lo ln2
+    o(f"fma.rn.f32x2 {dst}, v0, v1, v0;")
+
+
 class Gen:
     def __init__(self, R: int, special: bool = True, tape: bool = False):
         """special: finish the row-by-row forms of exp, log and sqrt inside
@@ -230,48 +296,7 @@ class Gen:
         self.o(f"setp.gtu.f32 p, m, {f(TRIG_RANGE)};")
         self.o("@p bra GG_EXIT;")
         for i in range(NP):
-            x = f"a{i}"
-            self.o(f"mov.b64 c1, {f2(TWO_OVER_PI)};")
-            self.o(f"mov.b64 c2, {f2(MAGIC)};")
-            self.o(f"fma.rn.f32x2 v0, {x}, c1, c2;")               # t
-            self.o(f"mov.b64 c1, {f2('-' + MAGIC)};")
-            self.o("add.rn.f32x2 v1, v0, c1;")                      # j
-            self.o("mov.b64 {q0, q1}, v0;")
-            self.o("add.u32 q0, q0, sh;")
-            self.o("add.u32 q1, q1, sh;")
-            self.o(f"mov.b64 c1, {f2(PIO2_1)};")
-            self.o(f"fma.rn.f32x2 v2, v1, c1, {x};")                # r
-            self.o(f"mov.b64 c1, {f2(PIO2_2)};")
-            self.o("fma.rn.f32x2 v2, v1, c1, v2;")
-            self.o(f"mov.b64 c1, {f2(PIO2_3)};")
-            self.o("fma.rn.f32x2 v2, v1, c1, v2;")
-            self.o("mul.rn.f32x2 v3, v2, v2;")                      # s
-            self.o(f"mov.b64 c1, {f2(SIN_C[0])};")
-            self.o(f"mov.b64 c2, {f2(SIN_C[1])};")
-            self.o("fma.rn.f32x2 v4, v3, c1, c2;")                  # ps
-            for k in (2, 3):
-                self.o(f"mov.b64 c1, {f2(SIN_C[k])};")
-                self.o("fma.rn.f32x2 v4, v3, v4, c1;")
-            self.o("mul.rn.f32x2 v5, v2, v3;")                      # r s
-            self.o("fma.rn.f32x2 v4, v5, v4, v2;")                  # sr
-            self.o(f"mov.b64 c1, {f2(COS_C[0])};")
-            self.o(f"mov.b64 c2, {f2(COS_C[1])};")
-            self.o("fma.rn.f32x2 v5, v3, c1, c2;")                  # pc
-            for k in (2, 3, 4):
-                self.o(f"mov.b64 c1, {f2(COS_C[k])};")
-                self.o("fma.rn.f32x2 v5, v3, v5, c1;")
-            self.o(f"mov.b64 c1, {f2('1.0')};")
-            self.o("fma.rn.f32x2 v5, v3, v5, c1;")                  # cr
-            self.o("mov.b64 {z0, z1}, v4;")
-            self.o("mov.b64 {z2, z3}, v5;")
-            for e in (0, 1):
-                self.o(f"and.b32 k, q{e}, 1;")
-                self.o("setp.ne.u32 p, k, 0;")
-                self.o(f"selp.b32 z{e}, z{2 + e}, z{e}, p;")
-                self.o(f"and.b32 k, q{e}, 2;")
-                self.o("shl.b32 k, k, 30;")
-                self.o(f"xor.b32 z{e}, z{e}, k;")
-            self.o(f"mov.b64 a{i}, {{z0, z1}};")
+            sincos_pair(self.o, f"a{i}", f"a{i}")
         self.next()
 
     def logsqrt_check(self, special):
@@ -471,20 +496,7 @@ class Gen:
         self.o(f"setp.gtu.f32 p, m, {f(EXP_RANGE)};")
         self.o("@p bra GG_EXP_SP;" if self.special else "@p bra GG_EXIT;")
         for i in range(self.NP):
-            self.o(f"mov.b64 c1, {f2(LOG2E_HI)};")
-            self.o(f"mul.rn.f32x2 v0, a{i}, c1;")                   # hi
-            self.o(f"mov.b64 c2, {f2('-1.0')};")
-            self.o("mul.rn.f32x2 v1, v0, c2;")                      # -hi
-            self.o(f"fma.rn.f32x2 v1, a{i}, c1, v1;")               # x L - hi (exact)
-            self.o(f"mov.b64 c2, {f2(LOG2E_LO)};")
-            self.o(f"fma.rn.f32x2 v1, a{i}, c2, v1;")               # lo
-            self.o("mov.b64 {z0, z1}, v0;")
-            self.o("ex2.approx.f32 z0, z0;")
-            self.o("ex2.approx.f32 z1, z1;")
-            self.o("mov.b64 v0, {z0, z1};")                         # 2^hi
-            self.o(f"mov.b64 c1, {f2(LN2_HI)};")
-            self.o("mul.rn.f32x2 v1, v1, c1;")                      # lo ln2
-            self.o(f"fma.rn.f32x2 a{i}, v0, v1, v0;")
+            exp_pair(self.o, f"a{i}", f"a{i}")
         self.next()
 
     def build(self):
@@ -616,9 +628,10 @@ class RevGen:
     next descriptor and its two operand rows loaded one step ahead, and an
     indexed branch on the form (table entries 64 + form first load the
     adjoint of a pushed value from V).  The forms of +, -, *, AQ, the
-    pushed ERC, square, log and sqrt run here; the others (sin, cos, exp,
-    division, pow) leave the statement with the descriptor and the C++
-    caller runs them (rev_cold) and re-enters.
+    pushed ERC and every unary operator run here (sin, cos and exp with the
+    forward's own forms, for a group within their range); division, pow
+    and out-of-range groups leave the statement with the descriptor and the
+    C++ caller runs them (rev_cold) and re-enters.
 
     Operands: %0 rp (next descriptor's address), %1 count left, %2 code
     (1: a form for the caller, 0: done), %3..%6 the descriptor left with,
@@ -723,80 +736,104 @@ class RevGen:
                 self.store("e", "z")
         elif kind == K_MUL:
             if grp in (G_BF, G_LF):
-                self.mul("g", "g", "v")
+                self.mul("g", "g", "vb")
             elif grp in (G_BC, G_LC):
-                self.mul("e", "g", "u")
+                self.mul("e", "g", "ua")
                 self.erc("e")
                 self.cpair()
                 self.mul("g", "g", "cc")
             elif grp == G_BS:
-                self.mul("e", "g", "v")
+                self.mul("e", "g", "vb")
                 self.store("e", "y")
-                self.mul("g", "g", "u")
+                self.mul("g", "g", "ua")
             else:  # RS
-                self.mul("e", "g", "u")
+                self.mul("e", "g", "ua")
                 self.store("e", "z")
-                self.mul("g", "g", "v")
+                self.mul("g", "g", "vb")
         else:  # K_AQ: da = q(b), db = -a b q^3
             if grp == G_BF:
-                self.aq_q("v", "q")
-                self.mul("g", "g", "q")
+                self.aq_q("vb", "aq")
+                self.mul("g", "g", "aq")
             elif grp == G_BC:
                 o("fma.rn.f32 s, cf, cf, 0f3F800000;")
                 o("rsqrt.approx.f32 s, s;")
-                o("mov.b64 q0, {s, s};")
-                o("mov.b64 q1, q0;")
+                o("mov.b64 aq0, {s, s};")
+                o("mov.b64 aq1, aq0;")
                 self.cpair()
-                self.aq_db("u", "cc", "q", "e")
+                self.aq_db("ua", "cc", "aq", "e")
                 self.mul("e", "g", "e")
                 self.erc("e")
-                self.mul("g", "g", "q")
+                self.mul("g", "g", "aq")
             elif grp == G_LF:
-                self.aq_q("u", "q")
-                self.aq_db("v", "u", "q", "e")
+                self.aq_q("ua", "aq")
+                self.aq_db("vb", "ua", "aq", "e")
                 self.mul("g", "g", "e")
             elif grp == G_LC:
-                self.aq_q("u", "q")
-                self.mul("e", "g", "q")
+                self.aq_q("ua", "aq")
+                self.mul("e", "g", "aq")
                 self.erc("e")
                 self.cpair()
-                self.aq_db("cc", "u", "q", "e")
+                self.aq_db("cc", "ua", "aq", "e")
                 self.mul("g", "g", "e")
             elif grp == G_BS:
-                self.aq_q("v", "q")
-                self.mul("e", "g", "q")
+                self.aq_q("vb", "aq")
+                self.mul("e", "g", "aq")
                 self.store("e", "y")
-                self.aq_db("u", "v", "q", "e")
+                self.aq_db("ua", "vb", "aq", "e")
                 self.mul("g", "g", "e")
             else:  # RS
-                self.aq_q("v", "q")
-                self.aq_db("u", "v", "q", "e")
+                self.aq_q("vb", "aq")
+                self.aq_db("ua", "vb", "aq", "e")
                 self.mul("e", "g", "e")
                 self.store("e", "z")
-                self.mul("g", "g", "q")
+                self.mul("g", "g", "aq")
         self.nxt()
+
+    def range_check(self, bound):
+        """Leave for the C++ form (which takes the library's path) unless
+        max |x| over the rows is within bound, as the forward's check."""
+        o = self.o
+        self.rows("ua", "r")
+        for r in range(4):
+            o(f"abs.f32 s, r{r};")
+            o("mov.f32 m, s;" if r == 0 else "max.f32 m, m, s;")
+        o(f"setp.gtu.f32 p, m, {f(bound)};")
+        o("@p bra RV_COLD;")
 
     def un_form(self, u):
         o = self.o
-        if u == U_SQUARE:
+        if u in (U_SIN, U_COS):  # sin' = cos, cos' = -sin
+            self.range_check(TRIG_RANGE)
+            o("mov.u32 sh, %d;" % (1 if u == U_SIN else 0))
             for i in range(2):
-                o(f"add.rn.f32x2 e{i}, u{i}, u{i};")
+                sincos_pair(o, f"ua{i}", f"e{i}")
+            self.mul("g", "g", "e")
+            if u == U_COS:
+                self.neg("g", "g")
+        elif u == U_EXP:
+            self.range_check(EXP_RANGE)
+            for i in range(2):
+                exp_pair(o, f"ua{i}", f"e{i}")
+            self.mul("g", "g", "e")
+        elif u == U_SQUARE:
+            for i in range(2):
+                o(f"add.rn.f32x2 e{i}, ua{i}, ua{i};")
             self.mul("g", "g", "e")
         elif u in (U_LOG_ABS, U_LOG):
-            self.rows("u", "r")
+            self.rows("ua", "r")
             for r in range(4):
                 o(f"rcp.rn.f32 r{r}, r{r};")
             self.pack("r", "e")
             self.mul("g", "g", "e")
         elif u == U_SQRT:
-            self.rows("u", "r")
+            self.rows("ua", "r")
             for r in range(4):
                 o(f"rsqrt.approx.f32 r{r}, r{r};")
                 o(f"mul.rn.f32 r{r}, r{r}, 0f3F000000;")
             self.pack("r", "e")
             self.mul("g", "g", "e")
         else:  # U_SQRT_ABS: x == 0 ? 0 : g copysign(0.5 rsqrt|x|, x)
-            self.rows("u", "r")
+            self.rows("ua", "r")
             self.rows("g", "h")
             for r in range(4):
                 o(f"abs.f32 s, r{r};")
@@ -812,9 +849,10 @@ class RevGen:
     def build(self):
         o = self.o
         o("{")
-        o(".reg .b64 g<2>, u<2>, v<2>, un<2>, vn<2>, e<2>, q<2>, cc<2>;")
-        o(".reg .f32 r<4>, h<4>, s, cf;")
-        o(".reg .u32 x, y, z, w, nx, ny, nz, nw, opc, ad, pa, kk;")
+        o(".reg .b64 g<2>, ua<2>, vb<2>, uan<2>, vbn<2>, e<2>, aq<2>, cc<2>, v<6>, c1, c2;")
+        o(".reg .f32 r<4>, h<4>, s, cf, m;")
+        o(".reg .u32 x, y, z, w, nx, ny, nz, nw, opc, ad, pa, kk, k, sh, q<2>;")
+        o(".reg .b32 z<4>;")
         o(".reg .pred p, pv<4>;")
         o("mov.b64 g0, {%7, %8};")
         o("mov.b64 g1, {%9, %10};")
@@ -827,12 +865,12 @@ class RevGen:
         o("sub.u32 %0, %0, 16;")
         o("sub.u32 %1, %1, 1;")
         o("add.u32 ad, %11, y;")
-        o("ld.shared.v2.b64 {u0, u1}, [ad];")
+        o("ld.shared.v2.b64 {ua0, ua1}, [ad];")
         o("add.u32 ad, %11, z;")
-        o("ld.shared.v2.b64 {v0, v1}, [ad];")
+        o("ld.shared.v2.b64 {vb0, vb1}, [ad];")
         # the table: forms 0..63, then the same forms after loading g from V
         hot = {RV_CONST: "RV_CONST"}
-        for u in (U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
+        for u in (U_SIN, U_COS, U_EXP, U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
             hot[RV_UN + u] = f"RV_U{u}"
         for grp in range(6):
             for kind in (K_ADD, K_SUB, K_MUL, K_AQ):
@@ -845,9 +883,9 @@ class RevGen:
         o("selp.b32 pa, %14, %0, p;")  # nothing left: a harmless in-range read
         o("ld.shared.v4.u32 {nx, ny, nz, nw}, [pa];")
         o("add.u32 ad, %11, ny;")
-        o("ld.shared.v2.b64 {un0, un1}, [ad];")
+        o("ld.shared.v2.b64 {uan0, uan1}, [ad];")
         o("add.u32 ad, %11, nz;")
-        o("ld.shared.v2.b64 {vn0, vn1}, [ad];")
+        o("ld.shared.v2.b64 {vbn0, vbn1}, [ad];")
         o("mov.b32 cf, w;")
         o("and.b32 opc, x, 127;")
         o("brx.idx.uni opc, RV_TBL;")
@@ -861,7 +899,7 @@ class RevGen:
         self.label("RV_CONST")
         self.erc("g")
         self.nxt()
-        for u in (U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
+        for u in (U_SIN, U_COS, U_EXP, U_SQUARE, U_LOG_ABS, U_LOG, U_SQRT, U_SQRT_ABS):
             self.label(f"RV_U{u}")
             self.un_form(u)
         for grp in range(6):
@@ -876,8 +914,8 @@ class RevGen:
         o("mov.u32 z, nz;")
         o("mov.u32 w, nw;")
         for i in range(2):
-            o(f"mov.b64 u{i}, un{i};")
-            o(f"mov.b64 v{i}, vn{i};")
+            o(f"mov.b64 ua{i}, uan{i};")
+            o(f"mov.b64 vb{i}, vbn{i};")
         o("sub.u32 %0, %0, 16;")
         o("sub.u32 %1, %1, 1;")
         o("bra.uni RV_LOOP;")
