@@ -19,9 +19,11 @@ Reported:
              every step
   plain      the one-launch-per-trial form (multi-block per trial + a
              second-stage reduction launch per trial)
-  roofline   the batched forward kernel against the FP32 issue peak
-             (152 SMs x 128 lanes x the SM clock sampled during the run),
-             counting the operations of the folded programs
+  roofline   the batched forward kernel's algorithmic FP32 and SFU
+             operations (of the folded programs) per second against the
+             FP32 and SFU issue rates measured in the same process
+             (ggeval_pipe_rates); the pipe with the larger fraction bounds
+             the kernel and gives the headline fields
   parity     the timed outputs of a sample of trials against the FP64 oracle
   cpu_baseline  the FP64 oracle on one host core, on a sample of trials
   cpu_baseline_all_cores  the same oracle over every host core (process pool)
@@ -99,6 +101,44 @@ def source_hash():
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+_PEAKS = {}
+
+
+def measured_peaks(gg, dev):
+    """FP32 and SFU issue rates (Gop/s) measured in this process by the
+    library's microbenchmarks (ggeval_pipe_rates): FP32 = the faster of
+    FFMA and FFMA2 chains, SFU = the median of the rsqrt, ex2, lg2 and sin
+    chains."""
+    if dev not in _PEAKS:
+        r = gg.pipe_rates(dev)
+        sfu = sorted(r[k] for k in ("rsqrt", "ex2", "lg2", "sin"))
+        _PEAKS[dev] = {"fp32": max(r["ffma"], r["ffma2"]) / 1e9,
+                       "sfu": 0.5 * (sfu[1] + sfu[2]) / 1e9,
+                       "rates_gops": {k: v / 1e9 for k, v in r.items()}}
+    return _PEAKS[dev]
+
+
+def pipe_roofline(alg_fp32, alg_sfu, ms, peaks, sm_mhz):
+    """Two-pipe roofline of an interpreter kernel: the achieved rate of the
+    algorithmic FP32 and SFU operations against the measured peaks; the
+    pipe with the larger fraction bounds the kernel and gives the headline
+    fields."""
+    fp = alg_fp32 / (ms * 1e-3) / 1e9
+    sf = alg_sfu / (ms * 1e-3) / 1e9
+    out = {"fp32": {"achieved": fp, "peak": peaks["fp32"], "frac": fp / peaks["fp32"]},
+           "sfu": {"achieved": sf, "peak": peaks["sfu"], "frac": sf / peaks["sfu"]}}
+    pipe = "sfu" if out["sfu"]["frac"] > out["fp32"]["frac"] else "fp32"
+    return {"bound": "alu", "pipe": pipe, "achieved": out[pipe]["achieved"],
+            "peak": out[pipe]["peak"], "unit": "Gop/s", "frac": out[pipe]["frac"],
+            **out,
+            "peak_basis": ("measured in this process by ggeval_pipe_rates (FP32: faster of "
+                           "FFMA / FFMA2 chains; SFU: median of rsqrt, ex2, lg2, sin chains); "
+                           f"nominal at the sampled {sm_mhz:.0f} MHz: "
+                           f"{SMS * FP32_LANES * sm_mhz / 1e3:.0f} / "
+                           f"{SMS * SFU_LANES * sm_mhz / 1e3:.0f} Gop/s"),
+            "pipe_rates_gops": peaks["rates_gops"]}
 
 
 def parse():
@@ -421,21 +461,15 @@ class Runner:
         w = self.w
         N = w["N"]
         sm_mhz = (ck or fallback_ck or {}).get("sm_mhz") or 1477.0
-        peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9  # Gop/s
-        peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
         alg_fp32 = (fp32_ops + ACC_FP32 * valid) * N  # per launch
         alg_sfu = sfu_ops * N
-        ach_fp32 = alg_fp32 / (fwd_avg * 1e-3) / 1e9
-        ach_sfu = alg_sfu / (fwd_avg * 1e-3) / 1e9
         x_bytes = (w["F"] + 1) * N * 4
         traffic = NCU_TRAFFIC.get((w["name"], source_hash()))
-        return {"bound": "alu", "achieved": ach_fp32, "peak": peak_fp32, "unit": "Gop/s",
-                "frac": ach_fp32 / peak_fp32, "traffic": traffic,
+        roof = pipe_roofline(alg_fp32, alg_sfu, fwd_avg, measured_peaks(self.gg, self.dev), sm_mhz)
+        return {**roof, "traffic": traffic,
                 "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
                 "algorithmic_fp32_ops_per_launch": alg_fp32,
-                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
-                              "(SM clock sampled during the kernel's timing)",
-                "sfu": {"achieved": ach_sfu, "peak": peak_sfu, "frac": ach_sfu / peak_sfu},
+                "algorithmic_sfu_ops_per_launch": alg_sfu,
                 "hbm_gbs": x_bytes / (fwd_avg * 1e-3) / 1e9,
                 "eager_ms_per_step": eager_ms / steps, "clocks": ck}
 
@@ -524,16 +558,13 @@ def run_extra_mode(a, gg, torch):
         adj_ms, launches = ds.profile_read()
         adj_avg = adj_ms / max(launches, 1)
         sm_mhz = (ck or {}).get("sm_mhz") or 1477.0
-        peak_fp32 = SMS * FP32_LANES * sm_mhz * 1e6 / 1e9
-        peak_sfu = SMS * SFU_LANES * sm_mhz * 1e6 / 1e9
+        roof = pipe_roofline(alg_fp32, alg_sfu, adj_avg, measured_peaks(gg, dev), sm_mhz)
         line["roofline"] = {
-            "bound": "alu", "kernel": "adjoint_kernel (forward recompute + reverse sweep)",
-            "kernel_ms": adj_avg, "unit": "Gop/s",
-            "achieved": alg_fp32 / (adj_avg * 1e-3) / 1e9, "peak": peak_fp32,
-            "frac": alg_fp32 / (adj_avg * 1e-3) / 1e9 / peak_fp32,
-            "sfu": {"achieved": alg_sfu / (adj_avg * 1e-3) / 1e9, "peak": peak_sfu,
-                    "frac": alg_sfu / (adj_avg * 1e-3) / 1e9 / peak_sfu},
-            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz",
+            **roof, "kernel": "adjoint (bin + one launch per length class: forward recompute + "
+                              "reverse sweep)",
+            "kernel_ms": adj_avg,
+            "algorithmic_fp32_ops_per_launch": alg_fp32,
+            "algorithmic_sfu_ops_per_launch": alg_sfu,
             "traffic": None, "clocks": ck}
 
         def step(t):

@@ -271,6 +271,53 @@ __device__ __forceinline__ void store_rows(float* __restrict__ p, const float (&
     reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// A lane's R rows in a shared-memory row array (a tile's feature row, a
+// stack slot): R consecutive rows for R <= 4; for R = 8 two runs of 4
+// consecutive rows, 128 rows apart, the lanes 4 rows apart.  A warp's
+// 16-byte access then covers 512 contiguous bytes without bank conflicts
+// (8 consecutive rows per lane put the lanes 32 bytes apart, and every
+// access conflicted two ways: 44 % of the forward kernel's shared-memory
+// wavefronts on 4,096 x h4 over 100,000 rows).
+template <int R>
+constexpr int LANE_STRIDE = R == 8 ? 4 : R;  // rows between neighbouring lanes
+template <int R>
+__host__ __device__ constexpr int row_of(int r) {  // row offset of the lane's r-th row
+  return R == 8 ? (r >> 2) * 128 + (r & 3) : r;
+}
+template <int R>
+constexpr int LANE_EXTENT = row_of<R>(R - 1) + 1;  // rows spanned from the lane's first
+
+template <int R>
+__device__ __forceinline__ void load_lane(const float* __restrict__ p, float (&v)[R]) {
+  if constexpr (R == 8) {
+    float a[4], b[4];
+    load_rows<4>(p, a);
+    load_rows<4>(p + 128, b);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[r] = a[r];
+      v[4 + r] = b[r];
+    }
+  } else {
+    load_rows<R>(p, v);
+  }
+}
+template <int R>
+__device__ __forceinline__ void store_lane(float* __restrict__ p, const float (&v)[R]) {
+  if constexpr (R == 8) {
+    float a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r] = v[r];
+      b[r] = v[4 + r];
+    }
+    store_rows<4>(p, a);
+    store_rows<4>(p + 128, b);
+  } else {
+    store_rows<R>(p, v);
+  }
+}
+
 // Bounds of the checked build (GGEVAL_CHECKED): a lane's stack slots and
 // the tile's feature rows.  Every stack and feature access of the C++
 // interpreter is tested first; an access outside records ST_CHECKED in the
@@ -288,7 +335,7 @@ static __device__ __noinline__ void record_violation(unsigned* status) {
 }
 #ifdef GGEVAL_CHECKED
 #define GG_IN(ptr, lo, hi)                                                          \
-  (cb && !((ptr) >= cb->lo && (ptr) + R <= cb->hi) ? (record_violation(cb->status), \
+  (cb && !((ptr) >= cb->lo && (ptr) + LANE_EXTENT<R> <= cb->hi) ? (record_violation(cb->status), \
                                                       const_cast<float*>(cb->lo))  \
                                                    : (ptr))
 #else
@@ -331,13 +378,13 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     // load without a push exactly there), so it is peeled off the switch
     const uint2 first = prog[0];
     if ((PRESCALED ? first.x : first.x & 0xffu) == I_LDF0) {
-      load_rows<R>(GG_IN(PRESCALED ? feature_at(xs, first.y) : xs + (first.x >> 8) * ts,
+      load_lane<R>(GG_IN(PRESCALED ? feature_at(xs, first.y) : xs + (first.x >> 8) * ts,
                          feat_lo, feat_hi), A);
     } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = __uint_as_float(first.y);
     }
-    if constexpr (TAPE) store_rows<R>(tape, A);
+    if constexpr (TAPE) store_lane<R>(tape, A);
   }
   uint2 ins = prog[1];
   for (int k = 1; k < L; ++k) {
@@ -354,7 +401,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;
 #define GG_BIN_AT(kd, off)                                                  \
   case I_BF + kd + (off):                                                \
-    load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
+    load_lane<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
     binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_BC + kd + (off):                                                \
@@ -362,7 +409,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     binop_rows<kd, R>(A, t, A);                                       \
     break;                                                            \
   case I_LF + kd + (off):                                                \
-    load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
+    load_lane<R>(GG_IN(xf, feat_lo, feat_hi), t);                     \
     binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_LC + kd + (off):                                                \
@@ -371,24 +418,24 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
     break;                                                            \
   case I_BS + kd + (off):                                                \
     sp -= SLOT;                                                       \
-    load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
+    load_lane<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
     binop_rows<kd, R>(t, A, A);                                       \
     break;                                                            \
   case I_RS + kd + (off):                                                \
     sp -= SLOT;                                                       \
-    load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
+    load_lane<R>(GG_IN(sp, stk_lo, stk_hi), t);                       \
     binop_rows<kd, R>(A, t, A);                                       \
     break;
 
 #define GG_BIN(kd) GG_BIN_AT(kd, 0u)
     switch (opc) {
       case I_PSF:
-        store_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
+        store_lane<R>(GG_IN(sp, stk_lo, stk_hi), A);
         sp += SLOT;
-        load_rows<R>(GG_IN(xf, feat_lo, feat_hi), A);
+        load_lane<R>(GG_IN(xf, feat_lo, feat_hi), A);
         break;
       case I_PSC:
-        store_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
+        store_lane<R>(GG_IN(sp, stk_lo, stk_hi), A);
         sp += SLOT;
         GG_ROWS A[r] = c;
         break;
@@ -428,7 +475,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
           switch (opc) {
             case I_PW + 0:
             case I_BF + K_DIV:
-              load_rows<R>(GG_IN(xf, feat_lo, feat_hi), t);
+              load_lane<R>(GG_IN(xf, feat_lo, feat_hi), t);
               break;
             case I_PW + 1:
             case I_BC + K_DIV:
@@ -437,7 +484,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
             case I_PW + 2:
             case I_LF + K_DIV:
               GG_ROWS t[r] = A[r];
-              load_rows<R>(GG_IN(xf, feat_lo, feat_hi), A);
+              load_lane<R>(GG_IN(xf, feat_lo, feat_hi), A);
               break;
             case I_PW + 3:
             case I_LC + K_DIV:
@@ -450,12 +497,12 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
             case I_BS + K_DIV:
               sp -= SLOT;
               GG_ROWS t[r] = A[r];
-              load_rows<R>(GG_IN(sp, stk_lo, stk_hi), A);
+              load_lane<R>(GG_IN(sp, stk_lo, stk_hi), A);
               break;
             case I_PWR:
             case I_RS + K_DIV:
               sp -= SLOT;
-              load_rows<R>(GG_IN(sp, stk_lo, stk_hi), t);
+              load_lane<R>(GG_IN(sp, stk_lo, stk_hi), t);
               break;
             default:  // the packer emits only the opcodes above
               __builtin_unreachable();
@@ -474,7 +521,7 @@ __device__ __forceinline__ void run_program(const uint2* __restrict__ prog, int 
 #undef GG_UN
 #undef GG_BIN
 #undef GG_BIN_AT
-    if constexpr (TAPE) store_rows<R>(tape + 32 * R * k, A);
+    if constexpr (TAPE) store_lane<R>(tape + 32 * R * k, A);
     ins = nxt;
   }
 }
@@ -645,7 +692,7 @@ __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R
         const float* xf = feature_at(xs, arg);
         switch (code) {
           case I_PW + 0:  // A = pow(A, X[f])
-            load_rows<R>(xf, t);
+            load_lane<R>(xf, t);
             break;
           case I_PW + 1:  // A = pow(A, c)
 #pragma unroll
@@ -654,7 +701,7 @@ __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R
           case I_PW + 2:  // A = pow(X[f], A)
 #pragma unroll
             for (int r = 0; r < R; ++r) t[r] = A[r];
-            load_rows<R>(xf, A);
+            load_lane<R>(xf, A);
             break;
           case I_PW + 3:  // A = pow(c, A)
 #pragma unroll
@@ -667,11 +714,11 @@ __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R
             sp -= SLOTB;
 #pragma unroll
             for (int r = 0; r < R; ++r) t[r] = A[r];
-            load_rows<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), A);
+            load_lane<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), A);
             break;
           default:  // I_PWR: A = pow(A, pop)
             sp -= SLOTB;
-            load_rows<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), t);
+            load_lane<R>(static_cast<const float*>(__cvta_shared_to_generic(sp)), t);
             break;
         }
 #pragma unroll 1

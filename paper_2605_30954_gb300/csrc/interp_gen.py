@@ -163,6 +163,9 @@ class Gen:
         self.NP = R // 2          # row pairs per lane
         self.NQ = R // 4          # 16-byte shared-memory accesses per row group
         self.SLOTB = 32 * R * 4   # bytes per stack slot (32 lanes x R rows)
+        # a lane's rows (device.cuh row_of): 8 rows as two runs of 4, 128
+        # rows (512 bytes) apart
+        self.QOFF = 512 if R == 8 else 16
         self.lines = []
         # asm operands: %0 pc, %1 sp, %2 code, %3 arg, %4.. A[0..R-1], then
         # (with tape) the tape address, then xs
@@ -179,11 +182,13 @@ class Gen:
     # -- shared-memory row groups -------------------------------------------
     def load(self, dst, addr):
         for q in range(self.NQ):
-            self.o(f"ld.shared.v2.b64 {{{dst}{2 * q}, {dst}{2 * q + 1}}}, [{addr}+{16 * q}];")
+            self.o(f"ld.shared.v2.b64 {{{dst}{2 * q}, {dst}{2 * q + 1}}}, "
+                   f"[{addr}+{self.QOFF * q}];")
 
     def store(self, src, addr):
         for q in range(self.NQ):
-            self.o(f"st.shared.v2.b64 [{addr}+{16 * q}], {{{src}{2 * q}, {src}{2 * q + 1}}};")
+            self.o(f"st.shared.v2.b64 [{addr}+{self.QOFF * q}], "
+                   f"{{{src}{2 * q}, {src}{2 * q + 1}}};")
 
     def const_pairs(self, dst):
         self.o(f"mov.b64 {dst}0, {{arg, arg}};")

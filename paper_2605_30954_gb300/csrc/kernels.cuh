@@ -48,9 +48,11 @@ __host__ __device__ inline size_t pack_warp_bytes(int stride) {
 // pass (a shift that keeps the sums well conditioned).  The warp combines
 // its lanes' sums in double-float arithmetic and writes one partial record
 // {c, S_d, S_dd, S_dy, max|f|} per (trial, tile), the sums as FP32 (hi, lo)
-// pairs; fin_kernel merges them in FP64.  (Section 3.2 accumulates squared errors per thread in registers
-// and reduces them per block; here the tile of rows is shared by many
-// trials so X is read from HBM once per group instead of once per trial.)
+// pairs; fin_kernel merges them in double-float arithmetic and forms the
+// fitness from the merged sums in FP64.  (Section 3.2 accumulates squared
+// errors per thread in registers and reduces them per block; here the tile
+// of rows is shared by many trials so X is read from HBM once per group
+// instead of once per trial.)
 struct FwdParams {
   const float* X;      // [F + 1][ldx]: features, then centred target
   int N, F, ldx;
@@ -72,7 +74,8 @@ struct FwdParams {
 };
 
 // partial record of one (trial, tile): the shift c, (hi, lo) of S_d, S_dd and
-// S_dy, and max |f|, all FP32; the finaliser combines them in FP64
+// S_dy, and max |f|, all FP32; the finaliser merges them in double-float
+// arithmetic
 constexpr int NPART = 8;
 
 // two tile buffers, one stack of `slots` x 32 lanes x R floats per warp, one
@@ -91,7 +94,7 @@ __device__ __forceinline__ void accumulate_exact(const float (&A)[R], const floa
                                                  float& s2l, float& s3h, float& s3l, float& fm) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const bool ok = !MASK || r < valid;
+    const bool ok = !MASK || row_of<R>(r) < valid;
     const float d = ok ? A[r] - cs : 0.f;
     fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
     acc_add(s1h, s1l, d);
@@ -114,7 +117,8 @@ __device__ __forceinline__ void accumulate_grouped(const float (&A)[R], const fl
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
       float2 d = __fadd2_rn(make_float2(A[2 * i], A[2 * i + 1]), nc);
-      const bool ok0 = !MASK || 2 * i < valid, ok1 = !MASK || 2 * i + 1 < valid;
+      const bool ok0 = !MASK || row_of<R>(2 * i) < valid,
+                 ok1 = !MASK || row_of<R>(2 * i + 1) < valid;
       if constexpr (MASK) {
         d.x = ok0 ? d.x : 0.f;
         d.y = ok1 ? d.y : 0.f;
@@ -128,7 +132,7 @@ __device__ __forceinline__ void accumulate_grouped(const float (&A)[R], const fl
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const bool ok = !MASK || r < valid;
+      const bool ok = !MASK || row_of<R>(r) < valid;
       const float d = ok ? A[r] - cs : 0.f;
       fm = fmaxf(fm, ok ? fabsf(A[r]) : 0.f);
       m1.x += d;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
   const int n_items = p.count ? p.n_tiles * ((P + group - 1) / group) : p.n_items;
   float* xsb = reinterpret_cast<float*>(smem);  // two tile buffers
   float* stacks = xsb + 2 * tile_floats;
-  float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * R;  // this lane, slot 0
+  float* stk = stacks + (size_t)warp * p.slots * 32 * R + lane * LANE_STRIDE<R>;  // slot 0
   uint2* progs = reinterpret_cast<uint2*>(stacks + (size_t)nw * p.slots * 32 * R);
   uint2* wprog = progs + (size_t)warp * (p.lstride + 1);
   uint64_t* bar = reinterpret_cast<uint64_t*>(progs + (size_t)nw * (p.lstride + 1));
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       float2 m1 = make_float2(0.f, 0.f), m2 = m1, m3 = m1;
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
-        const int r0 = ps * RPP + lane * R;
+        const int r0 = ps * RPP + lane * LANE_STRIDE<R>;  // the lane's first row (row_of)
 #ifdef GG_INTERP_CXX
         const Checks cb{stk, stk + (size_t)p.slots * 32 * R, xs + r0,
                         xs + r0 + (size_t)p.F * p.tile_rows, p.status};
@@ -325,24 +329,24 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
 #else
         run_program_fast<R, POW>(wprog, xs + r0, A, stk);
 #endif
-        const int valid = nrows - r0;  // rows of this lane inside the tile
+        const int valid = nrows - r0;  // the lane's row r is inside the tile if row_of(r) < valid
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            if (r < valid) out[r] = A[r];
+            if (row_of<R>(r) < valid) out[row_of<R>(r)] = A[r];
         }
         if (ps == 0) {  // shift: mean of f over the first pass's rows
           float sm = 0.f;
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            if (r < valid) sm += A[r];
+            if (row_of<R>(r) < valid) sm += A[r];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
           cs = sm / (float)min(nrows, RPP);
         }
         float yv[R];
-        load_rows<R>(xs + (size_t)p.F * p.tile_rows + r0, yv);
+        load_lane<R>(xs + (size_t)p.F * p.tile_rows + r0, yv);
         const bool full = (ps + 1) * RPP <= nrows;
         if constexpr (EXACT) {
           if (full)
@@ -390,8 +394,9 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
 }
 
 // ------------------------------------------------------------- finaliser
-// Merge the per-tile partial sums of every trial in FP64 (fixed order, so
-// the result is deterministic) and turn them into a*, b*, smse and mse.
+// Merge the per-tile partial sums of every trial in double-float arithmetic
+// (fixed order, so the result is deterministic) and turn the merged sums,
+// in FP64, into a*, b*, smse and mse.
 // With d = f - c* (c* the first tile's shift) and yc = y - mean(y):
 //   var_N = S_dd - S_d^2/N,  cov_N = S_dy - S_d S_yc/N,  b* = cov_N/var_N,
 //   smse  = (Syy_N - b* cov_N)/N   (the least-squares residual, Eq. 1 with

@@ -410,16 +410,21 @@ def pack_host(op, cval, index, heights=None, layout=LAYOUT_HEAP, n_features=223)
 class ScaledMSE(torch.autograd.Function):
     """Scaled MSE of every trial as a differentiable function of cval.
 
-    forward runs ggeval_grad_batch (fitness and adjoint in one call) and
-    keeps the gradient; backward scales it by the incoming gradient."""
+    forward evaluates the fitness only (ggeval_eval_batch); backward runs
+    the adjoint (ggeval_grad_batch, which evaluates the trials again on the
+    way), so the adjoint costs nothing unless a gradient is asked for."""
 
     @staticmethod
     def forward(ctx, cval, op, dataset, heights=None, layout=LAYOUT_HEAP, flags=0):
-        smse, dc = dataset.grad_batch(op, cval.detach().contiguous(), heights, layout, flags)
-        ctx.save_for_backward(dc)
+        c = cval.detach().contiguous()
+        smse = dataset.eval_batch(op, c, heights, layout, flags,
+                                  want=(True, False, False, False))[0]
+        ctx.save_for_backward(c, op)
+        ctx.dataset, ctx.heights, ctx.layout, ctx.flags = dataset, heights, layout, flags
         return smse
 
     @staticmethod
     def backward(ctx, g):
-        (dc,) = ctx.saved_tensors
+        c, op = ctx.saved_tensors
+        _, dc = ctx.dataset.grad_batch(op, c, ctx.heights, ctx.layout, ctx.flags)
         return dc * g[:, None], None, None, None, None, None
