@@ -322,13 +322,23 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * LANE_STRIDE<R>;  // the lane's first row (row_of)
+        // The kernels built with pow run the C++ interpreter: pow is a
+        // library call, and the PTX interpreter leaves its statement for
+        // every pow instruction (on the Table 2 set 0.3 exits per trial and
+        // pass, 1.75 ms per step against 1.24 ms with the C++ switch).  The
+        // checked build runs it everywhere (its bounds checks are C++).
 #ifdef GG_INTERP_CXX
-        const Checks cb{stk, stk + (size_t)p.slots * 32 * R, xs + r0,
-                        xs + r0 + (size_t)p.F * p.tile_rows, p.status};
-        run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk, nullptr, &cb);
+        constexpr bool CXX = true;
 #else
-        run_program_fast<R, POW>(wprog, xs + r0, A, stk);
+        constexpr bool CXX = POW;
 #endif
+        if constexpr (CXX) {
+          const Checks cb{stk, stk + (size_t)p.slots * 32 * R, xs + r0,
+                          xs + r0 + (size_t)p.F * p.tile_rows, p.status};
+          run_program<R, false, true, POW>(wprog, L, xs + r0, p.tile_rows, A, stk, nullptr, &cb);
+        } else {
+          run_program_fast<R, POW>(wprog, xs + r0, A, stk);
+        }
         const int valid = nrows - r0;  // the lane's row r is inside the tile if row_of(r) < valid
         if constexpr (ROWS) {
           float* out = p.rows_out + (size_t)trial * p.N + row0 + r0;
