@@ -276,7 +276,8 @@ ggeval_status ggeval_tuning_load(ggeval_dataset* ds, const char* path, int32_t* 
  * rows per tile, trials per work item, warps per CTA}.  variant: 0 = 8
  * rows per lane with grouped sums, 1 = 4 rows per lane grouped, 2 = 4 rows
  * per lane with per-row error-free sums, 4..6 = 0..2 built for at most 64
- * registers.  With `set` non-NULL the given configuration is checked (it
+ * registers, 8 and 9 = 0 and 5 running the C++ interpreter instead of the
+ * PTX one (the same results).  With `set` non-NULL the given configuration is checked (it
  * must fit in shared memory; rows per tile a multiple of 32 x rows per
  * lane) and kept for such batches, as ggeval_autotune keeps its choice;
  * with `get` non-NULL the configuration in force is written there.  The

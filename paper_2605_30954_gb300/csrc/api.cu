@@ -1114,7 +1114,8 @@ ggeval_status ggeval_autotune(ggeval_dataset* ds, const ggeval_batch* b, uint32_
   const Cfg base = default_cfg(ds, b->n, b->max_height, flags);
   std::vector<int> variants;
   if (base.variant == 2) variants = {2, 6};
-  else variants = {5, 1, 4, 0};
+  else if (flags & GGEVAL_F_POW) variants = {5, 1, 4, 0};
+  else variants = {5, 1, 4, 0, 8, 9};  // 8, 9: the C++ interpreter
   std::vector<Cfg> cands;
   for (int v : variants)
     for (int warps : {8, 16, 20, 24, 28})

@@ -108,24 +108,55 @@ static __device__ __noinline__ float sincos_library(float x, int shift) {
 // The row-by-row forms for a group of rows of which some lie outside the
 // own-math forms' common domain: out of line, with rolled loops, so that the
 // interpreter's switch stays compact and this cold code holds few registers
-// (the caller saves the ones it clobbers around the call).
+// (the caller saves the ones it clobbers around the call).  The rows go in
+// and out by value (ColdRows): passed by reference, the caller's row array
+// had its address taken and could no longer live in registers, which made
+// the C++ interpreter 1.3x (FOS-step) to 1.7x (largest workload) slower.
 template <int R>
-__device__ __noinline__ void sincos_special(float (&A)[R], int shift) {
+__device__ __noinline__ ColdRows<R> sincos_special_v(ColdRows<R> a, int shift) {
 #pragma unroll 1
   for (int r = 0; r < R; ++r) {
-    const float x = A[r];
-    A[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
+    const float x = a.v[r];
+    a.v[r] = fabsf(x) <= TRIG_RANGE ? sin_or_cos_reduced(x, shift) : sincos_library(x, shift);
   }
+  return a;
 }
 template <int R, bool LOG>
-__device__ __noinline__ void logsqrt_special(float (&A)[R]) {
+__device__ __noinline__ ColdRows<R> logsqrt_special_v(ColdRows<R> a) {
 #pragma unroll 1
-  for (int r = 0; r < R; ++r) A[r] = LOG ? log_total(__float_as_uint(A[r])) : sqrt_total(A[r]);
+  for (int r = 0; r < R; ++r)
+    a.v[r] = LOG ? log_total(__float_as_uint(a.v[r])) : sqrt_total(a.v[r]);
+  return a;
 }
 template <int R>
-__device__ __noinline__ void exp_special(float (&A)[R]) {
+__device__ __noinline__ ColdRows<R> exp_special_v(ColdRows<R> a) {
 #pragma unroll 1
-  for (int r = 0; r < R; ++r) A[r] = exp_total(A[r]);
+  for (int r = 0; r < R; ++r) a.v[r] = exp_total(a.v[r]);
+  return a;
+}
+template <int R>
+__device__ __forceinline__ ColdRows<R> to_cold(const float (&A)[R]) {
+  ColdRows<R> t;
+#pragma unroll
+  for (int r = 0; r < R; ++r) t.v[r] = A[r];
+  return t;
+}
+template <int R>
+__device__ __forceinline__ void from_cold(float (&A)[R], const ColdRows<R>& t) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) A[r] = t.v[r];
+}
+template <int R>
+__device__ __forceinline__ void sincos_special(float (&A)[R], int shift) {
+  from_cold(A, sincos_special_v<R>(to_cold(A), shift));
+}
+template <int R, bool LOG>
+__device__ __forceinline__ void logsqrt_special(float (&A)[R]) {
+  from_cold(A, logsqrt_special_v<R, LOG>(to_cold(A)));
+}
+template <int R>
+__device__ __forceinline__ void exp_special(float (&A)[R]) {
+  from_cold(A, exp_special_v<R>(to_cold(A)));
 }
 
 // sin and cos on the R rows of a lane: the branch-free form of gmath.cuh,
@@ -661,9 +692,16 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 // domain (row by row; the 4-row PTX finishes exp, log and sqrt itself), and
 // pow.  Out of line: the rare cases stay off the hot loop's instruction
 // stream.
+template <int R>
+struct ColdState {
+  float a[R];
+  uint32_t sp;
+};
 template <int R, bool POW>
-__device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R],
-                                       uint32_t& sp, const float* xs) {
+__device__ __noinline__ ColdState<R> exec_cold_v(uint32_t code, uint32_t arg, ColdState<R> st,
+                                                 const float* xs) {
+  float (&A)[R] = st.a;
+  uint32_t& sp = st.sp;
   constexpr uint32_t SLOTB = 32 * R * 4;
   switch (code) {
     case I_UN + U_SIN:
@@ -726,6 +764,21 @@ __device__ __noinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R
       }
       break;
   }
+  return st;
+}
+// exec_cold_v with the rows and the stack pointer copied in and out by value
+// (the caller's registers keep them; see the row-by-row forms above)
+template <int R, bool POW>
+__device__ __forceinline__ void exec_cold(uint32_t code, uint32_t arg, float (&A)[R],
+                                          uint32_t& sp, const float* xs) {
+  ColdState<R> st;
+#pragma unroll
+  for (int r = 0; r < R; ++r) st.a[r] = A[r];
+  st.sp = sp;
+  st = exec_cold_v<R, POW>(code, arg, st, xs);
+#pragma unroll
+  for (int r = 0; r < R; ++r) A[r] = st.a[r];
+  sp = st.sp;
 }
 
 // Run a staged program (words as run_program's PRESCALED form, a NOP after

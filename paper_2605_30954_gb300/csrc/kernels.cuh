@@ -219,7 +219,7 @@ __device__ __forceinline__ void produce_tile(const FwdParams& p, int n_items, in
 // -> 28 warps per SM each gained 1 to 8 % per step, the register caps cost
 // nothing measurable.
 constexpr int fwd_max_threads(int minb) { return minb == 1 ? 896 : 512; }
-template <int R, bool EXACT, bool ROWS, int MINB, bool POW>
+template <int R, bool EXACT, bool ROWS, int MINB, bool POW, bool CXXI = false>
 __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -322,15 +322,19 @@ __global__ void __launch_bounds__(fwd_max_threads(MINB), MINB) fwd_kernel(const 
       float cs = 0.f;
       for (int ps = 0; ps < npass; ++ps) {
         const int r0 = ps * RPP + lane * LANE_STRIDE<R>;  // the lane's first row (row_of)
-        // The kernels built with pow run the C++ interpreter: pow is a
-        // library call, and the PTX interpreter leaves its statement for
-        // every pow instruction (on the Table 2 set 0.3 exits per trial and
-        // pass, 1.75 ms per step against 1.24 ms with the C++ switch).  The
-        // checked build runs it everywhere (its bounds checks are C++).
+        // The C++ interpreter runs in the CXXI variants (the autotuner
+        // weighs them against the PTX ones: the compare tree costs more
+        // instructions per dispatch, the indirect branch more stalls, and
+        // short programs favour the tree) and in the kernels built with pow:
+        // pow is a library call, and the PTX interpreter leaves its
+        // statement for every pow instruction (on the Table 2 set 0.3 exits
+        // per trial and pass, 1.75 ms per step against 1.54 ms with the
+        // C++ switch).  The checked build runs it everywhere (its bounds
+        // checks are C++).
 #ifdef GG_INTERP_CXX
         constexpr bool CXX = true;
 #else
-        constexpr bool CXX = POW;
+        constexpr bool CXX = POW || CXXI;
 #endif
         if constexpr (CXX) {
           const Checks cb{stk, stk + (size_t)p.slots * 32 * R, xs + r0,
@@ -438,12 +442,15 @@ constexpr int FIN_WARPS = 16;  // trials per finaliser block
 // Kernel pointers: variant 0 = 8 rows/lane grouped sums, 1 = 4 rows/lane
 // grouped sums, 2 = 4 rows/lane exact sums, 3 = variant 2 writing per-row values;
 // variants 4, 5, 6 = variants 0, 1, 2 compiled for at most 64 registers;
-// 7 = variant 0 writing per-row values.  The per-row variants run the same
-// interpreter code as the variants with the same rows per lane.
+// 7 = variant 0 writing per-row values; 8, 9 = variants 0 and 5 with the C++
+// interpreter instead of the PTX one, 10, 11 = their per-row builds (in the
+// kernels with pow, which run the C++ interpreter throughout, 8..11 are
+// 0, 5, 7, 3).  The per-row variants run the same interpreter code as the
+// variants with the same rows per lane.
 // fwd.cu holds the table of the kernels without pow, fwd_pow.cu the kernels
 // that also run pow instructions (kept apart because the pow code costs the
 // other kernels registers and instruction-cache locality).
-constexpr int NVARIANT = 8;
+constexpr int NVARIANT = 12;
 template <bool P>
 const void* fwd_table(int variant) {
   switch (variant) {
@@ -455,17 +462,28 @@ const void* fwd_table(int variant) {
     case 5: return reinterpret_cast<const void*>(&fwd_kernel<4, false, false, 2, P>);
     case 6: return reinterpret_cast<const void*>(&fwd_kernel<4, true, false, 2, P>);
     case 7: return reinterpret_cast<const void*>(&fwd_kernel<8, false, true, 1, P>);
+    case 8: return reinterpret_cast<const void*>(&fwd_kernel<8, false, false, 1, P, !P>);
+    case 9: return reinterpret_cast<const void*>(&fwd_kernel<4, false, false, 2, P, !P>);
+    case 10: return reinterpret_cast<const void*>(&fwd_kernel<8, false, true, 1, P, !P>);
+    case 11: return reinterpret_cast<const void*>(&fwd_kernel<4, true, true, 1, P, !P>);
     default: return nullptr;
   }
 }
 const void* fwd_ptr_plain(int variant);
 const void* fwd_ptr_pow(int variant);
-inline int variant_rows(int v) { return (v == 0 || v == 4 || v == 7) ? 8 : 4; }
-// the variant that also writes per-row values, with v's rows per lane
-inline int rows_variant(int v) { return variant_rows(v) == 8 ? 7 : 3; }
+inline int variant_rows(int v) { return (v == 0 || v == 4 || v == 7 || v == 8 || v == 10) ? 8 : 4; }
+// the variant that also writes per-row values, with v's rows per lane and
+// interpreter
+inline int rows_variant(int v) {
+  if (v == 8 || v == 10) return 10;
+  if (v == 9 || v == 11) return 11;
+  return variant_rows(v) == 8 ? 7 : 3;
+}
 // variants a caller may choose for the fitness path (no per-row output)
-inline bool fitness_variant(int v) { return v >= 0 && v < 7 && v != 3; }
-inline int variant_max_warps(int v) { return fwd_max_threads(v >= 4 && v <= 6 ? 2 : 1) / 32; }
-inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6; }
+inline bool fitness_variant(int v) { return (v >= 0 && v < 7 && v != 3) || v == 8 || v == 9; }
+inline int variant_max_warps(int v) {
+  return fwd_max_threads((v >= 4 && v <= 6) || v == 9 ? 2 : 1) / 32;
+}
+inline bool variant_exact(int v) { return v == 2 || v == 3 || v == 6 || v == 11; }
 
 }  // namespace gg
