@@ -398,7 +398,7 @@ __device__ __forceinline__ void run_program_tape(const uint2* prog, const float*
 // the form reads (a V entry or the feature's row in the tile; unused ones
 // point at V's first entry); w = the constant's bits.  The PTX sweep
 // (interp_rev_asm, generated by interp_gen.py) runs the forms of +, -, *,
-// AQ, the pushed ERC, square, log and sqrt; rev_cold runs every form (the
+// AQ, the pushed ERC, square, log and sqrt; rev_cold_v runs every form (the
 // PTX leaves it sin, cos, exp, division and pow).
 enum : uint32_t {
   RV_CONST = 0,       // a pushed ERC: its adjoint is the ERC's contribution
@@ -474,11 +474,20 @@ __device__ __forceinline__ void rev_bin(const float (&g)[R], const float (&u)[R]
 }
 
 // One descriptor in C++: every form (the PTX sweep leaves it the forms it
-// does not run).  g is the carried adjoint G, or V's entry (GSM).
+// does not run).  g is the carried adjoint G, or V's entry (GSM).  G goes
+// in and out by value and the valid rows as a bit mask, so the caller's
+// arrays keep their registers (nothing of theirs has its address taken).
 template <bool POW>
-__device__ __noinline__ void rev_cold(const uint4 d, float (&G)[4], unsigned char* wl,
-                                      const float* V, float* pel, const bool (&valid)[4]) {
+__device__ __noinline__ ColdRows<4> rev_cold_v(const uint4 d, ColdRows<4> gin, unsigned char* wl,
+                                               const float* V, float* pel, uint32_t vmask) {
   constexpr int R = 4;
+  float G[R];
+  bool valid[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    G[r] = gin.v[r];
+    valid[r] = (vmask >> r) & 1u;
+  }
   float g[R], u[R], v[R];
   if (d.x & RV_GSM) {
     load_rows<R>(V + (size_t)(d.x >> 16) * 32 * R, g);
@@ -524,6 +533,10 @@ __device__ __noinline__ void rev_cold(const uint4 d, float (&G)[4], unsigned cha
       }
       break;
   }
+  ColdRows<4> gout;
+#pragma unroll
+  for (int r = 0; r < R; ++r) gout.v[r] = G[r];
+  return gout;
 }
 
 // The staged kernel (at most ADJ_FTILE_MAX features): per pass the lanes'
@@ -658,7 +671,12 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
           uint32_t code, dx, dy, dz, dw;
           interp_rev_asm(G, rp, cnt, code, dx, dy, dz, dw, wl32, wl32 + oV, pe32, rbase, vmask);
           if (code == 0) break;
-          rev_cold<POW>(make_uint4(dx, dy, dz, dw), G, wl, V, partl, valid);
+          ColdRows<4> gc;
+#pragma unroll
+          for (int r = 0; r < R; ++r) gc.v[r] = G[r];
+          gc = rev_cold_v<POW>(make_uint4(dx, dy, dz, dw), gc, wl, V, partl, vmask);
+#pragma unroll
+          for (int r = 0; r < R; ++r) G[r] = gc.v[r];
         }
       }
       __syncwarp();
