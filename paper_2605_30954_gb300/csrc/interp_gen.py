@@ -36,16 +36,15 @@ I_NOP, I_PW, I_COUNT = 42, 43, 49
 K_ADD, K_SUB, K_MUL, K_AQ, K_DIV = range(5)
 U_SIN, U_COS, U_EXP, U_LOG_ABS, U_SQRT_ABS, U_SQUARE, U_LOG, U_SQRT = range(8)
 
-# FP32 constants of gmath.cuh, as written there (decimal literals)
+# FP32 constants of gmath.cuh, as written there (decimal literals; SIN_C and
+# COS_C in Horner order, highest power first)
 TWO_OVER_PI = "0.636619746685028076"
 MAGIC = "12582912.0"
 PIO2_1 = "-1.57079637050628662"
 PIO2_2 = "4.37113882867379e-08"
 PIO2_3 = "1.71512451000588e-15"
-SIN_C = ("2.75573192239859e-06", "-1.98412698412698e-04", "8.33333333333333e-03",
-         "-1.66666666666667e-01")
-COS_C = ("-2.75573192239859e-07", "2.48015873015873e-05", "-1.38888888888889e-03",
-         "4.16666666666667e-02", "-0.5")
+SIN_C = ("-0.00019515285", "0.008332158", "-0.16666654")
+COS_C = ("2.4433153e-05", "-0.0013887319", "0.04166665", "-0.5")
 TRIG_RANGE = "131072.0"
 LN2_HI = "0.693147182464599609375"
 LN2_LO = "-1.9046542121259336e-09"
@@ -106,7 +105,7 @@ def sincos_pair(o, x, dst):
     o(f"mov.b64 c1, {f2(SIN_C[0])};")
     o(f"mov.b64 c2, {f2(SIN_C[1])};")
     o("fma.rn.f32x2 v4, v3, c1, c2;")                  # ps
-    for k in (2, 3):
+    for k in range(2, len(SIN_C)):
         o(f"mov.b64 c1, {f2(SIN_C[k])};")
         o("fma.rn.f32x2 v4, v3, v4, c1;")
     o("mul.rn.f32x2 v5, v2, v3;")                      # r s
@@ -114,7 +113,7 @@ def sincos_pair(o, x, dst):
     o(f"mov.b64 c1, {f2(COS_C[0])};")
     o(f"mov.b64 c2, {f2(COS_C[1])};")
     o("fma.rn.f32x2 v5, v3, c1, c2;")                  # pc
-    for k in (2, 3, 4):
+    for k in range(2, len(COS_C)):
         o(f"mov.b64 c1, {f2(COS_C[k])};")
         o("fma.rn.f32x2 v5, v3, v5, c1;")
     o(f"mov.b64 c1, {f2('1.0')};")
