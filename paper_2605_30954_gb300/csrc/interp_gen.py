@@ -86,7 +86,7 @@ def f2(s: str) -> str:
 def sincos_pair(o, x, dst):
     """gmath.cuh sin_or_cos_reduced2 on the pair x into dst (x is read
     before dst is written): the quadrant shift in sh (0 sin, 1 cos);
-    registers v0..v5, c1, c2, q0, q1, z0..z3, k, p."""
+    registers v0..v5, c1, c2, q0, q1, z0..z3, k, ks, p."""
     o(f"mov.b64 c1, {f2(TWO_OVER_PI)};")
     o(f"mov.b64 c2, {f2(MAGIC)};")
     o(f"fma.rn.f32x2 v0, {x}, c1, c2;")               # t
@@ -121,12 +121,12 @@ def sincos_pair(o, x, dst):
     o("mov.b64 {z0, z1}, v4;")
     o("mov.b64 {z2, z3}, v5;")
     for e in (0, 1):
-        o(f"and.b32 k, q{e}, 1;")
-        o("setp.ne.u32 p, k, 0;")
-        o(f"selp.b32 z{e}, z{2 + e}, z{e}, p;")
-        o(f"and.b32 k, q{e}, 2;")
-        o("shl.b32 k, k, 30;")
-        o(f"xor.b32 z{e}, z{e}, k;")
+        # the quadrant's bit 0 picks cos over sin (bit 0 moved to the sign
+        # for slct), bit 1 flips the sign (lop3: z ^ (k & 0x80000000))
+        o(f"shl.b32 ks, q{e}, 31;")
+        o(f"slct.b32.s32 z{e}, z{e}, z{2 + e}, ks;")
+        o(f"shl.b32 k, q{e}, 30;")
+        o(f"lop3.b32 z{e}, z{e}, k, 0x80000000, 0x78;")
     o(f"mov.b64 {dst}, {{z0, z1}};")
 
 
@@ -511,7 +511,7 @@ class Gen:
         o(f".reg .f32 x<{R}>, y<{R}>, w<2>, m;")
         o(f".reg .b32 z<4>, b<{R}>;")
         o(".reg .u32 opc, arg, nopc, narg, ad, sh, msk, k, q<2>, mm;")
-        o(".reg .s32 e<2>, ea, ee, kk;")
+        o(".reg .s32 e<2>, ea, ee, kk, ks;")
         o(".reg .f32 s<5>;")
         o(".reg .pred p;")
         for i in range(NP):
@@ -857,6 +857,7 @@ class RevGen:
         o(".reg .f32 r<4>, h<4>, s, cf, m;")
         o(".reg .u32 x, y, z, w, nx, ny, nz, nw, opc, ad, pa, kk, k, sh, q<2>;")
         o(".reg .b32 z<4>;")
+        o(".reg .s32 ks;")
         o(".reg .pred p, pv<4>;")
         o("mov.b64 g0, {%7, %8};")
         o("mov.b64 g1, {%9, %10};")
