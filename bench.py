@@ -85,12 +85,12 @@ PARITY_TRIALS = 64  # timed trials compared with the oracle per workload
 # capture, keyed by (workload, hash of the CUDA sources and the header at
 # the time of the capture); reported only while the sources still match
 NCU_TRAFFIC: dict = {
-    # dram__bytes_read.sum 182,445,056 + dram__bytes_write.sum 470,150,144: X and
-    # y from HBM (44 MB, re-read by later groups through L2) and the
+    # dram__bytes_read.sum 196,295,680 + dram__bytes_write.sum 487,198,720: X and
+    # y from HBM (44 MB, re-read by later trial groups through L2) and the
     # per-(trial, tile) partial records (16,384 x 977 x 32 B = 512 MB)
-    ("large-16384xh6-1000000x10", "009d43aace441aa5"): 652_595_200,
-    # 4,830,976 + 56,320: X, y and programs once; partial records stay in L2
-    ("fos-step-4096xh4-100000x8", "009d43aace441aa5"): 4_887_296,
+    ("large-16384xh6-1000000x10", "ed26ad3091a6e644"): 683_494_400,
+    # 4,984,320 + 2,560: X, y and programs once; partial records stay in L2
+    ("fos-step-4096xh4-100000x8", "ed26ad3091a6e644"): 4_986_880,
 }
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}
