@@ -34,8 +34,8 @@ struct AdjParams {
 
 // Length classes: program capacities (words, with the NOP) in increasing
 // order; a batch uses the ones below its lstride and lstride itself.
-constexpr int ADJ_NCLS_MAX = 12;
-constexpr int ADJ_CAPS[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+constexpr int ADJ_NCLS_MAX = 16;
+constexpr int ADJ_CAPS[] = {16, 24, 32, 40, 48, 56, 64, 80, 96, 128, 192, 256, 384, 512};
 
 struct AdjBinParams {
   const int* len;      // [P]
