@@ -82,15 +82,15 @@ OPS_REV_SFU = {"term": 0, "addsubmul": 0, "aq": 1, "div": 1, "sincos": 0, "exp":
 TUNE_STEPS = 20  # Adam steps of the constant-tuning report (grad mode)
 PARITY_TRIALS = 64  # timed trials compared with the oracle per workload
 # DRAM bytes (read + write) of one batched-forward launch from an ncu
-# capture, keyed by (workload, hash of the CUDA sources and the header at
-# the time of the capture); reported only while the sources still match
+# capture, keyed by (workload, hash of the forward kernel's sources at the
+# time of the capture, FWD_SOURCES); reported only while they still match
 NCU_TRAFFIC: dict = {
     # dram__bytes_read.sum 196,295,680 + dram__bytes_write.sum 487,198,720: X and
     # y from HBM (44 MB, re-read by later trial groups through L2) and the
     # per-(trial, tile) partial records (16,384 x 977 x 32 B = 512 MB)
-    ("large-16384xh6-1000000x10", "ed26ad3091a6e644"): 683_494_400,
+    ("large-16384xh6-1000000x10", "b35bfd2497ef5c82"): 683_494_400,
     # 4,984,320 + 2,560: X, y and programs once; partial records stay in L2
-    ("fos-step-4096xh4-100000x8", "ed26ad3091a6e644"): 4_986_880,
+    ("fos-step-4096xh4-100000x8", "b35bfd2497ef5c82"): 4_986_880,
 }
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}
@@ -99,14 +99,24 @@ EXEC_COLS = {"term": 14, "addsubmul": 15, "aq": 16, "div": 17, "sincos": 18, "ex
              "log": 20, "sqrt": 21, "square": 22, "pow": 23}
 
 
-def source_hash():
-    """Hash of the CUDA sources and the C header the library is built from."""
+# the sources the batched forward kernel is compiled from (its includes and
+# the generator of its PTX interpreter)
+FWD_SOURCES = ("kernels.cuh", "device.cuh", "gmath.cuh", "isa.h", "fwd.cu", "fwd_pow.cu",
+               "interp_gen.py")
+
+
+def source_hash(names=None):
+    """Hash of the CUDA sources and the C header the library is built from
+    (or of the named files of csrc/ only)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_30954_gb300", "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
-                   if f.endswith((".cu", ".cuh", ".h", ".py")))
-    files.append(os.path.join(ROOT, "include", "ggeval.h"))
+    if names is None:
+        files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
+                       if f.endswith((".cu", ".cuh", ".h", ".py")))
+        files.append(os.path.join(ROOT, "include", "ggeval.h"))
+    else:
+        files = [os.path.join(csrc, f) for f in names]
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
@@ -475,7 +485,7 @@ class Runner:
         alg_fp32 = (fp32_ops + ACC_FP32 * valid) * N  # per launch
         alg_sfu = sfu_ops * N
         x_bytes = (w["F"] + 1) * N * 4
-        traffic = NCU_TRAFFIC.get((w["name"], source_hash()))
+        traffic = NCU_TRAFFIC.get((w["name"], source_hash(FWD_SOURCES)))
         roof = pipe_roofline(alg_fp32, alg_sfu, fwd_avg, measured_peaks(self.gg, self.dev), sm_mhz)
         return {**roof, "traffic": traffic,
                 "kernel": "fwd_kernel (batched forward)", "kernel_ms": fwd_avg,
