@@ -240,10 +240,11 @@ def eval_tree_perturbed(t: Template, X: np.ndarray, rel: float, rng) -> np.ndarr
     return _eval(t, np.asarray(X), np.float64, perturb=(rel, rng))
 
 
-def condition_bound(t: Template, X: np.ndarray, rel: float) -> np.ndarray:
+def condition_bound(t: Template, X: np.ndarray, rel) -> np.ndarray:
     """First-order bound, per row, on how far the tree's value moves when the
     value of every function node carries a relative error of at most
-    ``rel``: rel * sum over function nodes n of |d f / d v_n| * |v_n|, with
+    ``rel`` (a number, or a mapping from opcode to that operator's relative
+    error): sum over function nodes n of rel_n * |d f / d v_n| * |v_n|, with
     the sensitivities d f / d v_n from an FP64 reverse sweep and |cos|, |sin|
     replaced by their bound 1 at sin and cos nodes (so a large argument is
     never hidden by a small local slope).  This is the forward error
@@ -253,6 +254,7 @@ def condition_bound(t: Template, X: np.ndarray, rel: float) -> np.ndarray:
     ill-conditioned (Section 5 of the paper notes FP32 error growth on such
     expressions).  Non-finite where any node value is non-finite."""
     X = np.asarray(X)
+    per_op = isinstance(rel, dict)
     vals = {}
     f = _eval(t, X, np.float64, store=vals)
     n = f.size
@@ -263,7 +265,7 @@ def condition_bound(t: Template, X: np.ndarray, rel: float) -> np.ndarray:
         o = int(t.op[pos])
         if o >= ERC:
             return
-        bound = bound + np.abs(adj * vals[pos])
+        bound = bound + (rel[o] if per_op else 1.0) * np.abs(adj * vals[pos])
         l, r = t.children(pos, depth)
         if o in BINARY:
             da, db = _dapply(o, vals[l], vals[r], vals[pos])
@@ -278,7 +280,7 @@ def condition_bound(t: Template, X: np.ndarray, rel: float) -> np.ndarray:
 
     with np.errstate(all="ignore"):
         back(0, 0, np.ones(n))
-        bound = np.where(np.isfinite(f), rel * bound, np.inf)
+        bound = np.where(np.isfinite(f), bound if per_op else rel * bound, np.inf)
         return np.where(np.isnan(bound), np.inf, bound)
 
 

@@ -366,16 +366,17 @@ FULL = {"c1": None, "c2": None, "c3": 512, "c4": None, "c5": 512, "t2": None}
 #: exclusion limits on the benchmark workloads: ill-conditioned trials and rows
 MAX_TRIAL_EXCL, MAX_ROW_EXCL = 0.02, 0.05
 #: workloads with more ill-conditioned trials: the Table 2 set's unprotected
-#: operators (plain division, log, sqrt, pow), and the gradient workload's
-#: ERC-dense trees of cancelling constants, where the worst-case error bound
-#: (a few FP32 roundings at each of some 30 function nodes, summed) exceeds
-#: half the tolerance on about 5 % of trials (the FP32 emulation itself stays
-#: within it); excluded trials are still held to the loose bound
-MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.08, "c4": 0.06}
+#: operators (plain division, log, sqrt, pow; 6.6 % of trials), and the
+#: gradient workload's ERC-dense trees of cancelling constants, where the
+#: worst-case error bound (each function node's rounding, summed over some 30
+#: nodes) exceeds half the tolerance on 2.4 % of trials (the FP32 emulation
+#: itself stays within it); excluded trials are still held to the loose bound
+MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.08, "c4": 0.03}
 #: the largest workload's height-6 trees (exp and sin chains, cancelling
-#: sums) leave about 15 % of their rows ill-conditioned in FP32; those rows
-#: are still held to the loose bound
-MAX_ROW_EXCL_BY_CFG = {"c5": 0.20}
+#: sums) leave about 11 % of their rows ill-conditioned in FP32 (a third of
+#: them through the FP32 emulation itself); those rows are still held to the
+#: loose bound
+MAX_ROW_EXCL_BY_CFG = {"c5": 0.13}
 
 
 def bench_config_eval(gg, ds, op, cv, hs, flags, P):
@@ -396,7 +397,7 @@ def test_full_size_config(gg, cfg):
     (C1, C2, C4, Table 2 set) or of 512 sampled trials (C3, C5) against the
     oracle, in the default launch configuration and in the benchmark's
     (autotuned, graph replay), with at most 2 % of trials excluded as
-    ill-conditioned in FP32 (8 % for the Table 2 set, 6 % for the gradient
+    ill-conditioned in FP32 (8 % for the Table 2 set, 3 % for the gradient
     workload)."""
     w = PA.build(cfg)
     P = w["P"]

@@ -447,6 +447,22 @@ def test_condition_bound_closed_forms():
                                rtol=1e-12)
 
 
+def test_condition_bound_per_operator_closed_form():
+    """The per-operator form: each function node carries its own relative
+    error, so exp(x0 * x1) gets rel_exp e + rel_mul e |x0 x1| (a mistake that
+    swapped the two, or used one for both, moves the bound)."""
+    rng, X = rand_xy(17)
+    rel = {O.MUL: 1e-7, O.EXP: 6e-7}
+    t = T(["exp", "*", None, "x0", "x1"], 2)
+    e = np.exp(X[:, 0] * X[:, 1])
+    np.testing.assert_allclose(O.condition_bound(t, X, rel),
+                               6e-7 * e + 1e-7 * e * np.abs(X[:, 0] * X[:, 1]), rtol=1e-12)
+    # a uniform number is the same as a table holding it for every operator
+    u = {k: 3e-7 for k in (O.MUL, O.EXP)}
+    np.testing.assert_allclose(O.condition_bound(t, X, u), O.condition_bound(t, X, 3e-7),
+                               rtol=1e-12)
+
+
 def test_eval_batch_matches_single():
     rng, X = rand_xy(11)
     y = X[:, 0] * 2
