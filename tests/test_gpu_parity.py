@@ -373,9 +373,9 @@ MAX_TRIAL_EXCL, MAX_ROW_EXCL = 0.02, 0.05
 #: itself stays within it); excluded trials are still held to the loose bound
 MAX_TRIAL_EXCL_BY_CFG = {"t2": 0.08, "c4": 0.03}
 #: the largest workload's height-6 trees (exp and sin chains, cancelling
-#: sums) leave about 11 % of their rows ill-conditioned in FP32 (a third of
-#: them through the FP32 emulation itself); those rows are still held to the
-#: loose bound
+#: sums) leave about 11 % of their rows ill-conditioned in FP32 (more than
+#: half of them because the FP32 emulation itself is beyond half the
+#: tolerance); those rows are still held to the loose bound
 MAX_ROW_EXCL_BY_CFG = {"c5": 0.13}
 
 
