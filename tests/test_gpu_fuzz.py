@@ -26,10 +26,12 @@ def gg():
     return pkg
 
 
-def random_case(seed):
+def random_case(seed, wide=False):
+    """wide: 17 to 28 features (the tile of many feature rows; the adjoint's
+    kernel that reads features from global memory), same draws otherwise."""
     rng = np.random.default_rng(1000 + seed)
     N = int(rng.choice([1, 7, 130, 1023, 1025, 2049, 5003]))
-    F = int(rng.integers(1, 13))
+    F = int(rng.integers(1, 13)) + (16 if wide else 0)
     h_max = int(rng.integers(0, 7))
     P = int(rng.integers(1, 97))
     funcs = tuple(rng.choice(ALL_FUNCS, size=int(rng.integers(2, len(ALL_FUNCS) + 1)),
@@ -46,12 +48,12 @@ def random_case(seed):
     mask = (rng.random(P) < 0.7).astype(np.uint8) if rng.random() < 0.5 else None
     flags_extra = int(rng.choice([0, 1, 2, 3]))  # bit 0: exact sums, bit 1: no folding
     # half the cases force a launch configuration: any fitness variant (8 or
-    # 4 rows per lane, grouped or exact sums, either register budget), tile,
-    # trials per work item and warps per CTA
+    # 4 rows per lane, grouped or exact sums, either register budget, either
+    # interpreter), tile, trials per work item and warps per CTA
     forced = None
     if rng.random() < 0.5:
-        v = int(rng.choice([0, 1, 2, 4, 5, 6]))
-        rpp = 32 * (8 if v in (0, 4) else 4)
+        v = int(rng.choice([0, 1, 2, 4, 5, 6, 8, 9]))
+        rpp = 32 * (8 if v in (0, 4, 8) else 4)
         forced = (v, rpp * int(rng.choice([1, 2, 4])), int(rng.integers(1, P + 1)),
                   int(rng.choice([1, 2, 4, 8, 16])))
     return dict(X=X, y=y, op=op, cval=cv, heights=hs.astype(np.int8), layout=layout, F=F,
@@ -60,7 +62,15 @@ def random_case(seed):
 
 @pytest.mark.parametrize("seed", range(40))
 def test_random_configurations(gg, seed):
-    w = random_case(seed)
+    run_case(gg, random_case(seed))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_configurations_wide(gg, seed):
+    run_case(gg, random_case(seed, wide=True))
+
+
+def run_case(gg, w):
     ds = gg.Dataset(torch.from_numpy(w["X"]), torch.from_numpy(w["y"]))
     op = torch.from_numpy(w["op"]).cuda()
     cv = torch.from_numpy(w["cval"]).cuda()
@@ -73,7 +83,12 @@ def test_random_configurations(gg, seed):
         flags |= gg.F_NO_FOLD
     P = w["P"]
     if w["forced"] is not None:
-        ds.tile_config(op, cv, hs, layout=lay, flags=flags, set=w["forced"])
+        try:
+            ds.tile_config(op, cv, hs, layout=lay, flags=flags, set=w["forced"])
+        except gg.GGEvalError:
+            # only the wide cases' forced tiles can exceed shared memory: the
+            # library refuses them and keeps its own configuration
+            assert w["F"] > 16, w["forced"]
     sentinel = -7.0
     outs = [torch.full((P,), sentinel, device="cuda") for _ in range(4)]
     if w["mask"] is None:

@@ -25,7 +25,17 @@ def gg():
 
 @pytest.mark.parametrize("seed", range(16))
 def test_random_gradients(gg, seed):
-    w = random_case(seed)
+    run_gradients(gg, random_case(seed), seed)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_gradients_wide(gg, seed):
+    """More than 16 features: the adjoint reads the features from global
+    memory (the kernel with 1, 2 or 4 rows per lane), per length class."""
+    run_gradients(gg, random_case(seed, wide=True), seed)
+
+
+def run_gradients(gg, w, seed):
     if int(w["heights"].max()) > 5 or w["N"] < 2:
         pytest.skip("the oracle's reverse mode is kept to heights up to 5 and two rows")
     mode = "mse" if seed % 3 == 2 else "smse"

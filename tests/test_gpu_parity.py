@@ -442,10 +442,10 @@ def test_rows_in_benchmark_configuration(gg, cfg, n_trials):
     ds.tile_config(sop, scv, set=(variant, tile, min(group, n_trials), warps))
     rows = ds.eval_rows(sop, scv)
     ref = rows.cpu().numpy()
-    for v in (0, 1, 2, 4, 5, 6):
+    for v in (0, 1, 2, 4, 5, 6, 8, 9):
         if v == variant:
             continue
-        r = 32 * (8 if v in (0, 4) else 4)
+        r = 32 * (8 if v in (0, 4, 8) else 4)
         ds.tile_config(sop, scv, set=(v, max(r, (tile // r) * r), min(group, n_trials), 8))
         other = ds.eval_rows(sop, scv).cpu().numpy()
         np.testing.assert_array_equal(other.view(np.uint32), ref.view(np.uint32), err_msg=f"variant {v}")
