@@ -88,9 +88,9 @@ NCU_TRAFFIC: dict = {
     # dram__bytes_read.sum 196,295,680 + dram__bytes_write.sum 487,198,720: X and
     # y from HBM (44 MB, re-read by later trial groups through L2) and the
     # per-(trial, tile) partial records (16,384 x 977 x 32 B = 512 MB)
-    ("large-16384xh6-1000000x10", "b35bfd2497ef5c82"): 683_494_400,
+    ("large-16384xh6-1000000x10", "8cffde60a4ef550f"): 683_494_400,
     # 4,984,320 + 2,560: X, y and programs once; partial records stay in L2
-    ("fos-step-4096xh4-100000x8", "b35bfd2497ef5c82"): 4_986_880,
+    ("fos-step-4096xh4-100000x8", "8cffde60a4ef550f"): 4_986_880,
 }
 STAT_COLS = {"term": 1, "addsubmul": 2, "aq": 3, "div": 4, "sincos": 5, "exp": 6, "log": 7,
              "sqrt": 8, "square": 9, "pow": 12}

@@ -398,8 +398,9 @@ __device__ __forceinline__ void run_program_tape(const uint2* prog, const float*
 // the form reads (a V entry or the feature's row in the tile; unused ones
 // point at V's first entry); w = the constant's bits.  The PTX sweep
 // (interp_rev_asm, generated by interp_gen.py) runs the forms of +, -, *,
-// AQ, the pushed ERC, square, log and sqrt; rev_cold_v runs every form (the
-// PTX leaves it sin, cos, exp, division and pow).
+// AQ, the pushed ERC and every unary operator (sin, cos and exp for a group
+// within their range); rev_cold_v runs every form (the PTX leaves it
+// division, pow and out-of-range groups).
 enum : uint32_t {
   RV_CONST = 0,       // a pushed ERC: its adjoint is the ERC's contribution
   RV_UN = 1,          // + u (1..8)

@@ -11,13 +11,15 @@ inline-PTX statement: every case ends by fetching the next instruction word
 
 Semantics are those of ``run_program`` in device.cuh, bit for bit: the same
 FP32 operations in the same order, two rows at a time as packed
-``.f32x2`` instructions, and row by row (gmath.cuh's ``*_total`` forms) for
-a group of rows in which some argument lies outside the common domain of
-exp, log or sqrt.  Instructions the PTX does not finish leave the statement
-with their opcode, and the C++ caller runs them (``exec_cold``) and
-re-enters: the end of the program (NOP), pow, and sin or cos with an
-argument beyond the reduction's range (the CUDA library function then takes
-those rows).
+``.f32x2`` instructions, and (4 rows per lane) row by row (gmath.cuh's
+``*_total`` forms) for a group of rows in which some argument lies outside
+the common domain of exp, log or sqrt.  Instructions the PTX does not finish
+leave the statement with their opcode, and the C++ caller runs them
+(``exec_cold``) and re-enters: the end of the program (NOP), pow, sin or cos
+with an argument beyond the reduction's range (the CUDA library function
+then takes those rows) and, with 8 rows per lane, such groups of exp, log or
+sqrt.  The file also generates the staged adjoint's reverse sweep
+(``RevGen``).
 
 Run by build.py before the CUDA sources are compiled; writes
 ``_build/gen/interp_asm.inc``.
