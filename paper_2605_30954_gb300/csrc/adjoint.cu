@@ -584,6 +584,7 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
     // stage: the interpreter's form of the program, and in program order
     // the ERC ordinals and the descriptors of the instructions with work
     int n_erc = 0, n_rev = 0;
+    uint32_t fmask = 0;  // the features the program reads (at most ADJ_FTILE_MAX)
     for (int k0 = 0; k0 <= L; k0 += 32) {
       const int k = k0 + lane;
       bool has = false, work = false;
@@ -592,6 +593,7 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
       if (k <= L) {
         const uint2 w = src[k];
         const uint32_t opc = w.x & 0xffu;
+        if (k < L && reads_feature(opc)) fmask |= 1u << (w.x >> 8);
         const uint32_t f = w.x >> 8;
         sprog[k] = make_uint2(opc, reads_feature(opc) ? f * SLOTB : w.y);
         if (k < L) {
@@ -641,6 +643,7 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
       n_rev += __popc(mw);
     }
     if (lane == 0) sprog[L + 1] = make_uint2(I_NOP, 0u);  // read ahead, never run
+    fmask = __reduce_or_sync(0xffffffffu, fmask);
     __syncwarp();
 
     const int r_beg = chunk * ch.chunk_rows;
@@ -650,7 +653,10 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
       bool valid[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) valid[r] = rb + lane * R + r < r_end;
-      for (int f = 0; f < p.F; ++f) {
+      // only the feature rows the program reads (a short program reads a
+      // few of them; the others' tile rows are never addressed)
+      for (uint32_t m = fmask; m != 0; m &= m - 1) {
+        const int f = __ffs(m) - 1;
         float v[R];
         load_rows<R>(p.X + (size_t)f * p.ldx + row0, v);
         store_rows<R>(xt + (size_t)f * SLOT, v);
