@@ -668,6 +668,9 @@ __global__ void __launch_bounds__(256) adjoint_fast_kernel(const AdjParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) A[r] = 0.f;
       run_program_tape<R, POW>(sprog, xt, A, stk, V);
+      // the stack's bytes are also the ERC partials, which the sweep writes
+      // across lanes: every lane leaves the forward recompute first
+      __syncwarp();
       seed_rows<R>(p, ab, A, yc, yl, valid, G);  // the root's adjoint, in registers
       if (n_rev > 0) {
         uint32_t vmask = 0;

@@ -86,7 +86,10 @@ struct TransposeParams {
 //   stk   [slots][32][R]    the forward stack
 //   part  [ecap][33]        per-pass ERC partial sums (32 lanes, padded)
 //   xt    [ftile][32][R]    the staged feature rows (staged kernel)
-// Every array starts on a 16-byte boundary.
+// Every array starts on a 16-byte boundary.  In the staged kernel stk and
+// part share their bytes: the forward recompute alone uses the stack, the
+// reverse sweep writes every ERC ordinal's partial of the pass before the
+// reduction reads it, and warp barriers separate the three phases.
 struct AdjLayout {
   size_t prog, aux, rins, wg, eord, ek, V, stk, part, xt, total;
 };
@@ -110,9 +113,15 @@ __host__ __device__ inline AdjLayout adj_layout(int lcap, int ecap, int slots, i
   l.V = o;
   o = adj_round16(o + (size_t)lcap * 32 * 4 * rows);
   l.stk = o;
-  o = adj_round16(o + (size_t)slots * 32 * 4 * rows);
-  l.part = o;
-  o = adj_round16(o + (size_t)ecap * 33 * 4);
+  const size_t stk_bytes = (size_t)slots * 32 * 4 * rows, part_bytes = (size_t)ecap * 33 * 4;
+  if (fast) {
+    l.part = o;
+    o = adj_round16(o + (stk_bytes > part_bytes ? stk_bytes : part_bytes));
+  } else {
+    o = adj_round16(o + stk_bytes);
+    l.part = o;
+    o = adj_round16(o + part_bytes);
+  }
   l.xt = o;
   if (fast) o = adj_round16(o + (size_t)ftile * 32 * 4 * rows);
   l.total = o;
