@@ -169,13 +169,20 @@ __device__ __forceinline__ void seed_rows(const AdjParams& p, const double* ab,
 // The pass's ERC sums: lane o adds up the 32 lane partials of the ERCs
 // o, o + 32, ... (rows padded to 33 floats: no bank conflicts) into its
 // error-free accumulators (one transposed reduction per pass instead of a
-// shuffle reduction per ERC instruction).
+// shuffle reduction per ERC instruction).  Four running sums over every
+// fourth partial keep the chain of dependent additions short.
 __device__ __forceinline__ void reduce_erc(const float* part, float2* wg, int n_erc, int lane) {
   for (int o = lane; o < n_erc; o += 32) {
     const float* q = part + (size_t)o * 33;
-    float sm = 0.f;
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) sm += q[j];
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      s0 += q[j];
+      s1 += q[j + 1];
+      s2 += q[j + 2];
+      s3 += q[j + 3];
+    }
+    const float sm = (s0 + s1) + (s2 + s3);
     float2 acc = wg[o];
     acc_add(acc.x, acc.y, sm);
     wg[o] = acc;
