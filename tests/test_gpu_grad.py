@@ -123,3 +123,32 @@ def test_constant_tuning_reduces_fitness(gg):
     assert improved >= 0.8, improved
     assert (s1[fin] < s0[fin] * 0.999).sum().item() >= 4
     ds.close()
+
+
+def test_adjoint_deep_stack_many_ercs(gg):
+    """Full height-6 trees (every leaf active; internal nodes +, -, AQ, x)
+    whose 64 leaves are 48 ERCs and 16 features: programs of 64
+    instructions that need the deepest forward stack (5 slots) and carry 48
+    ERCs (two rounds of the per-pass ERC reduction).  In the staged adjoint
+    the forward stack and the ERC partials share their shared-memory bytes;
+    here both are at their largest."""
+    import synth
+    w = PA.build("c5", 3000, 32)
+    rng = np.random.default_rng(11)
+    P, S = w["op"].shape
+    n_int = S // 2  # heap positions 0 .. 62 are internal, 63 .. 126 leaves
+    op = np.empty_like(w["op"])
+    cv = np.zeros_like(w["cval"])
+    op[:, :n_int] = rng.choice([synth.ADD, synth.SUB, synth.AQ, synth.MUL], size=(P, n_int),
+                               p=[0.35, 0.35, 0.2, 0.1])
+    leaves = np.full((P, S - n_int), synth.ERC, dtype=op.dtype)
+    for p in range(P):
+        k = rng.choice(S - n_int, 16, replace=False)
+        leaves[p, k] = synth.FEAT0 + rng.integers(0, w["F"], 16)
+    op[:, n_int:] = leaves
+    cv[:, n_int:] = rng.uniform(-1, 1, (P, S - n_int)).astype(cv.dtype)
+    w["op"], w["cval"] = op, cv
+    assert all(int(np.sum(op[p] == synth.ERC)) == 48 for p in range(P))
+    t, tf = grad_case(gg, w, name="adjoint full h6 trees, 48 ERCs each")
+    assert t.failed == 0 and tf.failed == 0, (repr(t), repr(tf))
+    assert t.checked >= P // 2, repr(t)
